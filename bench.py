@@ -1,0 +1,480 @@
+"""Benchmark of the SINDI search hot path on GB300.
+
+One step = one pass of the search over the workload's query batch (every query:
+window scan + window top-gamma, cross-window merge, exact rerank), with the
+index and the queries resident in HBM. The index build runs once before the
+timed region and is reported separately (build_ms).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                    [--workload pruned-1m] [--mode plain|batched]
+
+Under torchrun (N > 1) every rank searches its own share of queries against a
+replica of the index (queries are independent: weak scaling, no collective on
+the data path); the barrier and the max over ranks use torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    p.add_argument("--workload", default="pruned-1m")
+    p.add_argument("--mode", choices=["plain", "batched"], default="plain")
+    p.add_argument("--window", type=int, default=0, help="0 = the workload's window")
+    p.add_argument("--queries", type=int, default=0, help="0 = the workload's query count")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
+    p.add_argument("--no-forms", action="store_true", help="skip the batched / low-precision side lines")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(n):
+    import torch
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        try:
+            import torch
+
+            u = getattr(torch.cuda.get_device_properties(gpu_index), "uuid", None)
+            if u is not None:
+                self.gpu = "GPU-" + str(u)
+        except Exception:
+            pass
+        self.proc = None
+        self.path = os.path.join("/tmp", f"sindi_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, flags in rows:
+            for n, f in zip(names, flags[1:]):
+                if f.lower() in ("active", "0x1", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def measured_hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profile_traffic(kernel_src_sha):
+    """Per-launch DRAM bytes of the scan kernel from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "scan_window_pruned-1m.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if m and t and m.group(1) == kernel_src_sha:
+        return float(t.group(1))
+    return None
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in ("search.cu", "primitives.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2509_08395_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def postings_touched(seg, sigma, dim, qp, qx):
+    """Per query: sum over its terms of |I_j| (all windows) = postings the scan reads."""
+    j = np.arange(dim, dtype=np.int64)
+    lens = seg[(j + 1) * sigma].astype(np.int64) - seg[j * sigma].astype(np.int64)
+    out = np.empty(len(qp) - 1, np.int64)
+    for r in range(len(qp) - 1):
+        out[r] = lens[qx[qp[r]:qp[r + 1]]].sum()
+    return out
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, budget_s, gpu_ids=None, k=None):
+    """The oracle as it stands, single-threaded, on a bounded sample of the workload's queries.
+
+    Returns (qps, n_sampled, recall list vs FP64 brute force for the GPU ids if given)."""
+    import oracle
+
+    D = oracle.Dataset(ip, ix, v, w.dim)
+    Q = oracle.Dataset(qp, qx, qv, w.dim)
+    I = oracle.Index(D, window=w.window, alpha=w.alpha)
+    done, t0 = 0, time.perf_counter()
+    elapsed = 0.0
+    while done < Q.n and elapsed < budget_s:
+        I.search(Q, done, k=w.k, gamma=w.gamma)
+        done += 1
+        elapsed = time.perf_counter() - t0
+    qps = done / elapsed if elapsed > 0 else 0.0
+    recalls = []
+    if gpu_ids is not None:
+        # FP64 exact ground truth on an evenly spread sample of the same queries
+        t1 = time.perf_counter()
+        step = max(1, Q.n // 40)
+        for r in range(0, Q.n, step):
+            truth, _ = oracle.brute_force(D, Q, r, k)
+            recalls.append(oracle.recall(gpu_ids[r], truth))
+            if time.perf_counter() - t1 > budget_s:
+                break
+    return qps, done, recalls
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, bounded samples of the workload per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    w = datagen.WORKLOADS[args.workload]
+    if args.window:
+        w = w.scaled(window=args.window)
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    D = oracle.Dataset(ip, ix, v, w.dim)
+    Q = oracle.Dataset(qp, qx, qv, w.dim)
+    I = oracle.Index(D, window=w.window, alpha=w.alpha)
+    per_step = 4
+    nxt = 0
+    for _ in range(args.warmup):
+        for _ in range(per_step):
+            I.search(Q, nxt % Q.n, k=w.k, gamma=w.gamma)
+            nxt += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            I.search(Q, nxt % Q.n, k=w.k, gamma=w.gamma)
+            nxt += 1
+    el = time.perf_counter() - t0
+    qps = args.steps * per_step / el
+    line = {
+        "impl": "reference", "metric": "QPS at Recall@50>=0.99 (sparse MIPS, top-50)", "value": qps,
+        "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_docs": w.docs.n_rows, "dim": w.dim, "k": w.k, "gamma": w.gamma,
+                   "alpha": w.alpha, "window": w.window, "queries_per_step": per_step},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps * per_step} queries of {w.name}, single-threaded FP64 oracle"},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_2509_08395_gb300 as sindi
+
+    rank, ws, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    w = datagen.WORKLOADS[args.workload]
+    if args.window:
+        w = w.scaled(window=args.window)
+    if args.queries:
+        w = w.scaled(n_queries=args.queries)
+    # each rank its own queries (weak scaling); rank 0 gets the workload's seed
+    wq = w.scaled(query_seed=w.query_seed + 7919 * rank)
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(wq)
+    nq = len(qp) - 1
+
+    t_b0 = time.perf_counter()
+    dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
+    torch.cuda.synchronize()
+    t_b1 = time.perf_counter()
+    idx = sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=w.alpha, value_dtype="f32")
+    torch.cuda.synchronize()
+    build_ms = 1000 * (time.perf_counter() - t_b1)
+    h2d_docs_ms = 1000 * (t_b1 - t_b0)
+    del dip, dix, dv
+    info = idx.info
+
+    q_dev = [torch.from_numpy(a).to(dev) for a in (qp, qx, qv)]
+    out_ids = torch.empty((nq, w.k), dtype=torch.int32, device=dev)
+    out_sc = torch.empty((nq, w.k), dtype=torch.float32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(mode):
+        idx.search(*q_dev, k=w.k, gamma=w.gamma, mode=mode, out=(out_ids, out_sc))
+
+    for _ in range(args.warmup):
+        step(args.mode)
+    idx.check()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time of K steps, L2 flushed between steps
+    sindi.sindi_reset_stats(idx.handle)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            step(args.mode)
+            e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    stats = sindi.sindi_get_stats(idx.handle)
+    dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    dev_ms_max = max_over_ranks(dev_ms, ws)
+    idx.check()
+    value = ws * nq * args.steps / (dev_ms_max / 1000.0)
+    launches = int(stats["launches"])
+
+    # ---- roofline pass: CUDA events around every scan launch (same steps again)
+    sindi.sindi_reset_stats(idx.handle)
+    sindi.sindi_set_timing(idx.handle, True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step(args.mode)
+    torch.cuda.synchronize()
+    sindi.sindi_set_timing(idx.handle, False)
+    st2 = sindi.sindi_get_stats(idx.handle)
+    scan_ms_per_launch = st2["scan_ms"] / max(1, st2["scan_timed"])
+    ex = idx.export()
+    sigma = info["n_windows"]
+    touched = postings_touched(ex["seg"], sigma, w.dim, qp, qx)
+    vbytes = {0: 4, 1: 2, 2: 1}[info["value_dtype"]]
+    nterms = np.diff(qp)
+    # algorithmic bytes of one scan launch: postings (uint16 id + value) + the two offsets of every
+    # (term, window) + the query's terms; a plain launch covers one query, a batched launch all of them
+    per_query_bytes = touched * (2 + vbytes) + nterms * sigma * 8 + nterms * 8
+    queries_per_launch = 1 if args.mode == "plain" else nq
+    alg_bytes_per_launch = float(per_query_bytes.mean()) * queries_per_launch
+    achieved_gbs = alg_bytes_per_launch / (scan_ms_per_launch / 1000.0) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    sha = source_sha()
+
+    # ---- e2e through the public C ABI with pinned host buffers (copies inside the timed region)
+    h_ip = torch.from_numpy(qp).pin_memory()
+    h_ix = torch.from_numpy(qx).pin_memory()
+    h_v = torch.from_numpy(qv).pin_memory()
+    h_ids = torch.empty((nq, w.k), dtype=torch.int32).pin_memory()
+    h_sc = torch.empty((nq, w.k), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        idx.search(h_ip, h_ix, h_v, k=w.k, gamma=w.gamma, mode=args.mode, out=(h_ids, h_sc), stream=stream.cuda_stream)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        idx.search(h_ip, h_ix, h_v, k=w.k, gamma=w.gamma, mode=args.mode, out=(h_ids, h_sc), stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    barrier(ws)
+    e2e = ws * nq * args.steps / e2e_s
+    h2d = int(h_ip.numel() * 8 + h_ix.numel() * 4 + h_v.numel() * 4)
+    d2h = int(h_ids.numel() * 4 + h_sc.numel() * 4)
+    gpu_ids = out_ids.cpu().numpy().view(np.uint32)
+    assert np.array_equal(gpu_ids, h_ids.numpy().view(np.uint32)), "host-buffer results differ from device results"
+
+    # ---- side forms on the same queries (batched schedule; FP16 / FP8 postings)
+    forms = {}
+    if not args.no_forms:
+        def timed(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            return nq * reps / (tot / 1000.0)
+
+        other = "batched" if args.mode == "plain" else "plain"
+        forms[other] = {"qps": timed(lambda: step(other), args.steps)}
+        forms[other]["ids_equal_to_main"] = float(np.mean(out_ids.cpu().numpy().view(np.uint32) == gpu_ids))
+        for dt in ("f16", "f8"):
+            dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
+            with sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=w.alpha, value_dtype=dt) as lp:
+                del dip, dix, dv
+                oi = torch.empty_like(out_ids)
+                os_ = torch.empty_like(out_sc)
+                qps = timed(lambda: lp.search(*q_dev, k=w.k, gamma=w.gamma, mode=args.mode, out=(oi, os_)),
+                            args.steps)
+                lp.check()
+                forms[dt + "_" + args.mode] = {"qps": qps, "_ids": oi.cpu().numpy().view(np.uint32)}
+
+    # ---- CPU baseline (oracle) + recall against FP64 exact, rank 0 only
+    cpu = None
+    recall = None
+    if rank == 0:
+        qps_cpu, n_cpu, recalls = cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, args.cpu_seconds, gpu_ids, w.k)
+        recall = float(np.mean(recalls)) if recalls else None
+        cpu = {"value": qps_cpu, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {n_cpu} of {nq} queries of {w.name} (Algorithm 4, FP64, single thread, "
+                         f"about {args.cpu_seconds:.0f} s)"}
+        if forms:
+            import oracle
+
+            D = oracle.Dataset(ip, ix, v, w.dim)
+            Q = oracle.Dataset(qp, qx, qv, w.dim)
+            step_r = max(1, nq // 40)
+            truth = {r: oracle.brute_force(D, Q, r, w.k)[0] for r in range(0, nq, step_r)}
+            for name, f in forms.items():
+                if "_ids" in f:
+                    f["recall_at_k"] = float(np.mean([oracle.recall(f["_ids"][r], t) for r, t in truth.items()]))
+                    del f["_ids"]
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": "QPS at Recall@50>=0.99 (sparse MIPS, top-50)",
+        "value": value,
+        "unit": "queries/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dev_ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n_docs": w.docs.n_rows, "dim": w.dim, "queries_per_rank": nq,
+                   "k": w.k, "gamma": w.gamma, "alpha": w.alpha, "window": info["window"],
+                   "n_windows": sigma, "postings": info["postings"], "mode": args.mode,
+                   "batch": 1 if args.mode == "plain" else nq,
+                   "l2": "flushed between steps (256 MiB write)"},
+        "recall_at_k": recall,
+        "build_ms": build_ms,
+        "h2d_docs_ms": h2d_docs_ms,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": achieved_gbs / peak, "peak_kind": peak_kind,
+                     "frac_of_nominal_8tbs": achieved_gbs / NOMINAL_HBM_GBS,
+                     "traffic": profile_traffic(sha), "kernel": "scan_window_kernel",
+                     "alg_bytes_per_launch": alg_bytes_per_launch, "ms_per_launch": scan_ms_per_launch,
+                     "postings_per_query": float(touched.mean())},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "forms": forms,
+        "scan_source_sha256": sha,
+    }
+    print(json.dumps(line), flush=True)
+    idx.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * sindi.h — C ABI of the GB300 (sm_103a) implementation of SINDI's search
+ * hot path (arXiv 2509.08395, "SINDI: an Efficient Index for Sparse Vector
+ * Approximate Maximum Inner Product Search").
+ *
+ * What the library computes
+ *   Build (Algorithm 3, with Algorithm 1 inside): every document x_i is cut
+ *   to its alpha-mass subvector (Sec. 4.1, Definition "alpha-Mass
+ *   Subvector"); the kept entries become value-storing inverted lists
+ *   (Sec. 3.1) split into windows of lambda document ids, I_{j,w}
+ *   (Sec. 3.3.1). The unpruned documents stay on the device for reordering.
+ *   Search (Algorithm 4, with Algorithm 2 inside): for every window w and
+ *   every query term q^j, A[i mod lambda] += q^j * x_i^j over I_{j,w}; the
+ *   best gamma (score, id) pairs over all windows are the candidates; their
+ *   exact inner products delta(x_i, q) (Definition 2) on the full vectors
+ *   give the top-k.
+ *
+ * Conventions shared by every call
+ *   - Sparse matrices are CSR: indptr int64[n+1] (indptr[0] = 0,
+ *     non-decreasing), indices int32[nnz] (dims in [0, dim), unique within a
+ *     row, any order), values float32[nnz] (finite). Explicit zeros are not
+ *     entries (Definition 1) and are ignored.
+ *   - Pointers may be host or device memory; the library asks the CUDA
+ *     driver which. All inputs of one call must be of one kind, and all
+ *     outputs of one kind.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - Order of results: larger score first; equal scores: lower document
+ *     id first (the paper does not fix tie order).
+ *   - The caller owns every buffer it passes. The library owns the index
+ *     and all scratch memory it allocates (stream-ordered, from a pool of
+ *     its own that keeps freed blocks for reuse).
+ *   - Errors: invalid arguments are reported before any device work with
+ *     SINDI_ERR_INVALID_ARG. Malformed data is found on the device; it sets
+ *     the index's error word, which sindi_build returns at once and which a
+ *     search returns when it synchronises (host buffers) or on the next
+ *     sindi_check. No exception crosses the ABI; sindi_last_error() holds a
+ *     message for the calling thread.
+ *   - An index is never modified by a search, so searches on different
+ *     streams may run concurrently.
+ */
+#ifndef SINDI_H
+#define SINDI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sindi_index sindi_index;
+
+typedef enum {
+    SINDI_OK = 0,
+    SINDI_ERR_INVALID_ARG = 1,   /* bad pointer, size or parameter; nothing ran            */
+    SINDI_ERR_INVALID_DATA = 2,  /* malformed CSR contents found on the device             */
+    SINDI_ERR_OOM = 3,           /* device memory exhausted                                 */
+    SINDI_ERR_CUDA = 4,          /* a CUDA call failed (message in sindi_last_error)        */
+    SINDI_ERR_TIMEOUT = 5,       /* a bounded device wait gave up                           */
+    SINDI_ERR_UNSUPPORTED = 6    /* valid but outside what this build handles              */
+} sindi_status;
+
+/* Storage type of posting values (the reduced-precision form; the paper
+   stores full-precision values). Accumulation is FP32 in every case. */
+typedef enum {
+    SINDI_F32 = 0,
+    SINDI_F16 = 1,      /* IEEE binary16, round to nearest even               */
+    SINDI_F8E4M3 = 2    /* OCP FP8 E4M3 with one FP32 scale per list I_j:
+                           scale_j = max|x| over I_j / 448; code = RNE(x / scale_j),
+                           saturating; the stored value is code * scale_j    */
+} sindi_dtype;
+
+/* Search schedule. Both give the same results (within FP32 rounding). */
+typedef enum {
+    SINDI_MODE_PLAIN = 0,    /* one query per launch sequence                         */
+    SINDI_MODE_BATCHED = 1   /* all queries of the call in shared launches             */
+} sindi_mode;
+
+/* Parameters of Algorithm 3. */
+typedef struct {
+    uint32_t window;       /* lambda, documents per window (Sec. 3.3.1); 1..32768.
+                              0 picks a default. A window's FP32 score array lives
+                              in one thread block's shared memory.                */
+    int32_t value_dtype;   /* sindi_dtype                                          */
+    double alpha;          /* document pruning ratio in (0, 1]; 1 = no pruning     */
+} sindi_build_params;
+
+/* Parameters of Algorithm 4. */
+typedef struct {
+    uint32_t k;            /* results per query, 1..1024                            */
+    uint32_t gamma;        /* reorder pool size; 0 = no reordering (the coarse
+                              top-k is the answer), else k <= gamma <= 8192        */
+    double beta;           /* query pruning ratio in (0, 1]; 1 = off              */
+    uint32_t mode;         /* sindi_mode                                           */
+    uint32_t reserved;     /* must be 0                                            */
+} sindi_search_params;
+
+typedef struct {
+    int64_t n_docs;        /* ||D||                                               */
+    int32_t dim;           /* d                                                   */
+    int32_t value_dtype;   /* sindi_dtype                                         */
+    uint32_t window;       /* lambda                                              */
+    uint32_t n_windows;    /* sigma = ceil(||D|| / lambda)                        */
+    int64_t postings;      /* kept entries = sum of |alpha-mass(x_i)|             */
+    int64_t doc_nnz;       /* entries of the unpruned documents                   */
+    int64_t index_bytes;   /* device bytes of lists + offsets + scales            */
+    int64_t doc_bytes;     /* device bytes of the unpruned documents              */
+    double alpha;
+} sindi_index_info_t;
+
+/* Counters of the calling index (for benchmarks). */
+typedef struct {
+    uint64_t launches;         /* kernels launched by searches on this index     */
+    uint64_t scan_launches;    /* of which window-scan kernels                    */
+    uint64_t queries;          /* queries searched                                */
+    double scan_ms;            /* summed CUDA-event time of scan kernels while
+                                  timing is on (see sindi_set_timing)              */
+    uint64_t scan_timed;       /* scan launches included in scan_ms               */
+} sindi_stats_t;
+
+/*
+ * Build an index (Algorithm 3: alpha-mass every document, then Algorithm 1
+ * over the pruned documents, with the lists split into windows as in
+ * Sec. 3.3.1). Postings are sorted by (dim, document) on the device; inside
+ * a list I_{j,w} they are in ascending document id, stored as the 16-bit
+ * window-local id i mod lambda beside the value.
+ *   indptr/indices/values: the documents (CSR, see conventions), n_docs rows,
+ *       n_docs < 2^32 - 1, dims in [0, dim).
+ *   params: see sindi_build_params. NULL = window 0, FP32, alpha 1.
+ *   stream: the stream the build runs on; the call returns when it is done.
+ *   out: receives the new index (owned by the caller, free with
+ *       sindi_index_free). Untouched on error.
+ * Returns SINDI_ERR_INVALID_DATA for a malformed CSR (decreasing indptr, dim
+ * out of range, duplicate dim in a row, non-finite value) and
+ * SINDI_ERR_UNSUPPORTED for a row with more than 16384 entries or more than
+ * 2^32 - 1 kept entries in total.
+ */
+sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const float* values,
+                         int64_t n_docs, int32_t dim, const sindi_build_params* params,
+                         void* stream, sindi_index** out);
+
+/*
+ * Search a batch of queries (Algorithm 4 per query, with Algorithm 2 for the
+ * coarse stage and exact reordering of the gamma candidates).
+ *   q_indptr/q_indices/q_values: the queries (CSR), n_queries rows (>= 0).
+ *   params: see sindi_search_params (not NULL).
+ *   out_ids:    uint32 [n_queries * k], row-major; document ids.
+ *   out_scores: float  [n_queries * k]; delta(x_i, q) in FP32 when gamma > 0,
+ *               else the coarse score. When the index has fewer than k
+ *               documents, the tail of each row is id 0xFFFFFFFF, score -inf.
+ *   stream: device inputs and outputs: the search is queued on the stream and
+ *       the call returns at once. Host inputs or outputs: the call copies
+ *       through device memory and returns when the results are in place.
+ * Malformed queries (dim out of range, duplicate dim, non-finite value) set
+ * the index's error word; they never read outside the index.
+ */
+sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
+                          const float* q_values, int64_t n_queries, const sindi_search_params* params,
+                          uint32_t* out_ids, float* out_scores, void* stream);
+
+/* Synchronise `stream`, then return (and clear) the device error word of the
+   index as a status: SINDI_ERR_INVALID_DATA if a malformed query or document
+   was seen since the last check, SINDI_ERR_TIMEOUT if a bounded wait gave up. */
+sindi_status sindi_check(const sindi_index* index, void* stream);
+
+/* Sizes and parameters of an index. */
+sindi_status sindi_index_info(const sindi_index* index, sindi_index_info_t* out);
+
+/*
+ * Copy the index layout to host buffers (for inspection and tests).
+ *   seg:   uint32 [dim * n_windows + 1]; list I_{j,w} is postings
+ *          seg[j * n_windows + w] .. seg[j * n_windows + w + 1] - 1.
+ *   ids:   uint16 [postings]; window-local id i mod lambda.
+ *   vals:  [postings] of the value dtype (float / binary16 bits / E4M3 codes).
+ *   scale: float [dim]; per-list E4M3 scale (1 for the other dtypes).
+ *   kept:  uint32 [n_docs]; |alpha-mass(x_i)| for every document.
+ * Any pointer may be NULL to skip that array.
+ */
+sindi_status sindi_index_export(const sindi_index* index, uint32_t* seg, uint16_t* ids, void* vals,
+                                float* scale, uint32_t* kept);
+
+/* Turn CUDA-event timing of scan kernels on (1) or off (0), and read or reset
+   the index's counters. */
+sindi_status sindi_set_timing(const sindi_index* index, int enable);
+sindi_status sindi_get_stats(const sindi_index* index, sindi_stats_t* out);
+sindi_status sindi_reset_stats(const sindi_index* index);
+
+/* Free an index and everything it owns. NULL is ignored. Waits for work
+   queued on the index's streams to finish. */
+void sindi_index_free(sindi_index* index);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sindi_last_error(void);
+
+/* Library version string. */
+const char* sindi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SINDI_H */

@@ -1,0 +1,22 @@
+"""GB300 (sm_103a) implementation of SINDI's sparse MIPS search hot path (arXiv 2509.08395).
+
+The computation lives in hand-written CUDA kernels behind the C ABI of
+``include/sindi.h`` (``lib/libsindi.so``); ``sindi`` is its Python binding.
+"""
+from .sindi import (  # noqa: F401
+    DTYPES,
+    MODES,
+    Index,
+    SindiError,
+    load,
+    sindi_build,
+    sindi_check,
+    sindi_get_stats,
+    sindi_index_export,
+    sindi_index_free,
+    sindi_index_info,
+    sindi_reset_stats,
+    sindi_search,
+    sindi_set_timing,
+    sindi_version,
+)

@@ -1,0 +1,449 @@
+// Index construction on the device: Algorithm 3 (alpha-mass of every
+// document, Sec. 4.1) followed by Algorithm 1 (value-storing inverted lists,
+// Sec. 3.1) with the lists cut into windows of lambda ids (Sec. 3.3.1).
+//
+// Pipeline (one stream):
+//   validate_indptr  -> prune_rows (warp per row) [+ prune_long_rows (block per row)]
+//   -> exclusive scan of kept counts -> compact -> (window, dim) counts -> scan = seg
+//   -> stable radix sort of kept entries by dim (input is in document order, so
+//      equal dims stay in ascending document id: the order is (dim, doc))
+//   -> [E4M3 per-list scales] -> pack (uint16 window-local id + value).
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "index.cuh"
+#include "primitives.cuh"
+
+namespace sindi {
+
+constexpr int kPruneWarps = 8;                 // warps per block in prune_rows
+constexpr int kPruneRowCap = 1024;             // longest row a warp sorts (smem 8 KB / warp)
+
+__global__ void validate_indptr_kernel(const int64_t* indptr, int64_t n, uint32_t* err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && indptr[0] != 0) atomicOr(err, kErrDocIndptr);
+    if (i < n && indptr[i + 1] < indptr[i]) atomicOr(err, kErrDocIndptr);
+}
+
+void launch_validate_indptr(const int64_t* indptr, int64_t n, uint32_t* err, cudaStream_t stream) {
+    const int64_t threads = n + 1;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    validate_indptr_kernel<<<blocks, 256, 0, stream>>>(indptr, n, err);
+    SINDI_CUDA(cudaGetLastError());
+}
+
+// Sort key for the alpha-mass order pi: |x| descending, then dim ascending.
+// High word: bit-inverted |x| (positive floats order like their bit patterns).
+// Low word: dim << 1 | sign of x, so the signed value can be rebuilt.
+__device__ __forceinline__ uint64_t mass_key(int32_t j, float v) {
+    uint32_t a = __float_as_uint(fabsf(v));
+    uint32_t lo = ((uint32_t)j << 1) | (__float_as_uint(v) >> 31);
+    return ((uint64_t)(~a) << 32) | lo;
+}
+
+__device__ __forceinline__ float mass_key_abs(uint64_t k) { return __uint_as_float(~(uint32_t)(k >> 32)); }
+__device__ __forceinline__ int32_t mass_key_dim(uint64_t k) { return (int32_t)((uint32_t)k >> 1); }
+__device__ __forceinline__ float mass_key_value(uint64_t k) {
+    float a = mass_key_abs(k);
+    return ((uint32_t)k & 1u) ? -a : a;
+}
+
+// The alpha-mass rule on a row already sorted by mass_key (m_nz non-zero
+// entries first). FP64, sequential in pi order, exactly as the definition
+// reads: mass = sum |x|, r = smallest r with prefix_r >= alpha * mass.
+__device__ __forceinline__ int alpha_mass_count(const uint64_t* s, int m_nz, double alpha) {
+    if (m_nz == 0) return 0;
+    if (alpha >= 1.0) return m_nz;
+    double mass = 0.0;
+    for (int t = 0; t < m_nz; t++) mass = __dadd_rn(mass, (double)mass_key_abs(s[t]));
+    const double target = __dmul_rn(alpha, mass);
+    double prefix = 0.0;
+    for (int t = 0; t < m_nz; t++) {
+        prefix = __dadd_rn(prefix, (double)mass_key_abs(s[t]));
+        if (prefix >= target) return t + 1;
+    }
+    return m_nz;
+}
+
+// One warp per document. Validates the row (dims in range, finite values, no
+// duplicate dim), computes r_i = |alpha-mass(x_i)| and writes the kept
+// entries (in pi order) to kdim/kval at the row's own input positions.
+__global__ void __launch_bounds__(kPruneWarps * 32) prune_rows_kernel(
+    const int64_t* indptr, const int32_t* indices, const float* values, int64_t n, int32_t dim, double alpha,
+    uint32_t* kept, int32_t* kdim, float* kval, uint32_t* long_rows, uint32_t* n_long, uint32_t* err) {
+    __shared__ uint64_t sm[kPruneWarps][kPruneRowCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* s = sm[warp];
+    for (int64_t i = (int64_t)blockIdx.x * kPruneWarps + warp; i < n; i += (int64_t)gridDim.x * kPruneWarps) {
+        const int64_t b = indptr[i];
+        const int64_t m = indptr[i + 1] - b;
+        if (m > kPruneRowCap) {
+            if (lane == 0) {
+                if (m > kMaxRowNnz) {
+                    atomicOr(err, kErrDocTooLong);
+                    kept[i] = 0;
+                } else {
+                    uint32_t slot = atomicAdd(n_long, 1u);
+                    long_rows[slot] = (uint32_t)i;
+                }
+            }
+            continue;
+        }
+        const int mm = (int)m;
+        int p2 = 32;
+        while (p2 < mm) p2 <<= 1;
+        // 1) dims: range check, and duplicates unless the row is strictly ascending
+        bool bad = false, ascending = true;
+        for (int t = lane; t < p2; t += 32) {
+            if (t < mm) {
+                int32_t j = indices[b + t];
+                float v = values[b + t];
+                if (j < 0 || j >= dim) { bad = true; atomicOr(err, kErrDocDim); }
+                if (!isfinite(v)) { bad = true; atomicOr(err, kErrDocValue); }
+                if (t + 1 < mm && indices[b + t + 1] <= j) ascending = false;
+                s[t] = ((uint64_t)(uint32_t)j << 32) | (uint32_t)t;
+            } else {
+                s[t] = ~0ull;
+            }
+        }
+        bad = __any_sync(kFull, bad);
+        ascending = __all_sync(kFull, ascending);
+        __syncwarp();
+        if (bad) {
+            if (lane == 0) kept[i] = 0;
+            continue;
+        }
+        if (!ascending) {
+            warp_bitonic_sort_asc(s, p2);
+            bool dup = false;
+            for (int t = lane + 1; t < mm; t += 32)
+                if ((s[t] >> 32) == (s[t - 1] >> 32)) dup = true;
+            dup = __any_sync(kFull, dup);
+            __syncwarp();
+            if (dup) {
+                if (lane == 0) {
+                    atomicOr(err, kErrDocDup);
+                    kept[i] = 0;
+                }
+                continue;
+            }
+        }
+        // 2) the pi order; explicit zeros are not entries (Definition 1) and sort last
+        int nz = 0;
+        for (int t = lane; t < p2; t += 32) {
+            uint64_t key = ~0ull;
+            if (t < mm) {
+                float v = values[b + t];
+                if (v != 0.0f) {
+                    key = mass_key(indices[b + t], v);
+                    nz++;
+                }
+            }
+            s[t] = key;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(kFull, nz, o);
+        __syncwarp();
+        warp_bitonic_sort_asc(s, p2);
+        int r = 0;
+        if (lane == 0) r = alpha_mass_count(s, nz, alpha);
+        r = __shfl_sync(kFull, r, 0);
+        for (int t = lane; t < r; t += 32) {
+            kdim[b + t] = mass_key_dim(s[t]);
+            kval[b + t] = mass_key_value(s[t]);
+        }
+        if (lane == 0) kept[i] = (uint32_t)r;
+        __syncwarp();
+    }
+}
+
+// One block per long row (kPruneRowCap < m <= kMaxRowNnz); same rules.
+constexpr int kLongBlock = 512;
+__global__ void __launch_bounds__(kLongBlock) prune_long_rows_kernel(
+    const int64_t* indptr, const int32_t* indices, const float* values, const uint32_t* rows, int32_t dim,
+    double alpha, uint32_t* kept, int32_t* kdim, float* kval, uint32_t* err) {
+    extern __shared__ uint64_t s[];
+    __shared__ int flags[2];
+    __shared__ int s_r;
+    const int64_t i = rows[blockIdx.x];
+    const int64_t b = indptr[i];
+    const int mm = (int)(indptr[i + 1] - b);
+    int p2 = 32;
+    while (p2 < mm) p2 <<= 1;
+    if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; }
+    __syncthreads();
+    for (int t = threadIdx.x; t < p2; t += kLongBlock) {
+        if (t < mm) {
+            int32_t j = indices[b + t];
+            float v = values[b + t];
+            if (j < 0 || j >= dim) { flags[0] = 1; atomicOr(err, kErrDocDim); }
+            if (!isfinite(v)) { flags[0] = 1; atomicOr(err, kErrDocValue); }
+            s[t] = ((uint64_t)(uint32_t)j << 32) | (uint32_t)t;
+        } else {
+            s[t] = ~0ull;
+        }
+    }
+    __syncthreads();
+    if (flags[0]) {
+        if (threadIdx.x == 0) kept[i] = 0;
+        return;
+    }
+    // ascending sort of dims: reuse the descending sort on inverted keys
+    for (int t = threadIdx.x; t < p2; t += kLongBlock) s[t] = ~s[t];
+    __syncthreads();
+    block_bitonic_sort_desc<kLongBlock>(s, p2);
+    for (int t = threadIdx.x + 1; t < mm; t += kLongBlock)
+        if (((~s[t]) >> 32) == ((~s[t - 1]) >> 32)) flags[1] = 1;
+    __syncthreads();
+    if (flags[1]) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, kErrDocDup);
+            kept[i] = 0;
+        }
+        return;
+    }
+    __shared__ int s_nz;
+    if (threadIdx.x == 0) s_nz = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < p2; t += kLongBlock) {
+        uint64_t key = ~0ull;
+        if (t < mm) {
+            float v = values[b + t];
+            if (v != 0.0f) {
+                key = mass_key(indices[b + t], v);
+                atomicAdd(&s_nz, 1);
+            }
+        }
+        s[t] = ~key;  // descending sort of inverted keys = ascending mass_key
+    }
+    __syncthreads();
+    block_bitonic_sort_desc<kLongBlock>(s, p2);
+    for (int t = threadIdx.x; t < p2; t += kLongBlock) s[t] = ~s[t];
+    __syncthreads();
+    if (threadIdx.x == 0) s_r = alpha_mass_count(s, s_nz, alpha);
+    __syncthreads();
+    const int r = s_r;
+    for (int t = threadIdx.x; t < r; t += kLongBlock) {
+        kdim[b + t] = mass_key_dim(s[t]);
+        kval[b + t] = mass_key_value(s[t]);
+    }
+    if (threadIdx.x == 0) kept[i] = (uint32_t)r;
+}
+
+// Kept entries of every row -> compact arrays in document order.
+__global__ void compact_kernel(const int64_t* indptr, const int64_t* kept_off, const int32_t* kdim, const float* kval,
+                               int64_t n, uint32_t* sdim, uint32_t* sdoc, uint32_t* sval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int64_t b = indptr[i], o = kept_off[i], r = kept_off[i + 1] - o;
+        for (int64_t t = lane; t < r; t += 32) {
+            sdim[o + t] = (uint32_t)kdim[b + t];
+            sdoc[o + t] = (uint32_t)i;
+            sval[o + t] = __float_as_uint(kval[b + t]);
+        }
+    }
+}
+
+// Count postings of every list I_{j,w}: cnt[j * sigma + w].
+__global__ void list_count_kernel(const uint32_t* sdim, const uint32_t* sdoc, int64_t P, uint32_t lambda,
+                                  uint32_t sigma, uint32_t* cnt) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[(uint64_t)sdim[p] * sigma + sdoc[p] / lambda], 1u);
+}
+
+// Per-list E4M3 scale: max |x| over the list I_j (all windows) / 448.
+__global__ void list_scale_kernel(const uint32_t* seg, const uint32_t* sval, int32_t dim, uint32_t sigma,
+                                  float* scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < dim; j += warps) {
+        const uint32_t lo = seg[(uint64_t)j * sigma], hi = seg[(uint64_t)(j + 1) * sigma];
+        float amax = 0.0f;
+        for (uint32_t p = lo + lane; p < hi; p += 32) amax = fmaxf(amax, fabsf(__uint_as_float(sval[p])));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, o));
+        if (lane == 0) {
+            float sc = __fdiv_rn(amax, 448.0f);
+            scale[j] = sc > 0.0f ? sc : 1.0f;
+        }
+    }
+}
+
+// Window-local ids and stored values.
+template <int DT>
+__global__ void pack_kernel(const uint32_t* sdim, const uint32_t* sdoc, const uint32_t* sval, int64_t P,
+                            uint32_t lambda, const float* scale, uint16_t* pid, void* pval) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        pid[p] = (uint16_t)(sdoc[p] % lambda);
+        float v = __uint_as_float(sval[p]);
+        if (DT == SINDI_F32) {
+            static_cast<float*>(pval)[p] = v;
+        } else if (DT == SINDI_F16) {
+            static_cast<__half*>(pval)[p] = __float2half_rn(v);
+        } else {
+            float ratio = __fdiv_rn(v, scale[sdim[p]]);
+            static_cast<__nv_fp8_storage_t*>(pval)[p] = __nv_cvt_float_to_fp8(ratio, __NV_SATFINITE, __NV_E4M3);
+        }
+    }
+}
+
+__global__ void fill_u32_kernel(float* p, int64_t n, float v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+static int grid_for(int64_t n, int block, int cap = 152 * 16) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+static uint32_t read_u32(const uint32_t* d, cudaStream_t s) {
+    uint32_t h = 0;
+    SINDI_CUDA(cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, s));
+    SINDI_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+static int64_t read_i64(const int64_t* d, cudaStream_t s) {
+    int64_t h = 0;
+    SINDI_CUDA(cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s));
+    SINDI_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+static std::string doc_error_text(uint32_t e) {
+    std::string m;
+    if (e & kErrDocIndptr) m += "indptr[0] != 0 or decreasing; ";
+    if (e & kErrDocDim) m += "a document dim outside [0, dim); ";
+    if (e & kErrDocValue) m += "a non-finite document value; ";
+    if (e & kErrDocDup) m += "a dim repeated within a document; ";
+    if (e & kErrDocTooLong) m += "a document row longer than 16384 entries; ";
+    return m;
+}
+
+// Builds the lists of `ix`. Its documents are on the device and indptr has
+// been validated (indptr[0] = 0, non-decreasing). Allocates the index arrays
+// (seg, pid, pval, scale, kept) from the library pool; they belong to `ix`.
+// Returns SINDI_OK or an error status with the message set.
+sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
+    Pool P{ix.pool, stream};
+    const int64_t n = ix.n_docs;
+    const int32_t d = ix.dim;
+    const uint32_t lambda = ix.lambda;
+    const uint32_t sigma = ix.sigma;
+    uint32_t e = 0;
+    ix.kept = P.alloc<uint32_t>(n > 0 ? n : 1);
+    ix.scale = P.alloc<float>(d);
+    ix.seg = P.alloc<uint32_t>((size_t)d * sigma + 1);
+    const int64_t nnz = ix.doc_nnz;
+    uint32_t* kept = ix.kept;
+    int32_t* kdim = P.alloc<int32_t>(nnz);
+    float* kval = P.alloc<float>(nnz);
+    uint32_t* long_rows = P.alloc<uint32_t>(n > 0 ? n : 1);
+    uint32_t* n_long = P.alloc<uint32_t>(1);
+    SINDI_CUDA(cudaMemsetAsync(n_long, 0, 4, stream));
+    if (n > 0) {
+        prune_rows_kernel<<<grid_for(n, kPruneWarps, 152 * 32), kPruneWarps * 32, 0, stream>>>(
+            ix.indptr, ix.indices, ix.values, n, d, ix.alpha, kept, kdim, kval, long_rows, n_long, ix.err);
+        SINDI_CUDA(cudaGetLastError());
+    }
+    uint32_t nl = n > 0 ? read_u32(n_long, stream) : 0;
+    if (nl > 0) {
+        size_t sm = (size_t)kMaxRowNnz * sizeof(uint64_t);
+        SINDI_CUDA(cudaFuncSetAttribute(prune_long_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        prune_long_rows_kernel<<<nl, kLongBlock, sm, stream>>>(ix.indptr, ix.indices, ix.values, long_rows, d,
+                                                                ix.alpha, kept, kdim, kval, ix.err);
+        SINDI_CUDA(cudaGetLastError());
+    }
+    e = read_u32(ix.err, stream);
+    if (e) {
+        P.free(kdim); P.free(kval); P.free(long_rows); P.free(n_long);
+        set_last_error("malformed documents: " + doc_error_text(e));
+        return (e & kErrDocTooLong) && !(e & ~kErrDocTooLong) ? SINDI_ERR_UNSUPPORTED : SINDI_ERR_INVALID_DATA;
+    }
+    P.free(long_rows);
+    P.free(n_long);
+
+    // --- compact kept entries (document order)
+    int64_t* kept_off = P.alloc<int64_t>(n + 1);
+    exclusive_scan<uint32_t, int64_t>(kept, kept_off, n, P);
+    const int64_t Pn = read_i64(kept_off + n, stream);
+    if (Pn >= (int64_t)0xFFFFFFFFLL) {
+        P.free(kdim); P.free(kval); P.free(kept_off);
+        set_last_error("more than 2^32 - 1 kept entries");
+        return SINDI_ERR_UNSUPPORTED;
+    }
+    ix.postings = Pn;
+    ix.pid = P.alloc<uint16_t>(Pn);
+    ix.pval = P.alloc<uint8_t>((size_t)Pn * ix.value_bytes());
+    uint32_t* sdim = P.alloc<uint32_t>(Pn);
+    uint32_t* sdoc = P.alloc<uint32_t>(Pn);
+    uint32_t* sval = P.alloc<uint32_t>(Pn);
+    if (n > 0) {
+        compact_kernel<<<grid_for(n, 8, 152 * 32), 256, 0, stream>>>(ix.indptr, kept_off, kdim, kval, n, sdim, sdoc,
+                                                                     sval);
+        SINDI_CUDA(cudaGetLastError());
+    }
+    P.free(kdim);
+    P.free(kval);
+    P.free(kept_off);
+
+    // --- offsets of every list I_{j,w}
+    const int64_t S = (int64_t)d * sigma;
+    uint32_t* cnt = P.alloc<uint32_t>(S > 0 ? S : 1);
+    SINDI_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)(S > 0 ? S : 1), stream));
+    if (Pn > 0) {
+        list_count_kernel<<<grid_for(Pn, 256), 256, 0, stream>>>(sdim, sdoc, Pn, lambda, sigma, cnt);
+        SINDI_CUDA(cudaGetLastError());
+    }
+    exclusive_scan<uint32_t, uint32_t>(cnt, ix.seg, S, P);
+    P.free(cnt);
+
+    // --- stable sort by dim: (dim, doc) order
+    {
+        uint32_t* kb = P.alloc<uint32_t>(Pn);
+        uint32_t* db = P.alloc<uint32_t>(Pn);
+        uint32_t* vb = P.alloc<uint32_t>(Pn);
+        int bits = 0;
+        while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)d) bits++;
+        radix_sort_triples(sdim, sdoc, sval, kb, db, vb, Pn, bits, P);
+        P.free(kb); P.free(db); P.free(vb);
+    }
+
+    // --- values and window-local ids
+    if (ix.dtype == SINDI_F8E4M3) {
+        if (d > 0) {
+            list_scale_kernel<<<grid_for(d, 8, 152 * 32), 256, 0, stream>>>(ix.seg, sval, d, sigma, ix.scale);
+            SINDI_CUDA(cudaGetLastError());
+        }
+    } else if (d > 0) {
+        fill_u32_kernel<<<grid_for(d, 256), 256, 0, stream>>>(ix.scale, d, 1.0f);
+        SINDI_CUDA(cudaGetLastError());
+    }
+    if (Pn > 0) {
+        if (ix.dtype == SINDI_F32)
+            pack_kernel<SINDI_F32><<<grid_for(Pn, 256), 256, 0, stream>>>(sdim, sdoc, sval, Pn, lambda, ix.scale,
+                                                                          ix.pid, ix.pval);
+        else if (ix.dtype == SINDI_F16)
+            pack_kernel<SINDI_F16><<<grid_for(Pn, 256), 256, 0, stream>>>(sdim, sdoc, sval, Pn, lambda, ix.scale,
+                                                                          ix.pid, ix.pval);
+        else
+            pack_kernel<SINDI_F8E4M3><<<grid_for(Pn, 256), 256, 0, stream>>>(sdim, sdoc, sval, Pn, lambda,
+                                                                             ix.scale, ix.pid, ix.pval);
+        SINDI_CUDA(cudaGetLastError());
+    }
+    P.free(sdim);
+    P.free(sdoc);
+    P.free(sval);
+    SINDI_CUDA(cudaStreamSynchronize(stream));
+    return SINDI_OK;
+}
+
+}  // namespace sindi

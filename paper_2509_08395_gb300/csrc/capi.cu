@@ -1,0 +1,424 @@
+// The C ABI (include/sindi.h): argument checks, host/device staging, memory
+// pool, error reporting. The computation lives in build.cu and search.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "index.cuh"
+#include "primitives.cuh"
+
+namespace sindi {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// One pool per device, owned by the library, that keeps freed blocks for
+// reuse (release threshold = unlimited); big temporaries of a build are
+// returned with an explicit trim.
+cudaMemPool_t library_pool(int device) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(device);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool;
+    SINDI_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t thr = ~0ull;
+    SINDI_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    pools[device] = pool;
+    return pool;
+}
+
+enum class Where { Host, Device, Invalid };
+
+static Where where_is(const void* p) {
+    if (!p) return Where::Invalid;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return Where::Host;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? Where::Device : Where::Host;
+}
+
+static sindi_status from_cuda(const CudaError& e) {
+    set_last_error(std::string(cudaGetErrorString(e.code)) + " (" + e.where + ")");
+    if (e.code == cudaErrorMemoryAllocation) return SINDI_ERR_OOM;
+    return SINDI_ERR_CUDA;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) (void)cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) (void)cudaSetDevice(prev);
+    }
+};
+
+static void free_index_memory(IndexImpl& ix, cudaStream_t s) {
+    void* ptrs[] = {ix.indptr, ix.indices, ix.values, ix.seg, ix.pid, ix.pval, ix.scale, ix.kept, ix.err};
+    for (void* p : ptrs)
+        if (p) (void)cudaFreeAsync(p, s);
+    (void)cudaStreamSynchronize(s);
+    ix.indptr = nullptr;
+    ix.indices = nullptr;
+    ix.values = nullptr;
+    ix.seg = nullptr;
+    ix.pid = nullptr;
+    ix.pval = nullptr;
+    ix.scale = nullptr;
+    ix.kept = nullptr;
+    ix.err = nullptr;
+}
+
+static std::string query_error_text(uint32_t e) {
+    std::string m;
+    if (e & kErrQueryDim) m += "a query dim outside [0, dim); ";
+    if (e & kErrQueryValue) m += "a non-finite query value; ";
+    if (e & kErrQueryDup) m += "a dim repeated within a query; ";
+    if (e & kErrQueryTooLong) m += "a query with more than 2048 entries; ";
+    if (e & kErrCandOverflow) m += "candidate buffer overflow; ";
+    if (e & kErrTimeout) m += "a bounded device wait gave up; ";
+    return m;
+}
+
+static sindi_status status_of_error_word(uint32_t e) {
+    if (e == 0) return SINDI_OK;
+    set_last_error("device error word: " + query_error_text(e));
+    if (e & kErrTimeout) return SINDI_ERR_TIMEOUT;
+    return SINDI_ERR_INVALID_DATA;
+}
+
+}  // namespace sindi
+
+using namespace sindi;
+
+extern "C" {
+
+const char* sindi_last_error(void) { return g_last_error.c_str(); }
+
+const char* sindi_version(void) { return "sindi-gb300 0.1 (sm_103a)"; }
+
+sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const float* values, int64_t n_docs,
+                         int32_t dim, const sindi_build_params* params, void* stream, sindi_index** out) {
+    set_last_error("");
+    if (!out) {
+        set_last_error("out is NULL");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    sindi_build_params prm = params ? *params : sindi_build_params{0, SINDI_F32, 1.0};
+    if (n_docs < 0 || n_docs >= (int64_t)0xFFFFFFFFLL || dim <= 0 || !indptr) {
+        set_last_error("n_docs must be in [0, 2^32 - 1), dim > 0, indptr not NULL");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    if (!(prm.alpha > 0.0 && prm.alpha <= 1.0) || prm.window > kMaxWindow || prm.value_dtype < SINDI_F32 ||
+        prm.value_dtype > SINDI_F8E4M3) {
+        set_last_error("alpha must be in (0, 1], window in [0, 32768], value_dtype a sindi_dtype");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    if ((uint64_t)dim * (uint64_t)std::max<int64_t>(1, (n_docs + std::max<uint32_t>(prm.window, 1) - 1) /
+                                                          std::max<uint32_t>(prm.window, 1)) >= (1ull << 34)) {
+        set_last_error("dim * n_windows too large for the offset table");
+        return SINDI_ERR_UNSUPPORTED;
+    }
+    const Where w_ptr = where_is(indptr);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        set_last_error("no CUDA device");
+        return SINDI_ERR_CUDA;
+    }
+    sindi_index* h = new (std::nothrow) sindi_index;
+    if (!h) return SINDI_ERR_OOM;
+    IndexImpl& ix = h->impl;
+    try {
+        ix.device = dev;
+        ix.pool = library_pool(dev);
+        ix.n_docs = n_docs;
+        ix.dim = dim;
+        ix.lambda = prm.window ? prm.window : kDefaultWindow;
+        ix.sigma = (uint32_t)((n_docs + ix.lambda - 1) / ix.lambda);
+        ix.dtype = prm.value_dtype;
+        ix.alpha = prm.alpha;
+        Pool P{ix.pool, s};
+        ix.err = P.alloc<uint32_t>(1);
+        SINDI_CUDA(cudaMemsetAsync(ix.err, 0, 4, s));
+        ix.indptr = P.alloc<int64_t>(n_docs + 1);
+        SINDI_CUDA(cudaMemcpyAsync(ix.indptr, indptr, sizeof(int64_t) * (n_docs + 1),
+                                   w_ptr == Where::Device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        // indptr validity first: the number of entries comes from it
+        launch_validate_indptr(ix.indptr, n_docs, ix.err, s);
+        uint32_t e = 0;
+        int64_t nnz = 0;
+        SINDI_CUDA(cudaMemcpyAsync(&e, ix.err, 4, cudaMemcpyDeviceToHost, s));
+        SINDI_CUDA(cudaMemcpyAsync(&nnz, ix.indptr + n_docs, 8, cudaMemcpyDeviceToHost, s));
+        SINDI_CUDA(cudaStreamSynchronize(s));
+        if (e != 0 || nnz < 0) {
+            free_index_memory(ix, s);
+            delete h;
+            set_last_error("malformed documents: indptr[0] != 0 or decreasing");
+            return SINDI_ERR_INVALID_DATA;
+        }
+        if (nnz > 0 && (!indices || !values)) {
+            free_index_memory(ix, s);
+            delete h;
+            set_last_error("indices / values are NULL");
+            return SINDI_ERR_INVALID_ARG;
+        }
+        ix.doc_nnz = nnz;
+        ix.indices = P.alloc<int32_t>(nnz);
+        ix.values = P.alloc<float>(nnz);
+        if (nnz > 0) {
+            const bool dsrc = where_is(indices) == Where::Device;
+            SINDI_CUDA(cudaMemcpyAsync(ix.indices, indices, sizeof(int32_t) * nnz,
+                                       dsrc ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+            SINDI_CUDA(cudaMemcpyAsync(ix.values, values, sizeof(float) * nnz,
+                                       where_is(values) == Where::Device ? cudaMemcpyDeviceToDevice
+                                                                         : cudaMemcpyHostToDevice,
+                                       s));
+        }
+        sindi_status st = build_lists(ix, s);
+        SINDI_CUDA(cudaStreamSynchronize(s));
+        SINDI_CUDA(cudaMemPoolTrimTo(ix.pool, 0));
+        if (st != SINDI_OK) {
+            free_index_memory(ix, s);
+            delete h;
+            return st;
+        }
+    } catch (const CudaError& e) {
+        sindi_status st = from_cuda(e);
+        free_index_memory(ix, s);
+        delete h;
+        return st;
+    } catch (const std::bad_alloc&) {
+        free_index_memory(ix, s);
+        delete h;
+        set_last_error("host out of memory");
+        return SINDI_ERR_OOM;
+    }
+    *out = h;
+    return SINDI_OK;
+}
+
+sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
+                          const float* q_values, int64_t n_queries, const sindi_search_params* params,
+                          uint32_t* out_ids, float* out_scores, void* stream) {
+    set_last_error("");
+    if (!index || !params) {
+        set_last_error("index / params is NULL");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    const sindi_search_params prm = *params;
+    if (prm.k < 1 || prm.k > kMaxK || (prm.gamma != 0 && (prm.gamma < prm.k || prm.gamma > kMaxGamma)) ||
+        !(prm.beta > 0.0 && prm.beta <= 1.0) || prm.mode > SINDI_MODE_BATCHED || prm.reserved != 0) {
+        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; reserved 0");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    if (prm.beta < 1.0) {
+        set_last_error("query pruning (beta < 1) is not in this build");
+        return SINDI_ERR_UNSUPPORTED;
+    }
+    if (n_queries < 0 || n_queries > (int64_t)1 << 31) {
+        set_last_error("n_queries out of range");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    if (n_queries == 0) return SINDI_OK;
+    if (!q_indptr || !out_ids || !out_scores) {
+        set_last_error("NULL query or output pointer");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    const IndexImpl& ix = index->impl;
+    DeviceGuard dg(ix.device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool in_dev = where_is(q_indptr) == Where::Device;
+    const bool out_dev = where_is(out_ids) == Where::Device;
+    if (in_dev && out_dev) {
+        if (!q_indices || !q_values) {
+            set_last_error("NULL query arrays");
+            return SINDI_ERR_INVALID_ARG;
+        }
+        try {
+            return search_impl(ix, q_indptr, q_indices, q_values, n_queries, prm, out_ids, out_scores, s);
+        } catch (const CudaError& e) {
+            return from_cuda(e);
+        }
+    }
+    // staged path: copy host inputs in, run, copy results out, synchronise
+    Pool P{ix.pool, s};
+    int64_t* d_ip = nullptr;
+    int32_t* d_ix = nullptr;
+    float* d_v = nullptr;
+    uint32_t* d_ids = nullptr;
+    float* d_sc = nullptr;
+    sindi_status st = SINDI_OK;
+    try {
+        const int64_t* ip = q_indptr;
+        const int32_t* qi = q_indices;
+        const float* qv = q_values;
+        if (!in_dev) {
+            const int64_t nnz = q_indptr[n_queries];
+            if (q_indptr[0] != 0 || nnz < 0 || (nnz > 0 && (!q_indices || !q_values))) {
+                set_last_error("malformed query indptr");
+                return SINDI_ERR_INVALID_ARG;
+            }
+            for (int64_t r = 0; r < n_queries; r++)
+                if (q_indptr[r + 1] < q_indptr[r]) {
+                    set_last_error("query indptr decreases");
+                    return SINDI_ERR_INVALID_ARG;
+                }
+            d_ip = P.alloc<int64_t>(n_queries + 1);
+            d_ix = P.alloc<int32_t>(nnz);
+            d_v = P.alloc<float>(nnz);
+            SINDI_CUDA(cudaMemcpyAsync(d_ip, q_indptr, 8 * (n_queries + 1), cudaMemcpyHostToDevice, s));
+            if (nnz > 0) {
+                SINDI_CUDA(cudaMemcpyAsync(d_ix, q_indices, 4 * nnz, cudaMemcpyHostToDevice, s));
+                SINDI_CUDA(cudaMemcpyAsync(d_v, q_values, 4 * nnz, cudaMemcpyHostToDevice, s));
+            }
+            ip = d_ip;
+            qi = d_ix;
+            qv = d_v;
+        }
+        uint32_t* oi = out_ids;
+        float* os = out_scores;
+        const size_t nout = (size_t)n_queries * prm.k;
+        if (!out_dev) {
+            d_ids = P.alloc<uint32_t>(nout);
+            d_sc = P.alloc<float>(nout);
+            oi = d_ids;
+            os = d_sc;
+        }
+        st = search_impl(ix, ip, qi, qv, n_queries, prm, oi, os, s);
+        if (st == SINDI_OK && !out_dev) {
+            SINDI_CUDA(cudaMemcpyAsync(out_ids, d_ids, 4 * nout, cudaMemcpyDeviceToHost, s));
+            SINDI_CUDA(cudaMemcpyAsync(out_scores, d_sc, 4 * nout, cudaMemcpyDeviceToHost, s));
+        }
+        P.free(d_ip);
+        P.free(d_ix);
+        P.free(d_v);
+        P.free(d_ids);
+        P.free(d_sc);
+        SINDI_CUDA(cudaStreamSynchronize(s));
+        if (st == SINDI_OK) {
+            uint32_t e = 0;
+            SINDI_CUDA(cudaMemcpy(&e, ix.err, 4, cudaMemcpyDeviceToHost));
+            if (e) {
+                SINDI_CUDA(cudaMemset(ix.err, 0, 4));
+                st = status_of_error_word(e);
+            }
+        }
+    } catch (const CudaError& e) {
+        return from_cuda(e);
+    }
+    return st;
+}
+
+sindi_status sindi_check(const sindi_index* index, void* stream) {
+    set_last_error("");
+    if (!index) return SINDI_ERR_INVALID_ARG;
+    const IndexImpl& ix = index->impl;
+    DeviceGuard dg(ix.device);
+    try {
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        SINDI_CUDA(cudaStreamSynchronize(s));
+        uint32_t e = 0;
+        SINDI_CUDA(cudaMemcpy(&e, ix.err, 4, cudaMemcpyDeviceToHost));
+        if (e) SINDI_CUDA(cudaMemset(ix.err, 0, 4));
+        return status_of_error_word(e);
+    } catch (const CudaError& e) {
+        return from_cuda(e);
+    }
+}
+
+sindi_status sindi_index_info(const sindi_index* index, sindi_index_info_t* out) {
+    if (!index || !out) return SINDI_ERR_INVALID_ARG;
+    const IndexImpl& ix = index->impl;
+    out->n_docs = ix.n_docs;
+    out->dim = ix.dim;
+    out->value_dtype = ix.dtype;
+    out->window = ix.lambda;
+    out->n_windows = ix.sigma;
+    out->postings = ix.postings;
+    out->doc_nnz = ix.doc_nnz;
+    out->index_bytes = (int64_t)(((int64_t)ix.dim * ix.sigma + 1) * 4 + ix.postings * (2 + (int64_t)ix.value_bytes()) +
+                                 (int64_t)ix.dim * 4);
+    out->doc_bytes = (ix.n_docs + 1) * 8 + ix.doc_nnz * 8;
+    out->alpha = ix.alpha;
+    return SINDI_OK;
+}
+
+sindi_status sindi_index_export(const sindi_index* index, uint32_t* seg, uint16_t* ids, void* vals, float* scale,
+                                uint32_t* kept) {
+    set_last_error("");
+    if (!index) return SINDI_ERR_INVALID_ARG;
+    const IndexImpl& ix = index->impl;
+    DeviceGuard dg(ix.device);
+    try {
+        if (seg) SINDI_CUDA(cudaMemcpy(seg, ix.seg, 4 * ((size_t)ix.dim * ix.sigma + 1), cudaMemcpyDeviceToHost));
+        if (ids && ix.postings) SINDI_CUDA(cudaMemcpy(ids, ix.pid, 2 * (size_t)ix.postings, cudaMemcpyDeviceToHost));
+        if (vals && ix.postings)
+            SINDI_CUDA(cudaMemcpy(vals, ix.pval, ix.value_bytes() * (size_t)ix.postings, cudaMemcpyDeviceToHost));
+        if (scale) SINDI_CUDA(cudaMemcpy(scale, ix.scale, 4 * (size_t)ix.dim, cudaMemcpyDeviceToHost));
+        if (kept && ix.n_docs) SINDI_CUDA(cudaMemcpy(kept, ix.kept, 4 * (size_t)ix.n_docs, cudaMemcpyDeviceToHost));
+    } catch (const CudaError& e) {
+        return from_cuda(e);
+    }
+    return SINDI_OK;
+}
+
+sindi_status sindi_set_timing(const sindi_index* index, int enable) {
+    if (!index) return SINDI_ERR_INVALID_ARG;
+    index->impl.timing.store(enable ? 1 : 0);
+    return SINDI_OK;
+}
+
+sindi_status sindi_get_stats(const sindi_index* index, sindi_stats_t* out) {
+    if (!index || !out) return SINDI_ERR_INVALID_ARG;
+    const IndexImpl& ix = index->impl;
+    out->launches = ix.launches.load();
+    out->scan_launches = ix.scan_launches.load();
+    out->queries = ix.queries.load();
+    out->scan_timed = ix.scan_timed.load();
+    std::lock_guard<std::mutex> lk(ix.tmu);
+    out->scan_ms = ix.scan_ms;
+    return SINDI_OK;
+}
+
+sindi_status sindi_reset_stats(const sindi_index* index) {
+    if (!index) return SINDI_ERR_INVALID_ARG;
+    const IndexImpl& ix = index->impl;
+    ix.launches = 0;
+    ix.scan_launches = 0;
+    ix.queries = 0;
+    ix.scan_timed = 0;
+    std::lock_guard<std::mutex> lk(ix.tmu);
+    ix.scan_ms = 0.0;
+    return SINDI_OK;
+}
+
+void sindi_index_free(sindi_index* index) {
+    if (!index) return;
+    {
+        DeviceGuard dg(index->impl.device);
+        (void)cudaDeviceSynchronize();
+        free_index_memory(index->impl, nullptr);
+    }
+    delete index;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// The library-side index object behind the opaque sindi_index handle.
+#pragma once
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sindi {
+
+struct IndexImpl {
+    int device = 0;
+    int64_t n_docs = 0;
+    int32_t dim = 0;
+    uint32_t lambda = 0;
+    uint32_t sigma = 0;
+    int32_t dtype = SINDI_F32;
+    double alpha = 1.0;
+    int64_t doc_nnz = 0;
+    int64_t postings = 0;
+    cudaMemPool_t pool = nullptr;
+
+    // unpruned documents (Algorithm 3 keeps D for reordering)
+    int64_t* indptr = nullptr;
+    int32_t* indices = nullptr;
+    float* values = nullptr;
+    // lists I_{j,w}
+    uint32_t* seg = nullptr;     // [dim * sigma + 1]
+    uint16_t* pid = nullptr;     // [postings]
+    void* pval = nullptr;        // [postings]
+    float* scale = nullptr;      // [dim]
+    uint32_t* kept = nullptr;    // [n_docs]
+    uint32_t* err = nullptr;     // device error word
+
+    // counters
+    mutable std::atomic<uint64_t> launches{0}, scan_launches{0}, queries{0}, scan_timed{0};
+    mutable std::mutex tmu;
+    mutable double scan_ms = 0.0;
+    mutable std::atomic<int> timing{0};
+
+    DevIndex dev() const {
+        DevIndex d;
+        d.n_docs = n_docs;
+        d.dim = dim;
+        d.lambda = lambda;
+        d.sigma = sigma;
+        d.dtype = dtype;
+        d.seg = seg;
+        d.pid = pid;
+        d.pval = pval;
+        d.scale = scale;
+        d.indptr = indptr;
+        d.indices = indices;
+        d.values = values;
+        d.err = err;
+        return d;
+    }
+
+    size_t value_bytes() const { return dtype == SINDI_F32 ? 4 : (dtype == SINDI_F16 ? 2 : 1); }
+};
+
+sindi_status build_lists(IndexImpl& ix, cudaStream_t stream);
+
+// Sets kErrDocIndptr in *err unless indptr[0] == 0 and indptr never decreases.
+void launch_validate_indptr(const int64_t* indptr, int64_t n, uint32_t* err, cudaStream_t stream);
+
+// Search entry used by the C API (search.cu).
+sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
+                         const float* q_values, int64_t n_queries, const sindi_search_params& prm,
+                         uint32_t* out_ids, float* out_scores, cudaStream_t stream);
+
+}  // namespace sindi
+
+struct sindi_index {
+    sindi::IndexImpl impl;
+};

@@ -1,0 +1,249 @@
+"""Python binding of the C ABI in include/sindi.h (ctypes; argument marshalling only).
+
+Functions keep the C names (``sindi_build``, ``sindi_search``, ...) and take
+torch tensors or numpy arrays; every step of the search runs in the CUDA
+kernels of ``lib/libsindi.so``. There is no CPU fallback: if the library is
+missing, loading raises.
+
+``Index`` is a small convenience wrapper over the same calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsindi.so")
+
+SINDI_OK, SINDI_ERR_INVALID_ARG, SINDI_ERR_INVALID_DATA, SINDI_ERR_OOM = 0, 1, 2, 3
+SINDI_ERR_CUDA, SINDI_ERR_TIMEOUT, SINDI_ERR_UNSUPPORTED = 4, 5, 6
+SINDI_F32, SINDI_F16, SINDI_F8E4M3 = 0, 1, 2
+SINDI_MODE_PLAIN, SINDI_MODE_BATCHED = 0, 1
+DTYPES = {"f32": SINDI_F32, "f16": SINDI_F16, "f8": SINDI_F8E4M3, "e4m3": SINDI_F8E4M3}
+MODES = {"plain": SINDI_MODE_PLAIN, "batched": SINDI_MODE_BATCHED}
+STATUS_NAMES = {0: "SINDI_OK", 1: "SINDI_ERR_INVALID_ARG", 2: "SINDI_ERR_INVALID_DATA", 3: "SINDI_ERR_OOM",
+                4: "SINDI_ERR_CUDA", 5: "SINDI_ERR_TIMEOUT", 6: "SINDI_ERR_UNSUPPORTED"}
+
+
+class SindiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sindi_build_params(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_uint32), ("value_dtype", ctypes.c_int32), ("alpha", ctypes.c_double)]
+
+
+class sindi_search_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("gamma", ctypes.c_uint32), ("beta", ctypes.c_double),
+                ("mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class sindi_index_info_t(ctypes.Structure):
+    _fields_ = [("n_docs", ctypes.c_int64), ("dim", ctypes.c_int32), ("value_dtype", ctypes.c_int32),
+                ("window", ctypes.c_uint32), ("n_windows", ctypes.c_uint32), ("postings", ctypes.c_int64),
+                ("doc_nnz", ctypes.c_int64), ("index_bytes", ctypes.c_int64), ("doc_bytes", ctypes.c_int64),
+                ("alpha", ctypes.c_double)]
+
+
+class sindi_stats_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("scan_launches", ctypes.c_uint64), ("queries", ctypes.c_uint64),
+                ("scan_ms", ctypes.c_double), ("scan_timed", ctypes.c_uint64)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "sindi_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                   ctypes.POINTER(sindi_build_params), ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    "sindi_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int64, ctypes.POINTER(sindi_search_params), ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "sindi_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sindi_index_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_index_info_t)]),
+    "sindi_index_export": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "sindi_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "sindi_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_stats_t)]),
+    "sindi_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
+    "sindi_index_free": (None, [ctypes.c_void_p]),
+    "sindi_last_error": (ctypes.c_char_p, []),
+    "sindi_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load lib/libsindi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"native library missing: {path} (build it with __graft_entry__.build() or "
+                           "python -m paper_2509_08395_gb300.build_native)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != SINDI_OK:
+        raise SindiError(status, f"{what}: {load().sindi_last_error().decode(errors='replace')}")
+
+
+def _ptr(a, dtype):
+    """Data pointer of a contiguous torch tensor or numpy array of the given numpy dtype."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous:
+            raise TypeError(f"expected a contiguous {np.dtype(dtype).name} array")
+        return a.ctypes.data
+    import torch
+    tmap = {np.int64: torch.int64, np.int32: torch.int32, np.float32: torch.float32,
+            np.uint32: torch.uint32 if hasattr(torch, "uint32") else torch.int32}
+    if a.dtype != tmap[dtype] and not (dtype == np.uint32 and a.dtype == torch.int32):
+        raise TypeError(f"expected a {tmap[dtype]} tensor, got {a.dtype}")
+    if not a.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    return a.data_ptr()
+
+
+def _stream(stream, *tensors):
+    if stream is not None:
+        return stream
+    for t in tensors:
+        if t is not None and not isinstance(t, np.ndarray) and t.is_cuda:
+            import torch
+            return torch.cuda.current_stream(t.device).cuda_stream
+    return None
+
+
+# ---- the C entry points, same names -------------------------------------------------
+def sindi_build(indptr, indices, values, n_docs: int, dim: int, window: int = 0, alpha: float = 1.0,
+                value_dtype: str = "f32", stream=None) -> int:
+    """Algorithm 3 on the device; returns the opaque index handle (int)."""
+    lib = load()
+    prm = sindi_build_params(window=int(window), value_dtype=DTYPES[value_dtype], alpha=float(alpha))
+    out = ctypes.c_void_p()
+    st = lib.sindi_build(_ptr(indptr, np.int64), _ptr(indices, np.int32), _ptr(values, np.float32), int(n_docs),
+                         int(dim), ctypes.byref(prm), _stream(stream, indptr), ctypes.byref(out))
+    _check(st, "sindi_build")
+    return out.value
+
+
+def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
+                 gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None) -> None:
+    """Algorithm 4 for every query row; writes out_ids (uint32/int32) and out_scores (float32), [n_queries, k]."""
+    lib = load()
+    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], reserved=0)
+    st = lib.sindi_search(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
+                          _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm), _ptr(out_ids, np.uint32),
+                          _ptr(out_scores, np.float32), _stream(stream, q_indptr, out_ids))
+    _check(st, "sindi_search")
+
+
+def sindi_check(index: int, stream=None) -> None:
+    _check(load().sindi_check(ctypes.c_void_p(index), stream), "sindi_check")
+
+
+def sindi_index_info(index: int) -> dict:
+    info = sindi_index_info_t()
+    _check(load().sindi_index_info(ctypes.c_void_p(index), ctypes.byref(info)), "sindi_index_info")
+    return {f: getattr(info, f) for f, _ in sindi_index_info_t._fields_}
+
+
+def sindi_index_export(index: int) -> dict:
+    """Copy the lists to host numpy arrays: seg, ids, vals, scale, kept."""
+    info = sindi_index_info(index)
+    S = info["dim"] * info["n_windows"]
+    P = info["postings"]
+    vdt = {SINDI_F32: np.float32, SINDI_F16: np.uint16, SINDI_F8E4M3: np.uint8}[info["value_dtype"]]
+    seg = np.empty(S + 1, np.uint32)
+    ids = np.empty(max(P, 1), np.uint16)
+    vals = np.empty(max(P, 1), vdt)
+    scale = np.empty(info["dim"], np.float32)
+    kept = np.empty(max(info["n_docs"], 1), np.uint32)
+    _check(load().sindi_index_export(ctypes.c_void_p(index), seg.ctypes.data, ids.ctypes.data, vals.ctypes.data,
+                                     scale.ctypes.data, kept.ctypes.data), "sindi_index_export")
+    return {"seg": seg, "ids": ids[:P], "vals": vals[:P], "scale": scale, "kept": kept[: info["n_docs"]],
+            "info": info}
+
+
+def sindi_set_timing(index: int, enable: bool) -> None:
+    _check(load().sindi_set_timing(ctypes.c_void_p(index), 1 if enable else 0), "sindi_set_timing")
+
+
+def sindi_get_stats(index: int) -> dict:
+    s = sindi_stats_t()
+    _check(load().sindi_get_stats(ctypes.c_void_p(index), ctypes.byref(s)), "sindi_get_stats")
+    return {f: getattr(s, f) for f, _ in sindi_stats_t._fields_}
+
+
+def sindi_reset_stats(index: int) -> None:
+    _check(load().sindi_reset_stats(ctypes.c_void_p(index)), "sindi_reset_stats")
+
+
+def sindi_index_free(index: int) -> None:
+    if index:
+        load().sindi_index_free(ctypes.c_void_p(index))
+
+
+def sindi_version() -> str:
+    return load().sindi_version().decode()
+
+
+# ---- convenience wrapper ------------------------------------------------------------
+class Index:
+    """A device-resident SINDI index (owns the C handle)."""
+
+    def __init__(self, indptr, indices, values, dim: int, window: int = 0, alpha: float = 1.0,
+                 value_dtype: str = "f32", stream=None):
+        n_docs = (indptr.shape[0] if hasattr(indptr, "shape") else len(indptr)) - 1
+        self.handle = sindi_build(indptr, indices, values, n_docs, dim, window, alpha, value_dtype, stream)
+        self.info = sindi_index_info(self.handle)
+
+    def search(self, q_indptr, q_indices, q_values, k: int, gamma: int = 0, beta: float = 1.0,
+               mode: str = "plain", out=None, stream=None):
+        """Returns (ids, scores) of shape [n_queries, k]; device tensors for device queries."""
+        n_q = (q_indptr.shape[0] if hasattr(q_indptr, "shape") else len(q_indptr)) - 1
+        if out is None:
+            if isinstance(q_indptr, np.ndarray):
+                out = (np.empty((n_q, k), np.uint32), np.empty((n_q, k), np.float32))
+            else:
+                import torch
+                dev = q_indptr.device
+                out = (torch.empty((n_q, k), dtype=torch.int32, device=dev),
+                       torch.empty((n_q, k), dtype=torch.float32, device=dev))
+        sindi_search(self.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma, beta, mode, stream)
+        return out
+
+    def check(self, stream=None):
+        sindi_check(self.handle, stream)
+
+    def export(self) -> dict:
+        return sindi_index_export(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sindi_index_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

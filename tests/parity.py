@@ -1,0 +1,103 @@
+"""Comparison rules between the GPU results and the FP64 oracle.
+
+Tolerance: scores within REL_TOL = 1e-5 relative (FP32 accumulation of at
+most a few hundred positive products stays below that). IDs must be
+bit-identical wherever the oracle's scores separate them by more than the
+tolerance; inside a group of near-equal oracle scores any order is valid,
+and the lower id wins only among exact ties, which FP32 cannot guarantee to
+reproduce.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+REL_TOL = 1e-5
+PAD_ID = 0xFFFFFFFF
+
+
+def _close(a, b, tol=REL_TOL):
+    return abs(float(a) - float(b)) <= tol * max(abs(float(a)), abs(float(b)), 1e-30)
+
+
+def tie_groups(scores, tol=REL_TOL):
+    """Split a best-first score list into runs whose neighbours are within tol."""
+    groups, start = [], 0
+    for i in range(1, len(scores) + 1):
+        if i == len(scores) or not _close(scores[i - 1], scores[i], tol):
+            groups.append((start, i))
+            start = i
+    return groups
+
+
+def check_ranked(gids, gsc, oids, osc, k, n_docs, tol=REL_TOL, what=""):
+    """GPU top-k (gids, gsc) against the oracle's best-first list (oids, osc).
+
+    The oracle list must extend past rank k far enough to close the tie group
+    that straddles rank k (callers ask for k + 64 results)."""
+    n = min(k, n_docs)
+    gids = np.asarray(gids).astype(np.int64) & 0xFFFFFFFF
+    gsc = np.asarray(gsc, np.float64)
+    assert np.all(gids[n:] == PAD_ID) and np.all(np.isneginf(gsc[n:])), f"{what}: padding"
+    for r in range(n):
+        assert _close(gsc[r], osc[r], tol), f"{what}: score at rank {r}: gpu {gsc[r]!r} oracle {osc[r]!r}"
+    groups = tie_groups(osc, tol)
+    for a, b in groups:
+        if a >= n:
+            break
+        want = set(int(x) for x in oids[a:b])
+        got = set(int(x) for x in gids[a:min(b, n)])
+        if b <= n:
+            assert got == want, f"{what}: ranks [{a},{b}) gpu {sorted(got)} oracle {sorted(want)}"
+        else:
+            assert b < len(osc) or len(osc) >= n_docs, f"{what}: oracle list too short to close the last tie group"
+            assert got <= want, f"{what}: boundary ranks [{a},{n}) gpu {sorted(got)} not in oracle group"
+
+
+def check_reranked(gids, gsc, D, Q, r, I, k, gamma, tol=REL_TOL, what=""):
+    """GPU results of Algorithm 4 (pruned coarse stage + exact reorder of gamma candidates).
+
+    The GPU's coarse scores are FP32, so its candidate set may differ from the
+    oracle's only by documents whose coarse score is within tol of the
+    oracle's gamma-th coarse score ("ambiguous"). The GPU answer must be the
+    exact top-k of some candidate set C with robust <= C <= robust + ambiguous.
+    Returns the number of ambiguous documents that touched the answer."""
+    n = min(k, D.n)
+    g = min(gamma, D.n)
+    cids, csc = I.search(Q, r, k=min(g + 256, D.n), gamma=0)
+    s_g = csc[g - 1]
+    amb = set(int(c) for c, s in zip(cids, csc) if _close(s, s_g, tol))
+    robust = set(int(c) for c in cids[:g]) - amb
+    if len(cids) > g and _close(csc[-1], s_g, tol) and len(cids) < D.n:
+        raise AssertionError(f"{what}: coarse tie group at rank gamma longer than the probe")
+    gids = np.asarray(gids).astype(np.int64) & 0xFFFFFFFF
+    gsc = np.asarray(gsc, np.float64)
+    assert np.all(gids[n:] == PAD_ID), f"{what}: padding"
+    exact = {}
+
+    def ex(i):
+        if i not in exact:
+            exact[i] = oracle.inner_product(D, i, Q, r)
+        return exact[i]
+
+    got = [int(x) for x in gids[:n]]
+    assert len(set(got)) == n, f"{what}: duplicate ids {got}"
+    for rank, i in enumerate(got):
+        assert i in robust or i in amb, f"{what}: id {i} at rank {rank} was not a coarse candidate"
+        assert _close(gsc[rank], ex(i), tol), f"{what}: score of {i}: gpu {gsc[rank]} exact {ex(i)}"
+        if rank:
+            assert ex(got[rank - 1]) >= ex(i) * (1 - tol) - 1e-30, f"{what}: order at rank {rank}"
+    kth = ex(got[-1])
+    gotset = set(got)
+    for c in robust:
+        if ex(c) > kth * (1 + tol) + 1e-30:
+            assert c in gotset, f"{what}: robust candidate {c} (exact {ex(c)}) beats the k-th {kth} but is missing"
+    touched = len(amb & gotset)
+    oi, osc = I.search(Q, r, k=k, gamma=gamma)
+    if not (amb & (gotset | set(int(x) for x in oi))):
+        # no ambiguity reached the answer: the tie-group rule against the oracle itself
+        full = sorted(((ex(c) if c in exact else oracle.inner_product(D, c, Q, r), c) for c in
+                       set(int(x) for x in cids[:g])), key=lambda t: (-t[0], t[1]))
+        check_ranked(gids, gsc, np.array([c for _, c in full]), np.array([s for s, _ in full]), k, D.n, tol, what)
+    return touched

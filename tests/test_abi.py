@@ -1,0 +1,59 @@
+"""The C ABI library: it loads without a GPU and exports every function include/*.h declares."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(sindi_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_08395_gb300 import build_native
+
+    path = build_native.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("sindi_build", "sindi_search", "sindi_check", "sindi_index_info", "sindi_index_free",
+              "sindi_last_error", "sindi_index_export"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_2509_08395_gb300 import sindi
+
+    assert _declared() <= set(sindi._SIGS)
+
+
+def test_calls_without_device_fail_cleanly(lib):
+    """No compute: argument checks return INVALID_ARG before touching a device."""
+    from paper_2509_08395_gb300 import sindi
+
+    L = sindi.load()
+    out = ctypes.c_void_p()
+    assert L.sindi_build(None, None, None, 10, 4, None, None, ctypes.byref(out)) == sindi.SINDI_ERR_INVALID_ARG
+    prm = sindi.sindi_search_params(k=0, gamma=0, beta=1.0, mode=0, reserved=0)
+    assert L.sindi_search(None, None, None, None, 1, ctypes.byref(prm), None, None, None) == \
+        sindi.SINDI_ERR_INVALID_ARG
+    assert b"NULL" in L.sindi_last_error()
+    assert L.sindi_version().startswith(b"sindi-gb300")

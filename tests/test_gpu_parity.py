@@ -1,0 +1,262 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI (needs a GB300)."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from parity import REL_TOL, check_ranked, check_reranked
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU machines, never run there
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2509_08395_gb300 as sindi  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def run_search(idx, qp, qx, qv, k, gamma=0, mode="plain", host=False):
+    if host:
+        ids, sc = idx.search(qp, qx, qv, k=k, gamma=gamma, mode=mode)
+        return ids.astype(np.int64), sc
+    ids, sc = idx.search(dev(qp), dev(qx), dev(qv), k=k, gamma=gamma, mode=mode)
+    idx.check()
+    return ids.cpu().numpy().view(np.uint32).astype(np.int64), sc.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def exact10k():
+    w = datagen.WORKLOADS["exact-10k"]
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    return w, (ip, ix, v), (qp, qx, qv), oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_exact_10k_top10_equals_brute_force(exact10k, mode):
+    """10k docs x 1,024 dims, no pruning, window 4,096: top-10 ids are the FP64 brute-force ids."""
+    w, (ip, ix, v), (qp, qx, qv), D, Q = exact10k
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=w.window, alpha=1.0) as idx:
+        assert idx.info["n_windows"] == 3
+        ids, sc = run_search(idx, qp, qx, qv, k=w.k, gamma=0, mode=mode)
+    for r in range(Q.n):
+        oi, os_ = oracle.brute_force(D, Q, r, w.k + 64)
+        check_ranked(ids[r], sc[r], oi, os_, w.k, D.n, what=f"query {r}")
+
+
+def _dequant(vals, dtype, scale, seg, sigma, dim):
+    if dtype == "f32":
+        return vals.astype(np.float64)
+    if dtype == "f16":
+        return vals.view(np.float16).astype(np.float64)
+    codes = torch.from_numpy(vals.copy()).view(torch.float8_e4m3fn).float().numpy()
+    out = np.empty(len(vals), np.float64)
+    for j in range(dim):
+        lo, hi = seg[j * sigma], seg[(j + 1) * sigma]
+        out[lo:hi] = (codes[lo:hi] * scale[j]).astype(np.float32)
+    return out
+
+
+@pytest.mark.parametrize("window,alpha,dtype", [(64, 1.0, "f32"), (300, 0.5, "f32"), (4096, 0.3, "f32"),
+                                                (128, 0.7, "f16"), (256, 0.5, "f8"), (1, 0.6, "f32")])
+def test_device_index_equals_oracle_lists(window, alpha, dtype):
+    """The device build (alpha-mass, (dim, doc) sort, windows, packing) gives the oracle's lists bit for bit."""
+    n = 700 if window > 1 else 90
+    ip, ix, v = datagen.random_csr(n, 97, 14.0, seed=50 + window, zipf_s=1.05, val_sigma=1.2)
+    # shuffle dims inside rows (unsorted input) and plant explicit zeros
+    rng = np.random.default_rng(window)
+    for i in range(0, n, 7):
+        a, b = ip[i], ip[i + 1]
+        p = rng.permutation(b - a)
+        ix[a:b], v[a:b] = ix[a:b][p], v[a:b][p]
+    v[::37] = 0.0
+    D = oracle.Dataset(ip, ix, v, 97)
+    I = oracle.Index(D, window=window, alpha=alpha, dtype=dtype)
+    seg, pid, pval, scale, kept = I.export()
+    with sindi.Index(dev(ip), dev(ix), dev(v), 97, window=window, alpha=alpha, value_dtype=dtype) as idx:
+        ex = idx.export()
+    assert ex["info"]["n_windows"] == I.sigma and ex["info"]["postings"] == I.postings
+    np.testing.assert_array_equal(ex["seg"].astype(np.int64), seg)
+    np.testing.assert_array_equal(ex["kept"].astype(np.int64), kept)
+    np.testing.assert_array_equal(ex["ids"].astype(np.int64), pid % window)
+    if dtype == "f8":
+        np.testing.assert_array_equal(ex["scale"], scale)
+    got = _dequant(ex["vals"], dtype, ex["scale"], ex["seg"], I.sigma, 97)
+    np.testing.assert_array_equal(got, pval)
+
+
+def test_device_index_host_and_device_inputs_agree():
+    ip, ix, v = datagen.random_csr(500, 64, 10.0, seed=77)
+    with sindi.Index(ip, ix, v, 64, window=100, alpha=0.5) as a, \
+            sindi.Index(dev(ip), dev(ix), dev(v), 64, window=100, alpha=0.5) as b:
+        ea, eb = a.export(), b.export()
+    for key in ("seg", "ids", "vals", "kept"):
+        np.testing.assert_array_equal(ea[key], eb[key])
+
+
+@pytest.fixture(scope="module")
+def pruned_small():
+    w = datagen.WORKLOADS["pruned-1m"].scaled(n_docs=40_000, n_queries=40)
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    return w, (ip, ix, v), (qp, qx, qv), oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+
+
+@pytest.mark.parametrize("window,mode", [(2048, "plain"), (4096, "batched"), (8192, "plain")])
+def test_pruned_coarse_topk_parity(pruned_small, window, mode):
+    """Coarse stage alone (gamma = 0): FP32 window accumulation vs the oracle's FP64 Algorithm 2."""
+    w, (ip, ix, v), (qp, qx, qv), D, Q = pruned_small
+    I = oracle.Index(D, window=window, alpha=0.5)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=window, alpha=0.5) as idx:
+        ids, sc = run_search(idx, qp, qx, qv, k=100, gamma=0, mode=mode)
+    for r in range(Q.n):
+        oi, os_ = I.search(Q, r, k=164, gamma=0)
+        check_ranked(ids[r], sc[r], oi, os_, 100, D.n, what=f"query {r}")
+
+
+@pytest.mark.parametrize("window,gamma,k,mode", [(2048, 200, 10, "plain"), (8192, 500, 50, "plain"),
+                                                 (4096, 500, 50, "batched"), (1024, 1000, 100, "batched")])
+def test_pruned_rerank_parity(pruned_small, window, gamma, k, mode):
+    """Algorithm 4: alpha = 0.5 coarse candidates, exact FP32 reorder against full vectors."""
+    w, (ip, ix, v), (qp, qx, qv), D, Q = pruned_small
+    I = oracle.Index(D, window=window, alpha=0.5)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=window, alpha=0.5) as idx:
+        ids, sc = run_search(idx, qp, qx, qv, k=k, gamma=gamma, mode=mode)
+    touched = 0
+    for r in range(Q.n):
+        touched += check_reranked(ids[r], sc[r], D, Q, r, I, k, gamma, what=f"query {r}")
+    assert touched <= 2
+
+
+@pytest.mark.parametrize("dtype", ["f16", "f8"])
+def test_reduced_precision_coarse_parity(pruned_small, dtype):
+    """FP16 / E4M3 postings: GPU coarse scores vs the oracle on the same dequantised values."""
+    w, (ip, ix, v), (qp, qx, qv), D, Q = pruned_small
+    I = oracle.Index(D, window=4096, alpha=0.5, dtype=dtype)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=4096, alpha=0.5, value_dtype=dtype) as idx:
+        ids, sc = run_search(idx, qp, qx, qv, k=50, gamma=0)
+        rids, rsc = run_search(idx, qp, qx, qv, k=10, gamma=500)
+    I32 = oracle.Index(D, window=4096, alpha=0.5)
+    for r in range(Q.n):
+        oi, os_ = I.search(Q, r, k=114, gamma=0)
+        check_ranked(ids[r], sc[r], oi, os_, 50, D.n, what=f"{dtype} query {r}")
+        for rank in range(10):
+            exact = oracle.inner_product(D, int(rids[r, rank]), Q, r)
+            assert abs(rsc[r, rank] - exact) <= REL_TOL * abs(exact)
+        fi, _ = I32.search(Q, r, k=10, gamma=500)
+        assert len(set(fi.tolist()) & set(rids[r].tolist())) >= 9
+
+
+def _csr(rows, dim):
+    ip, ix, v = [0], [], []
+    for row in rows:
+        for j, x in row:
+            ix.append(j)
+            v.append(x)
+        ip.append(len(ix))
+    return np.array(ip, np.int64), np.array(ix, np.int32), np.array(v, np.float32)
+
+
+def test_edge_cases_small():
+    """N < k, N < lambda, a ragged last window, empty docs, empty queries, queries with no hits, exact ties."""
+    docs = [[(1, 2.0)], [(1, 1.0)], [], [(1, 2.0)], [(3, 5.0)], [(1, 2.0), (2, 1.0)], [(4, 1.0)]]
+    ip, ix, v = _csr(docs, 8)
+    qs = [[(1, 1.0)], [(6, 1.0)], [], [(1, 1.0), (3, 1.0), (2, 2.0)]]
+    qp, qx, qv = _csr(qs, 8)
+    D, Q = oracle.Dataset(ip, ix, v, 8), oracle.Dataset(qp, qx, qv, 8)
+    for window in (1, 2, 3, 4, 7, 64):
+        I = oracle.Index(D, window=window, alpha=1.0)
+        with sindi.Index(dev(ip), dev(ix), dev(v), 8, window=window) as idx:
+            for mode in ("plain", "batched"):
+                ids, sc = run_search(idx, qp, qx, qv, k=10, gamma=0, mode=mode)
+                for r in range(Q.n):
+                    oi, os_ = I.search(Q, r, k=10, gamma=0)
+                    assert ids[r, :7].tolist() == oi.tolist(), (window, mode, r)
+                    np.testing.assert_array_equal(sc[r, :7], os_.astype(np.float32))
+                    assert np.all(ids[r, 7:] == 0xFFFFFFFF) and np.all(np.isneginf(sc[r, 7:]))
+                ids, sc = run_search(idx, qp, qx, qv, k=3, gamma=5, mode=mode)
+                for r in range(Q.n):
+                    oi, os_ = I.search(Q, r, k=3, gamma=5)
+                    assert ids[r].tolist() == oi.tolist(), (window, mode, r)
+
+
+def test_gamma_at_least_n_is_exhaustive(pruned_small):
+    """gamma >= N: the reorder sees every document, so any alpha gives the brute-force top-k."""
+    w, _, _, _, _ = pruned_small
+    ip, ix, v = datagen.random_csr(3000, 500, 20.0, seed=91, zipf_s=1.0)
+    qp, qx, qv = datagen.random_csr(10, 500, 12.0, seed=92, zipf_s=1.0, nnz_min=1)
+    D, Q = oracle.Dataset(ip, ix, v, 500), oracle.Dataset(qp, qx, qv, 500)
+    with sindi.Index(dev(ip), dev(ix), dev(v), 500, window=512, alpha=0.2) as idx:
+        ids, sc = run_search(idx, qp, qx, qv, k=20, gamma=4096)
+    for r in range(Q.n):
+        oi, os_ = oracle.brute_force(D, Q, r, 84)
+        check_ranked(ids[r], sc[r], oi, os_, 20, D.n, what=f"query {r}")
+
+
+def test_host_buffers_match_device_buffers(pruned_small):
+    w, (ip, ix, v), (qp, qx, qv), D, Q = pruned_small
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=4096, alpha=0.5) as idx:
+        a_ids, a_sc = run_search(idx, qp, qx, qv, k=50, gamma=500)
+        b_ids, b_sc = run_search(idx, qp, qx, qv, k=50, gamma=500, host=True)
+    np.testing.assert_array_equal(a_ids, b_ids)
+    np.testing.assert_array_equal(a_sc, b_sc)
+
+
+def test_invalid_documents_and_queries():
+    ip, ix, v = _csr([[(1, 1.0), (1, 2.0)]], 4)                   # duplicate dim
+    with pytest.raises(sindi.SindiError, match="INVALID_DATA"):
+        sindi.Index(dev(ip), dev(ix), dev(v), 4)
+    ip, ix, v = _csr([[(5, 1.0)]], 4)                               # dim out of range
+    with pytest.raises(sindi.SindiError, match="INVALID_DATA"):
+        sindi.Index(dev(ip), dev(ix), dev(v), 4)
+    ip, ix, v = _csr([[(1, float("nan"))]], 4)                      # non-finite
+    with pytest.raises(sindi.SindiError, match="INVALID_DATA"):
+        sindi.Index(ip, ix, v, 4)
+    bad_ip = np.array([0, 2, 1], np.int64)
+    with pytest.raises(sindi.SindiError, match="INVALID_DATA"):
+        sindi.Index(dev(bad_ip), dev(np.zeros(2, np.int32)), dev(np.ones(2, np.float32)), 4)
+    with pytest.raises(sindi.SindiError, match="INVALID_ARG"):
+        sindi.Index(ip, ix, v, 4, alpha=0.0)
+    ip, ix, v = _csr([[(1, 1.0)], [(2, 1.0)]], 4)
+    with sindi.Index(dev(ip), dev(ix), dev(v), 4) as idx:
+        for q in ([(9, 1.0)], [(1, 1.0), (1, 2.0)], [(1, float("inf"))]):
+            qp, qx, qv = _csr([q], 4)
+            idx.search(dev(qp), dev(qx), dev(qv), k=2)
+            with pytest.raises(sindi.SindiError, match="INVALID_DATA"):
+                idx.check()
+        qp, qx, qv = _csr([[(1, 1.0)]], 4)
+        with pytest.raises(sindi.SindiError, match="INVALID_ARG"):
+            idx.search(dev(qp), dev(qx), dev(qv), k=3, gamma=2)      # gamma < k
+        with pytest.raises(sindi.SindiError, match="UNSUPPORTED"):
+            idx.search(dev(qp), dev(qx), dev(qv), k=1, beta=0.5)
+        ids, sc = idx.search(dev(qp), dev(qx), dev(qv), k=2)          # the index still works after errors
+        idx.check()
+        assert ids.cpu().tolist() == [[0, 1]]
+
+
+@pytest.mark.slow
+def test_full_size_pruned_1m_sampled():
+    """1M docs x 30,522 dims, alpha 0.5, gamma 500, k 50, window as benchmarked: sampled queries vs the
+    oracle, plus Recall@50 against FP64 brute force."""
+    w = datagen.WORKLOADS["pruned-1m"]
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    D, Q = oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+    I = oracle.Index(D, window=w.window, alpha=w.alpha)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=w.window, alpha=w.alpha) as idx:
+        ids, sc = run_search(idx, qp, qx, qv, k=w.k, gamma=w.gamma, mode="plain")
+        bids, bsc = run_search(idx, qp, qx, qv, k=w.k, gamma=w.gamma, mode="batched")
+    sample = list(range(0, Q.n, 50))
+    recalls = []
+    for r in sample:
+        check_reranked(ids[r], sc[r], D, Q, r, I, w.k, w.gamma, what=f"query {r}")
+        check_reranked(bids[r], bsc[r], D, Q, r, I, w.k, w.gamma, what=f"batched query {r}")
+        truth, _ = oracle.brute_force(D, Q, r, w.k)
+        recalls.append(oracle.recall(ids[r], truth))
+    assert np.mean(recalls) >= 0.99, recalls
