@@ -20,7 +20,7 @@
 
 namespace sindi {
 
-constexpr int kPruneWarps = 8;                 // warps per block in prune_rows
+constexpr int kPruneWarps = 4;                 // warps per block in prune_rows (32 KiB static smem)
 constexpr int kPruneRowCap = 1024;             // longest row a warp sorts (smem 8 KB / warp)
 
 __global__ void validate_indptr_kernel(const int64_t* indptr, int64_t n, uint32_t* err) {
@@ -339,6 +339,7 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     const uint32_t lambda = ix.lambda;
     const uint32_t sigma = ix.sigma;
     uint32_t e = 0;
+    SINDI_TRACE_MSG("build_lists: enter");
     ix.kept = P.alloc<uint32_t>(n > 0 ? n : 1);
     ix.scale = P.alloc<float>(d);
     ix.seg = P.alloc<uint32_t>((size_t)d * sigma + 1);
@@ -349,6 +350,7 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     uint32_t* long_rows = P.alloc<uint32_t>(n > 0 ? n : 1);
     uint32_t* n_long = P.alloc<uint32_t>(1);
     SINDI_CUDA(cudaMemsetAsync(n_long, 0, 4, stream));
+    SINDI_TRACE_MSG("build_lists: launching prune_rows");
     if (n > 0) {
         prune_rows_kernel<<<grid_for(n, kPruneWarps, 152 * 32), kPruneWarps * 32, 0, stream>>>(
             ix.indptr, ix.indices, ix.values, n, d, ix.alpha, kept, kdim, kval, long_rows, n_long, ix.err);
@@ -371,6 +373,7 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     P.free(long_rows);
     P.free(n_long);
 
+    SINDI_TRACE_MSG("build_lists: pruning done");
     // --- compact kept entries (document order)
     int64_t* kept_off = P.alloc<int64_t>(n + 1);
     exclusive_scan<uint32_t, int64_t>(kept, kept_off, n, P);
@@ -395,6 +398,7 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     P.free(kval);
     P.free(kept_off);
 
+    SINDI_TRACE_MSG("build_lists: compacted %lld kept entries", (long long)Pn);
     // --- offsets of every list I_{j,w}
     const int64_t S = (int64_t)d * sigma;
     uint32_t* cnt = P.alloc<uint32_t>(S > 0 ? S : 1);
@@ -406,6 +410,7 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     exclusive_scan<uint32_t, uint32_t>(cnt, ix.seg, S, P);
     P.free(cnt);
 
+    SINDI_TRACE_MSG("build_lists: list offsets done");
     // --- stable sort by dim: (dim, doc) order
     {
         uint32_t* kb = P.alloc<uint32_t>(Pn);
@@ -417,6 +422,7 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
         P.free(kb); P.free(db); P.free(vb);
     }
 
+    SINDI_TRACE_MSG("build_lists: sort done");
     // --- values and window-local ids
     if (ix.dtype == SINDI_F8E4M3) {
         if (d > 0) {

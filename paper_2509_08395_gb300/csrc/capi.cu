@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <new>
@@ -17,6 +18,14 @@ namespace sindi {
 static thread_local std::string g_last_error;
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+bool trace_on() {
+    static const bool on = [] {
+        const char* e = std::getenv("SINDI_TRACE");
+        return e && e[0] && e[0] != '0';
+    }();
+    return on;
+}
 
 // One pool per device, owned by the library, that keeps freed blocks for
 // reuse (release threshold = unlimited); big temporaries of a build are
@@ -117,6 +126,7 @@ const char* sindi_version(void) { return "sindi-gb300 0.1 (sm_103a)"; }
 
 sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const float* values, int64_t n_docs,
                          int32_t dim, const sindi_build_params* params, void* stream, sindi_index** out) {
+    SINDI_TRACE_MSG("sindi_build: enter n_docs=%lld dim=%d", (long long)n_docs, (int)dim);
     set_last_error("");
     if (!out) {
         set_last_error("out is NULL");
@@ -138,6 +148,7 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
         return SINDI_ERR_UNSUPPORTED;
     }
     const Where w_ptr = where_is(indptr);
+    SINDI_TRACE_MSG("sindi_build: indptr is %s", w_ptr == Where::Device ? "device" : "host");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -149,7 +160,9 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
     IndexImpl& ix = h->impl;
     try {
         ix.device = dev;
+        SINDI_TRACE_MSG("sindi_build: device %d, creating pool", dev);
         ix.pool = library_pool(dev);
+        SINDI_TRACE_MSG("sindi_build: pool ready");
         ix.n_docs = n_docs;
         ix.dim = dim;
         ix.lambda = prm.window ? prm.window : kDefaultWindow;
@@ -163,6 +176,7 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
         SINDI_CUDA(cudaMemcpyAsync(ix.indptr, indptr, sizeof(int64_t) * (n_docs + 1),
                                    w_ptr == Where::Device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         // indptr validity first: the number of entries comes from it
+        SINDI_TRACE_MSG("sindi_build: indptr copied; validating");
         launch_validate_indptr(ix.indptr, n_docs, ix.err, s);
         uint32_t e = 0;
         int64_t nnz = 0;
@@ -181,6 +195,7 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
             set_last_error("indices / values are NULL");
             return SINDI_ERR_INVALID_ARG;
         }
+        SINDI_TRACE_MSG("sindi_build: indptr ok, nnz=%lld", (long long)nnz);
         ix.doc_nnz = nnz;
         ix.indices = P.alloc<int32_t>(nnz);
         ix.values = P.alloc<float>(nnz);
@@ -193,7 +208,9 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
                                                                          : cudaMemcpyHostToDevice,
                                        s));
         }
+        SINDI_TRACE_MSG("sindi_build: documents on device; building lists");
         sindi_status st = build_lists(ix, s);
+        SINDI_TRACE_MSG("sindi_build: lists done, status %d", (int)st);
         SINDI_CUDA(cudaStreamSynchronize(s));
         SINDI_CUDA(cudaMemPoolTrimTo(ix.pool, 0));
         if (st != SINDI_OK) {
@@ -202,6 +219,7 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
             return st;
         }
     } catch (const CudaError& e) {
+        SINDI_TRACE_MSG("sindi_build: CUDA error %s at %s", cudaGetErrorString(e.code), e.where.c_str());
         sindi_status st = from_cuda(e);
         free_index_memory(ix, s);
         delete h;

@@ -89,9 +89,20 @@ __host__ __device__ __forceinline__ uint32_t key_id(uint64_t k) { return 0xFFFFF
 __host__ __device__ __forceinline__ float key_score(uint64_t k) { return order_bits_float((uint32_t)(k >> 32)); }
 
 // ---------------------------------------------------------------------------
-// Host-side error plumbing.
+// Host-side error plumbing and tracing (SINDI_TRACE=1 in the environment
+// prints every host step of build and search to stderr).
 // ---------------------------------------------------------------------------
 void set_last_error(const std::string& msg);
+bool trace_on();
+
+#define SINDI_TRACE_MSG(...)                          \
+    do {                                              \
+        if (::sindi::trace_on()) {                    \
+            std::fprintf(stderr, "[sindi] " __VA_ARGS__); \
+            std::fprintf(stderr, "\n");               \
+            std::fflush(stderr);                      \
+        }                                             \
+    } while (0)
 
 struct CudaError {
     cudaError_t code;

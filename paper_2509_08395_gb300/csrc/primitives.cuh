@@ -120,12 +120,18 @@ void exclusive_scan(const TI* in, TO* out, int64_t n, Pool& P) {
         SINDI_CUDA(cudaMemsetAsync(out, 0, sizeof(TO), P.stream));
         return;
     }
-    int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    TO* sums = P.alloc<TO>(tiles);
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     TO* offs = P.alloc<TO>(tiles + 1);
-    scan_tile_sums_kernel<TI, TO><<<(unsigned)tiles, kScanBlock, 0, P.stream>>>(in, n, sums);
-    SINDI_CUDA(cudaGetLastError());
-    exclusive_scan<TO, TO>(sums, offs, tiles, P);
+    TO* sums = nullptr;
+    if (tiles == 1) {
+        // one tile: its offset is zero (base case of the recursion on tile sums)
+        SINDI_CUDA(cudaMemsetAsync(offs, 0, sizeof(TO) * 2, P.stream));
+    } else {
+        sums = P.alloc<TO>(tiles);
+        scan_tile_sums_kernel<TI, TO><<<(unsigned)tiles, kScanBlock, 0, P.stream>>>(in, n, sums);
+        SINDI_CUDA(cudaGetLastError());
+        exclusive_scan<TO, TO>(sums, offs, tiles, P);
+    }
     scan_tile_apply_kernel<TI, TO><<<(unsigned)tiles, kScanBlock, 0, P.stream>>>(in, n, offs, out);
     SINDI_CUDA(cudaGetLastError());
     P.free(sums);
