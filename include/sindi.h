@@ -157,6 +157,36 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
                           const float* q_values, int64_t n_queries, const sindi_search_params* params,
                           uint32_t* out_ids, float* out_scores, void* stream);
 
+/*
+ * The same search as sindi_search, for callers that cannot allocate device
+ * memory while they run: an application that fixes its memory budget at start
+ * and forbids later allocation, a host framework that owns every device
+ * allocation itself, or a latency-critical loop in which the implicit
+ * synchronisation of an allocation is not acceptable. The paper has no
+ * counterpart to this call.
+ *   All working memory comes from one static device array of 8 MiB
+ *   (SINDI_NOALLOC_SCRATCH_BYTES) inside the library, which every GPU that loads
+ *   the library holds until the process exits. The call allocates nothing:
+ *   no cudaMalloc, no pool, no staging.
+ *   Arguments and results are those of sindi_search, except that the queries
+ *   and both outputs must be device memory (SINDI_ERR_INVALID_ARG otherwise).
+ *   A search whose working memory for one query exceeds the array (about
+ *   n_windows * min(max(gamma, k), window) * 8 bytes) returns
+ *   SINDI_ERR_UNSUPPORTED with the sizes in sindi_last_error(). Batched mode
+ *   processes as many queries per launch group as fit.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ *   first call before any stream capture.
+ *   Every call uses the same array and clears the counters it starts from.
+ *   Calls whose work overlaps on the GPU (other streams, other threads, other
+ *   indexes) race on the array and give undefined results: order them on one
+ *   stream or synchronise between them.
+ */
+#define SINDI_NOALLOC_SCRATCH_BYTES (8u << 20)
+sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
+                                  const float* q_values, int64_t n_queries, const sindi_search_params* params,
+                                  uint32_t* out_ids, float* out_scores, void* stream);
+
 /* Synchronise `stream`, then return (and clear) the device error word of the
    index as a status: SINDI_ERR_INVALID_DATA if a malformed query or document
    was seen since the last check, SINDI_ERR_TIMEOUT if a bounded wait gave up. */

@@ -17,6 +17,7 @@ from .sindi import (  # noqa: F401
     sindi_index_info,
     sindi_reset_stats,
     sindi_search,
+    sindi_search_noalloc,
     sindi_set_timing,
     sindi_version,
 )

@@ -346,6 +346,49 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
     return st;
 }
 
+sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
+                                  const float* q_values, int64_t n_queries, const sindi_search_params* params,
+                                  uint32_t* out_ids, float* out_scores, void* stream) {
+    set_last_error("");
+    if (!index || !params) {
+        set_last_error("index / params is NULL");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    const sindi_search_params prm = *params;
+    if (prm.k < 1 || prm.k > kMaxK || (prm.gamma != 0 && (prm.gamma < prm.k || prm.gamma > kMaxGamma)) ||
+        !(prm.beta > 0.0 && prm.beta <= 1.0) || prm.mode > SINDI_MODE_BATCHED || prm.reserved != 0) {
+        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; reserved 0");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    if (prm.beta < 1.0) {
+        set_last_error("query pruning (beta < 1) is not in this build");
+        return SINDI_ERR_UNSUPPORTED;
+    }
+    if (n_queries < 0 || n_queries > (int64_t)1 << 31) {
+        set_last_error("n_queries out of range");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    if (n_queries == 0) return SINDI_OK;
+    if (!q_indptr || !q_indices || !q_values || !out_ids || !out_scores) {
+        set_last_error("NULL query or output pointer");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    const IndexImpl& ix = index->impl;
+    DeviceGuard dg(ix.device);
+    if (where_is(q_indptr) != Where::Device || where_is(q_indices) != Where::Device ||
+        where_is(q_values) != Where::Device || where_is(out_ids) != Where::Device ||
+        where_is(out_scores) != Where::Device) {
+        set_last_error("sindi_search_noalloc takes device buffers only (staging host buffers would allocate)");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    try {
+        return search_noalloc_impl(ix, q_indptr, q_indices, q_values, n_queries, prm, out_ids, out_scores,
+                                   static_cast<cudaStream_t>(stream));
+    } catch (const CudaError& e) {
+        return from_cuda(e);
+    }
+}
+
 sindi_status sindi_check(const sindi_index* index, void* stream) {
     set_last_error("");
     if (!index) return SINDI_ERR_INVALID_ARG;

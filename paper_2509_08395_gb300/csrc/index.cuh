@@ -70,6 +70,15 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
                          const float* q_values, int64_t n_queries, const sindi_search_params& prm,
                          uint32_t* out_ids, float* out_scores, cudaStream_t stream);
 
+// Size of the static device array behind sindi_search_noalloc (search.cu).
+constexpr size_t kNoAllocScratchBytes = (size_t)SINDI_NOALLOC_SCRATCH_BYTES;
+
+// sindi_search_noalloc: the same launches as search_impl, with all working
+// memory taken from that static array instead of the pool (search.cu).
+sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
+                                 const float* q_values, int64_t n_queries, const sindi_search_params& prm,
+                                 uint32_t* out_ids, float* out_scores, cudaStream_t stream);
+
 }  // namespace sindi
 
 struct sindi_index {

@@ -19,6 +19,8 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -548,6 +550,119 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
         ix.scan_ms += ms;
         ix.scan_timed += evs.size() / 2;
     }
+    return SINDI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Search without allocation (sindi_search_noalloc). The paper has no
+// counterpart: this serves callers that may not allocate device memory while
+// they run (their memory is fixed up front, or an allocation's implicit
+// synchronisation is not allowed on their path). All working memory of the
+// search comes from one file-scope device array, sized kNoAllocScratchBytes.
+// Every call shares it: calls whose work overlaps on the GPU race.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch on the current device. Resolved once per
+// device (cudaGetSymbolAddress, with that device current) and cached.
+static cudaError_t noalloc_scratch_address(int device, unsigned char** out) {
+    static std::mutex mu;
+    static std::map<int, unsigned char*> addr;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = addr.find(device);
+    if (it != addr.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    unsigned char* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    addr[device] = p;
+    *out = p;
+    return cudaSuccess;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
+                                 const float* q_values, int64_t n_queries, const sindi_search_params& prm,
+                                 uint32_t* out_ids, float* out_scores, cudaStream_t stream) {
+    unsigned char* base = nullptr;
+    cudaError_t ce = noalloc_scratch_address(ix.device, &base);
+    if (ce != cudaSuccess) {
+        set_last_error(std::string("sindi_search_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(ce));
+        return SINDI_ERR_CUDA;
+    }
+    const int64_t N = ix.n_docs;
+    const uint32_t k = prm.k;
+    if (n_queries == 0) return SINDI_OK;
+    if (N == 0) {
+        pad_results_kernel<<<256, 256, 0, stream>>>(out_ids, out_scores, n_queries * (int64_t)k);
+        SINDI_CUDA(cudaGetLastError());
+        return SINDI_OK;
+    }
+    const bool final_stage = prm.gamma == 0;
+    const uint32_t g = (uint32_t)std::min<int64_t>(final_stage ? k : prm.gamma, N);
+    const uint32_t cand_cap = ix.sigma * std::min<uint32_t>(g, ix.lambda);
+    const uint32_t top_cap = final_stage ? 1 : g;
+    // scratch of a group of c queries: six arrays, each 256-byte aligned
+    auto need = [&](int64_t c) {
+        return align256((size_t)cand_cap * 8 * c) + align256(4 * (size_t)c) + align256(8 * (size_t)c) +
+               align256((size_t)top_cap * 8 * c) + align256(4 * (size_t)c) + align256((size_t)top_cap * 8 * c) +
+               align256(4 * (size_t)c);
+    };
+    if (need(1) > kNoAllocScratchBytes) {
+        set_last_error("sindi_search_noalloc: one query needs " + std::to_string(need(1)) +
+                       " bytes of scratch (n_windows * min(candidates, window) * 8 + ...), more than the " +
+                       std::to_string(kNoAllocScratchBytes) + "-byte static scratch area; use sindi_search");
+        return SINDI_ERR_UNSUPPORTED;
+    }
+    const bool batched = prm.mode == SINDI_MODE_BATCHED;
+    int64_t chunk = 1;
+    if (batched) {
+        chunk = std::min<int64_t>(n_queries, 65535);
+        while (chunk > 1 && need(chunk) > kNoAllocScratchBytes) chunk = std::max<int64_t>(1, chunk / 2);
+    }
+    unsigned char* q = base;
+    auto carve = [&](size_t bytes) {
+        unsigned char* r = q;
+        q += align256(bytes);
+        return r;
+    };
+    uint64_t* cand = reinterpret_cast<uint64_t*>(carve((size_t)cand_cap * 8 * chunk));
+    uint32_t* cand_count = reinterpret_cast<uint32_t*>(carve(4 * (size_t)chunk));
+    unsigned long long* bound = reinterpret_cast<unsigned long long*>(carve(8 * (size_t)chunk));
+    uint64_t* top = reinterpret_cast<uint64_t*>(carve((size_t)top_cap * 8 * chunk));
+    uint32_t* top_count = reinterpret_cast<uint32_t*>(carve(4 * (size_t)chunk));
+    uint64_t* rr = reinterpret_cast<uint64_t*>(carve((size_t)top_cap * 8 * chunk));
+    uint32_t* done = reinterpret_cast<uint32_t*>(carve(4 * (size_t)chunk));
+    // the array keeps the previous call's contents: clear the counters the kernels start from
+    SINDI_CUDA(cudaMemsetAsync(cand_count, 0, 4 * chunk, stream));
+    SINDI_CUDA(cudaMemsetAsync(bound, 0, 8 * chunk, stream));
+    SINDI_CUDA(cudaMemsetAsync(done, 0, 4 * chunk, stream));
+
+    const DevIndex dix = ix.dev();
+    const size_t scan_smem = (size_t)ix.lambda * sizeof(float);
+    for (int64_t q0 = 0; q0 < n_queries; q0 += chunk) {
+        const uint32_t nq = (uint32_t)std::min<int64_t>(chunk, n_queries - q0);
+        ScanArgs sa{dix, q_indptr, q_indices, q_values, q0, g, cand, cand_count, bound, cand_cap};
+        launch_scan_any(ix.dtype, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem, stream);
+        MergeArgs ma{dix, q_indptr, q_indices, q_values, q0, g, cand, cand_count, bound, cand_cap,
+                     final_stage ? 1 : 0, k, out_ids, out_scores, top, top_count, top_cap};
+        merge_kernel<<<nq, kMergeThreads, 0, stream>>>(ma);
+        SINDI_CUDA(cudaGetLastError());
+        ix.launches += 2;
+        ix.scan_launches += 1;
+        if (!final_stage) {
+            RerankArgs ra{dix, q_indptr, q_indices, q_values, q0, top, top_count, top_cap, rr, done, k,
+                          out_ids, out_scores};
+            dim3 grid(ceil_div_u32(g, kRerankDocsPerBlock), nq);
+            rerank_kernel<<<grid, kRerankThreads, 0, stream>>>(ra);
+            SINDI_CUDA(cudaGetLastError());
+            ix.launches += 1;
+        }
+    }
+    ix.queries += (uint64_t)n_queries;
     return SINDI_OK;
 }
 

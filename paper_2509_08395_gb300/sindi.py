@@ -64,6 +64,9 @@ _SIGS = {
     "sindi_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int64, ctypes.POINTER(sindi_search_params), ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "sindi_search_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.POINTER(sindi_search_params), ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
     "sindi_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sindi_index_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_index_info_t)]),
     "sindi_index_export": (ctypes.c_int, [ctypes.c_void_p] * 6),
@@ -148,6 +151,19 @@ def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_
                           _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm), _ptr(out_ids, np.uint32),
                           _ptr(out_scores, np.float32), _stream(stream, q_indptr, out_ids))
     _check(st, "sindi_search")
+
+
+def sindi_search_noalloc(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
+                         gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None) -> None:
+    """sindi_search for callers that cannot allocate device memory: all working memory comes from the library's
+    static 8 MiB device array. Device tensors only; calls that overlap on the GPU race on that array."""
+    lib = load()
+    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], reserved=0)
+    st = lib.sindi_search_noalloc(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
+                                  _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm),
+                                  _ptr(out_ids, np.uint32), _ptr(out_scores, np.float32),
+                                  _stream(stream, q_indptr, out_ids))
+    _check(st, "sindi_search_noalloc")
 
 
 def sindi_check(index: int, stream=None) -> None:
