@@ -4,17 +4,25 @@
 //   scan_window  (one block per (query, window)): the query's postings in the
 //       window, I_{j,w} for every term j, are scatter-added into an FP32 score
 //       array A[lambda] in shared memory (Alg. 2, the product + accumulation
-//       loops); then the window's best g (score, id) pairs are selected by a
-//       radix select over A (the heap update of Alg. 2) and appended to the
-//       query's candidate list. A per-query bound (the best threshold any
-//       finished window has published) drops candidates that cannot reach
-//       the global top g.
-//   merge        (one block per query): the global top g of all windows
-//       (the heap H of Alg. 2 across windows). With gamma = 0 these are the
-//       sorted results; otherwise they are the gamma reorder candidates.
-//   rerank       (several blocks per query): delta(x_i, q) from the unpruned
+//       loops). The block then histograms the window's scores on the top 12
+//       bits of their order key and emits every slot in the bins at or above
+//       the bin that holds its g-th best slot (the window's share of the heap
+//       update of Alg. 2). When ties crowd that bin, an exact radix select
+//       emits exactly the best g. Each block adds the histogram of what it
+//       emitted to a per-query histogram; in batched schedules it first reads
+//       that histogram, and a bin reached by g already emitted slots bounds
+//       what can still enter the answer.
+//   merge        (a few blocks per query): from the per-query histogram, the
+//       bin of the global g-th best candidate; candidates below it are
+//       dropped, the rest (about g) gathered; the last block of the query
+//       selects the exact best g in shared memory (the heap H of Alg. 2
+//       across windows). With gamma = 0 these are the sorted results;
+//       otherwise they are the gamma reorder candidates.
+//   rerank       (one warp per candidate): delta(x_i, q) from the unpruned
 //       document and the unpruned query (Alg. 4, the reorder loop); the last
-//       block of a query selects and sorts the top k.
+//       block of a query sorts the scores and writes the top k.
+//
+// Order keys (common.cuh) make every comparison exact: (score desc, id asc).
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -32,25 +40,63 @@ namespace sindi {
 constexpr int kScanThreads = 512;
 constexpr int kScanWarps = kScanThreads / 32;
 constexpr int kTermChunk = kScanThreads;   // query terms staged per pass (one per thread)
-constexpr int kScanUnroll = 8;             // postings in flight per lane
+constexpr int kChunkU = 4;                 // postings per lane in one warp chunk
+constexpr int kChunkLen = 32 * kChunkU;    // postings of one warp chunk (one list only)
+constexpr int kHistBits = 12;
+constexpr int kHistBins = 1 << kHistBits;  // bins on the top 12 bits of a score key
+constexpr int kKeyBinShift = 64 - kHistBits;
 constexpr int kMergeThreads = 512;
 constexpr int kRerankThreads = 256;
-constexpr int kRerankDocsPerBlock = 16;
-constexpr int kHashSlots = 4096;           // query hash (load <= 1/2 for kMaxQueryTerms)
+constexpr int kRerankWarps = kRerankThreads / 32;
+constexpr int kHashSlots = 4096;           // query hash (load <= 1/2 at the term limit)
 constexpr int kQueryTermLimit = kHashSlots / 2;
 
-struct ScanArgs {
-    DevIndex ix;
-    const int64_t* q_indptr;
-    const int32_t* q_indices;
-    const float* q_values;
-    int64_t q_first;
-    uint32_t g;                     // candidates kept per query (min(gamma or k, N))
-    uint64_t* cand;                 // [queries][cand_cap]
-    uint32_t* cand_count;           // [queries]
-    unsigned long long* bound;      // [queries]
-    uint32_t cand_cap;
+// Working memory of a launch group of queries, all arrays [query][...].
+struct Workspace {
+    uint32_t* cand_count;   // window candidates appended so far
+    uint32_t* fcount;       // merge: candidates kept by the filter
+    uint32_t* mticket;      // merge: finished blocks
+    uint32_t* rticket;      // rerank: finished blocks
+    uint32_t* top_count;    // reorder candidates
+    uint32_t* hist;         // [kHistBins] histogram of emitted candidates
+    uint64_t* cand;         // [cand_cap]
+    uint64_t* fbuf;         // [fcap]
+    uint64_t* top;          // [top_cap]
+    uint64_t* rr;           // [top_cap]
+    uint32_t cand_cap, fcap, top_cap;
 };
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bytes of a workspace for c queries, counters first (one memset clears them).
+static size_t workspace_counter_bytes(int64_t c) { return align256((size_t)c * 4 * (5 + kHistBins)); }
+static size_t workspace_bytes(int64_t c, uint32_t cand_cap, uint32_t fcap, uint32_t top_cap) {
+    return workspace_counter_bytes(c) + align256((size_t)c * cand_cap * 8) + align256((size_t)c * fcap * 8) +
+           2 * align256((size_t)c * top_cap * 8);
+}
+
+static Workspace carve_workspace(unsigned char* base, int64_t c, uint32_t cand_cap, uint32_t fcap, uint32_t top_cap) {
+    Workspace w;
+    uint32_t* u = reinterpret_cast<uint32_t*>(base);
+    w.cand_count = u;
+    w.fcount = u + c;
+    w.mticket = u + 2 * c;
+    w.rticket = u + 3 * c;
+    w.top_count = u + 4 * c;
+    w.hist = u + 5 * c;
+    unsigned char* q = base + workspace_counter_bytes(c);
+    w.cand = reinterpret_cast<uint64_t*>(q);
+    q += align256((size_t)c * cand_cap * 8);
+    w.fbuf = reinterpret_cast<uint64_t*>(q);
+    q += align256((size_t)c * fcap * 8);
+    w.top = reinterpret_cast<uint64_t*>(q);
+    q += align256((size_t)c * top_cap * 8);
+    w.rr = reinterpret_cast<uint64_t*>(q);
+    w.cand_cap = cand_cap;
+    w.fcap = fcap;
+    w.top_cap = top_cap;
+    return w;
+}
 
 template <int DT>
 __device__ __forceinline__ float load_value(const void* pval, uint32_t p) {
@@ -74,16 +120,65 @@ __device__ __forceinline__ int term_of(const uint32_t* pre, int n, uint32_t f) {
     return lo;
 }
 
+// Block-wide (512 threads): the bin holding the g-th largest element of a
+// 4096-bin histogram read through `get`, counting from the top bin. Leaves the
+// bin in st[0] (0 when the total is below g), the count strictly above it in
+// st[1], its own count in st[2] and the histogram total in st[3].
+template <typename Get>
+__device__ void block_find_bin(const Get& get, uint32_t g, uint32_t* red, uint32_t* st) {
+    uint32_t c8[8];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        c8[j] = get(kHistBins - 1 - 8 * (int)threadIdx.x - j);
+        s += c8[j];
+    }
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_sum<uint32_t, kScanThreads>(s, &tot, red);
+    if (threadIdx.x == 0) {
+        st[0] = 0;
+        st[1] = tot;
+        st[2] = 0;
+        st[3] = tot;
+    }
+    __syncthreads();
+    if (ex < g && g <= ex + s) {
+        uint32_t above = ex;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (above < g && g <= above + c8[j]) {
+                st[0] = (uint32_t)(kHistBins - 1 - 8 * (int)threadIdx.x - j);
+                st[1] = above;
+                st[2] = c8[j];
+            }
+            above += c8[j];
+        }
+    }
+    __syncthreads();
+}
+
+struct ScanArgs {
+    DevIndex ix;
+    const int64_t* q_indptr;
+    const int32_t* q_indices;
+    const float* q_values;
+    int64_t q_first;
+    uint32_t g;             // candidates per query: min(gamma or k, N)
+    uint32_t win_cap;       // most candidates one window may emit without an exact select
+    int use_partial;        // read the per-query histogram before emitting
+    Workspace ws;
+};
+
 template <int DT, bool QUERY_MAJOR>
-__global__ void __launch_bounds__(kScanThreads) scan_window_kernel(ScanArgs a) {
+__global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a) {
     extern __shared__ float A[];                    // [lambda]
+    __shared__ uint32_t hist[kHistBins];
     __shared__ uint32_t t_start[kTermChunk];
-    __shared__ uint32_t t_pre[kTermChunk + 1];
+    __shared__ uint32_t t_end[kTermChunk];
+    __shared__ uint32_t c_pre[kTermChunk + 1];
     __shared__ float t_w[kTermChunk];
     __shared__ uint32_t red[kScanWarps + 1];
-    __shared__ uint32_t hist[256];
     __shared__ uint32_t st[4];
-    __shared__ unsigned long long s_bound;
 
     const DevIndex& ix = a.ix;
     const uint32_t w = QUERY_MAJOR ? blockIdx.y : blockIdx.x;
@@ -96,15 +191,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_window_kernel(ScanArgs a) {
     const int nt = (int)(a.q_indptr[r + 1] - qb);
 
     for (uint32_t m = threadIdx.x; m < lambda; m += kScanThreads) A[m] = 0.0f;
+    for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) hist[b] = 0;
 
     for (int c0 = 0; c0 < nt; c0 += kTermChunk) {
         const int nc = min(kTermChunk, nt - c0);
         __syncthreads();  // previous chunk fully consumed
-        uint32_t len = 0;
+        uint32_t nch = 0;
         if ((int)threadIdx.x < nc) {
             const int32_t j = a.q_indices[qb + c0 + threadIdx.x];
             const float qv = a.q_values[qb + c0 + threadIdx.x];
-            uint32_t start = 0;
+            uint32_t start = 0, len = 0;
             float wq = 0.0f;
             if (j >= 0 && j < ix.dim && isfinite(qv)) {
                 const uint64_t s = (uint64_t)j * ix.sigma + w;
@@ -115,84 +211,103 @@ __global__ void __launch_bounds__(kScanThreads) scan_window_kernel(ScanArgs a) {
                 atomicOr(ix.err, (j < 0 || j >= ix.dim) ? kErrQueryDim : kErrQueryValue);
             }
             t_start[threadIdx.x] = start;
+            t_end[threadIdx.x] = start + len;
             t_w[threadIdx.x] = wq;
+            nch = (len + kChunkLen - 1) / kChunkLen;
         }
         uint32_t total;
-        const uint32_t excl = block_exclusive_sum<uint32_t, kScanThreads>(len, &total, red);
-        if ((int)threadIdx.x < nc) t_pre[threadIdx.x] = excl;
+        const uint32_t excl = block_exclusive_sum<uint32_t, kScanThreads>(nch, &total, red);
+        if ((int)threadIdx.x < nc) c_pre[threadIdx.x] = excl;
         __syncthreads();
 
-        // scatter-add: lane-interleaved over the flattened postings of the chunk
-        for (uint32_t base = (uint32_t)warp * 32u * kScanUnroll; base < total;
-             base += (uint32_t)kScanWarps * 32u * kScanUnroll) {
-            uint32_t id[kScanUnroll];
-            float pr[kScanUnroll];
+        // scatter-add: a warp takes chunks of one list, lanes interleaved (coalesced)
+        for (uint32_t c = (uint32_t)warp; c < total; c += kScanWarps) {
+            const int t = term_of(c_pre, nc, c);
+            const uint32_t p0 = t_start[t] + (c - c_pre[t]) * (uint32_t)kChunkLen;
+            const uint32_t pe = t_end[t];
+            const float wq = t_w[t];
+            uint32_t id[kChunkU];
+            float pr[kChunkU];
 #pragma unroll
-            for (int u = 0; u < kScanUnroll; u++) {
-                const uint32_t f = base + (uint32_t)u * 32u + (uint32_t)lane;
+            for (int u = 0; u < kChunkU; u++) {
+                const uint32_t p = p0 + (uint32_t)(u * 32 + lane);
                 id[u] = 0xFFFFFFFFu;
                 pr[u] = 0.0f;
-                if (f < total) {
-                    const int t = term_of(t_pre, nc, f);
-                    const uint32_t p = t_start[t] + (f - t_pre[t]);
+                if (p < pe) {
                     id[u] = __ldg(ix.pid + p);
-                    pr[u] = t_w[t] * load_value<DT>(ix.pval, p);
+                    pr[u] = wq * load_value<DT>(ix.pval, p);
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kScanUnroll; u++)
+            for (int u = 0; u < kChunkU; u++)
                 if (id[u] != 0xFFFFFFFFu) atomicAdd(&A[id[u]], pr[u]);
         }
     }
     __syncthreads();
 
-    // window top-g (Alg. 2 heap update), ids >= N are not candidates
+    // ---- window selection (ids >= N are not candidates)
     const int64_t gbase = (int64_t)w * lambda;
     const int64_t rest = ix.n_docs - gbase;
     const int n_eff = (int)(rest < (int64_t)lambda ? rest : (int64_t)lambda);
-    const int g_w = (int)a.g < n_eff ? (int)a.g : n_eff;
+    const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
     auto key_of = [&](int i) -> uint64_t { return result_key(A[i], (uint32_t)(gbase + i)); };
-    uint64_t T = 0;
-    if (n_eff > g_w) T = block_select_threshold<kScanThreads>(key_of, n_eff, g_w, hist, st);
-    if (threadIdx.x == 0) {
-        unsigned long long* bp = a.bound + y;
-        unsigned long long B;
-        if (g_w == (int)a.g) {
-            unsigned long long old = atomicMax(bp, (unsigned long long)T);
-            B = old > T ? old : T;
-        } else {
-            unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(bp);
-            B = cur > T ? cur : T;
-        }
-        s_bound = B;
+    for (int base = 0; base < n_eff; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int bin = i < n_eff ? (int)(float_order_bits(A[i]) >> (32 - kHistBits)) : -1;
+        const unsigned peers = __match_any_sync(kFull, bin);
+        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    const uint64_t B = s_bound;
+    block_find_bin([&](int b) { return hist[b]; }, g_w, red, st);
+    const uint32_t bw = st[0];
+    const uint32_t c_bw = st[1] + st[2];  // slots in bins >= bw
+    __syncthreads();
+    uint32_t lo = bw;
+    uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
+    if (a.use_partial) {
+        // g slots already emitted at or above bin bp prove the answer lies there
+        block_find_bin([&](int b) { return __ldcg(H + b); }, a.g, red, st);
+        if (st[3] >= a.g && st[0] > lo) lo = st[0];
+        __syncthreads();
+    }
+    uint64_t thr = (uint64_t)lo << kKeyBinShift;
+    if (lo == bw && c_bw > a.win_cap) {
+        // ties crowd the cut bin: exact best g_w of the window
+        thr = block_select_threshold<kScanThreads>(key_of, n_eff, (int)g_w, t_start, st);
+    }
+    for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) hist[b] = 0;
+    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    uint64_t* cand = a.cand + (size_t)y * a.cand_cap;
+    uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
     for (int base = 0; base < n_eff; base += kScanThreads) {
         const int i = base + threadIdx.x;
         uint64_t k = 0;
         bool ok = false;
         if (i < n_eff) {
             k = key_of(i);
-            ok = k >= B;
+            ok = k >= thr;
         }
         const unsigned bal = __ballot_sync(kFull, ok);
         uint32_t wbase = 0;
-        if (lane == 0 && bal) wbase = atomicAdd(a.cand_count + y, (uint32_t)__popc(bal));
+        if (lane == 0 && bal) wbase = atomicAdd(a.ws.cand_count + y, (uint32_t)__popc(bal));
         wbase = __shfl_sync(kFull, wbase, 0);
+        const int bin = ok ? (int)(k >> kKeyBinShift) : -1;
+        const unsigned peers = __match_any_sync(kFull, bin);
         if (ok) {
             const uint32_t pos = wbase + (uint32_t)__popc(bal & lt);
-            if (pos < a.cand_cap) cand[pos] = k;
+            if (pos < a.ws.cand_cap) cand[pos] = k;
             else atomicOr(ix.err, kErrCandOverflow);
+            if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
         }
     }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kHistBins; b += kScanThreads)
+        if (hist[b]) atomicAdd(H + b, hist[b]);
 }
 
 // ---------------------------------------------------------------------------
-// Query checks shared by merge and rerank: an open-addressing hash of the
-// query's dims in shared memory.
+// Query hash in shared memory: dims -> weights (merge checks the query with
+// it; rerank reads weights from it).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t hash_slot(int32_t j) { return ((uint32_t)j * 2654435761u) >> (32 - 12); }
 
@@ -203,6 +318,7 @@ __device__ void build_query_hash(const int32_t* qi, const float* qv, int nt, int
     __syncthreads();
     if (nt > kQueryTermLimit) {
         if (report && threadIdx.x == 0) atomicOr(err, kErrQueryTooLong);
+        __syncthreads();
         return;
     }
     for (int t = threadIdx.x; t < nt; t += BLOCK) {
@@ -220,7 +336,7 @@ __device__ void build_query_hash(const int32_t* qi, const float* qv, int nt, int
         for (int probe = 0; probe < kHashSlots; probe++) {
             int32_t old = atomicCAS(&hk[s], -1, j);
             if (old == -1) {
-                hv[s] = v;
+                if (hv) hv[s] = v;
                 break;
             }
             if (old == j) {
@@ -244,11 +360,11 @@ __device__ __forceinline__ float query_weight(const int32_t* hk, const float* hv
     return 0.0f;
 }
 
-// Writes the selected keys (already gathered in s[0..cnt), cnt <= kMaxK) as
-// sorted results of query row y: ids and scores, padded to k.
+// Sorts s[0..cnt) (cnt <= kMaxK) descending and writes the first k as the
+// results of query row r, padded with id 0xFFFFFFFF / score -inf.
 template <int BLOCK>
 __device__ void write_sorted_results(uint64_t* s, int cnt, uint32_t k, uint32_t* out_ids, float* out_scores,
-                                     int64_t y) {
+                                     int64_t r) {
     int p2 = 1;
     while (p2 < cnt) p2 <<= 1;
     for (int i = cnt + threadIdx.x; i < p2; i += BLOCK) s[i] = 0;
@@ -261,9 +377,35 @@ __device__ void write_sorted_results(uint64_t* s, int cnt, uint32_t k, uint32_t*
             id = key_id(s[t]);
             sc = key_score(s[t]);
         }
-        out_ids[(size_t)y * k + t] = id;
-        out_scores[(size_t)y * k + t] = sc;
+        out_ids[(size_t)r * k + t] = id;
+        out_scores[(size_t)r * k + t] = sc;
     }
+}
+
+// Gathers the keys >= T of key_of(0..n) into dst[0..cap) (block-wide, order
+// arbitrary); *counter (shared, zero on entry) ends at the number found.
+template <int BLOCK, typename KeyOf>
+__device__ void gather_at_least(const KeyOf& key_of, uint32_t n, uint64_t T, uint64_t* dst, uint32_t cap,
+                                uint32_t* counter) {
+    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    for (uint32_t base = 0; base < n; base += BLOCK) {
+        const uint32_t i = base + threadIdx.x;
+        uint64_t k = 0;
+        bool ok = false;
+        if (i < n) {
+            k = key_of(i);
+            ok = k >= T;
+        }
+        const unsigned bal = __ballot_sync(kFull, ok);
+        uint32_t wb = 0;
+        if (lane == 0 && bal) wb = atomicAdd(counter, (uint32_t)__popc(bal));
+        wb = __shfl_sync(kFull, wb, 0);
+        if (ok) {
+            const uint32_t pos = wb + (uint32_t)__popc(bal & lt);
+            if (pos < cap) dst[pos] = k;
+        }
+    }
+    __syncthreads();
 }
 
 struct MergeArgs {
@@ -273,72 +415,105 @@ struct MergeArgs {
     const float* q_values;
     int64_t q_first;
     uint32_t g;
-    uint64_t* cand;
-    uint32_t* cand_count;
-    unsigned long long* bound;
-    uint32_t cand_cap;
-    int final_stage;           // 1: g = min(k, N) results are the answer
+    int final_stage;           // 1: the g = min(k, N) results are the answer
     uint32_t k;
-    uint32_t* out_ids;         // rows indexed from q_first
+    uint32_t* out_ids;         // absolute query rows
     float* out_scores;
-    uint64_t* top;             // [queries][top_cap] when final_stage == 0
-    uint32_t* top_count;
-    uint32_t top_cap;
+    Workspace ws;
 };
 
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
-    __shared__ int32_t hk[kHashSlots];
-    __shared__ float hv[kHashSlots];
-    __shared__ uint64_t s[kMaxK];
-    __shared__ uint32_t hist[256];
+    extern __shared__ uint64_t sbuf[];          // [fcap]
+    __shared__ uint64_t sel[kMaxK];
+    __shared__ uint32_t red[kScanWarps + 1];
     __shared__ uint32_t st[4];
+    __shared__ uint32_t hist256[256];
     __shared__ uint32_t s_n;
-    const uint32_t y = blockIdx.x;
+    __shared__ int s_last;
+    const Workspace& ws = a.ws;
+    const uint32_t y = blockIdx.y;
     const int64_t r = a.q_first + y;
-    const int64_t qb = a.q_indptr[r];
-    const int nt = (int)(a.q_indptr[r + 1] - qb);
-    build_query_hash<kMergeThreads>(a.q_indices + qb, a.q_values + qb, nt, a.ix.dim, hk, hv, a.ix.err, true);
+    const uint32_t C = min(ws.cand_count[y], ws.cand_cap);
+    const uint32_t g = a.g < C ? a.g : C;
+    const uint64_t* cand = ws.cand + (size_t)y * ws.cand_cap;
+    uint32_t* H = ws.hist + (size_t)y * kHistBins;
 
-    const uint32_t C = min(a.cand_count[y], a.cand_cap);
-    const uint64_t* cand = a.cand + (size_t)y * a.cand_cap;
-    const int g = (int)(a.g < C ? a.g : C);
-    auto key_of = [&](int i) -> uint64_t { return cand[i]; };
-    uint64_t T = 0;
-    if ((int)C > g) T = block_select_threshold<kMergeThreads>(key_of, (int)C, g, hist, st);
-    if (threadIdx.x == 0) s_n = 0;
+    // bin of the g-th best candidate; every candidate below it is out
+    block_find_bin([&](int b) { return H[b]; }, g, red, st);
+    const uint32_t bstar = st[0];
+    const uint32_t S = st[1] + st[2];  // candidates in bins >= bstar
     __syncthreads();
-    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
-    for (uint32_t base = 0; base < C; base += kMergeThreads) {
-        const uint32_t i = base + threadIdx.x;
-        uint64_t k = 0;
-        bool ok = false;
-        if (i < C) {
-            k = cand[i];
-            ok = k >= T;
-        }
-        const unsigned bal = __ballot_sync(kFull, ok);
-        uint32_t wb = 0;
-        if (lane == 0 && bal) wb = atomicAdd(&s_n, (uint32_t)__popc(bal));
-        wb = __shfl_sync(kFull, wb, 0);
-        if (ok) {
-            const uint32_t pos = wb + (uint32_t)__popc(bal & lt);
-            if (a.final_stage) {
-                if (pos < kMaxK) s[pos] = k;
-            } else if (pos < a.top_cap) {
-                a.top[(size_t)y * a.top_cap + pos] = k;
+    {
+        const uint32_t per = (C + gridDim.x - 1) / gridDim.x;
+        const uint32_t lo = blockIdx.x * per, hi = min(C, lo + per);
+        const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+        uint64_t* fb = ws.fbuf + (size_t)y * ws.fcap;
+        for (uint32_t base = lo; base < hi; base += kMergeThreads * 4) {
+            uint64_t kk[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint32_t i = base + (uint32_t)(u * kMergeThreads) + threadIdx.x;
+                kk[u] = i < hi ? __ldcg(cand + i) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint32_t i = base + (uint32_t)(u * kMergeThreads) + threadIdx.x;
+                const bool ok = i < hi && (uint32_t)(kk[u] >> kKeyBinShift) >= bstar;
+                const unsigned bal = __ballot_sync(kFull, ok);
+                uint32_t wb = 0;
+                if (lane == 0 && bal) wb = atomicAdd(ws.fcount + y, (uint32_t)__popc(bal));
+                wb = __shfl_sync(kFull, wb, 0);
+                if (ok) {
+                    const uint32_t pos = wb + (uint32_t)__popc(bal & lt);
+                    if (pos < ws.fcap) fb[pos] = kk[u];
+                }
             }
         }
     }
+    __threadfence();
     __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(ws.mticket + y, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+
+    // ---- last block of the query: check the query, exact best g
+    {
+        const int64_t qb = a.q_indptr[r];
+        const int nt = (int)(a.q_indptr[r + 1] - qb);
+        build_query_hash<kMergeThreads>(a.q_indices + qb, a.q_values + qb, nt, a.ix.dim,
+                                        reinterpret_cast<int32_t*>(sbuf), nullptr, a.ix.err, true);
+    }
+    const uint32_t nf = min(__ldcg(ws.fcount + y), ws.fcap);
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    uint64_t* dst = a.final_stage ? sel : ws.top + (size_t)y * ws.top_cap;
+    const uint32_t dcap = a.final_stage ? (uint32_t)kMaxK : ws.top_cap;
+    if (S <= ws.fcap) {
+        const uint64_t* fb = ws.fbuf + (size_t)y * ws.fcap;
+        for (uint32_t i = threadIdx.x; i < nf; i += kMergeThreads) sbuf[i] = __ldcg(fb + i);
+        __syncthreads();
+        auto key_of = [&](int i) -> uint64_t { return sbuf[i]; };
+        const uint64_t T = nf > g ? block_select_threshold<kMergeThreads>(key_of, (int)nf, (int)g, hist256, st) : 0ull;
+        gather_at_least<kMergeThreads>(key_of, nf, T, dst, dcap, &s_n);
+    } else {
+        // a crowded bin at the cut: select over every candidate
+        auto key_of = [&](int i) -> uint64_t { return __ldcg(cand + i); };
+        const uint64_t T = C > g ? block_select_threshold<kMergeThreads>(key_of, (int)C, (int)g, hist256, st) : 0ull;
+        gather_at_least<kMergeThreads>(key_of, C, T, dst, dcap, &s_n);
+    }
     if (a.final_stage) {
-        write_sorted_results<kMergeThreads>(s, (int)min(s_n, (uint32_t)kMaxK), a.k, a.out_ids, a.out_scores, r);
+        write_sorted_results<kMergeThreads>(sel, (int)min(s_n, (uint32_t)kMaxK), a.k, a.out_ids, a.out_scores, r);
     } else if (threadIdx.x == 0) {
-        a.top_count[y] = min(s_n, a.top_cap);
+        ws.top_count[y] = min(s_n, ws.top_cap);
     }
     __syncthreads();
+    // leave the query's counters at zero for the next launch
+    for (int b = threadIdx.x; b < kHistBins; b += kMergeThreads) H[b] = 0;
     if (threadIdx.x == 0) {
-        a.cand_count[y] = 0;
-        a.bound[y] = 0ull;
+        ws.cand_count[y] = 0;
+        ws.fcount[y] = 0;
+        ws.mticket[y] = 0;
     }
 }
 
@@ -348,79 +523,78 @@ struct RerankArgs {
     const int32_t* q_indices;
     const float* q_values;
     int64_t q_first;
-    const uint64_t* top;
-    const uint32_t* top_count;
-    uint32_t top_cap;
-    uint64_t* rr;              // [queries][top_cap]
-    uint32_t* done;            // [queries]
     uint32_t k;
     uint32_t* out_ids;
     float* out_scores;
+    Workspace ws;
 };
 
 __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
     __shared__ int32_t hk[kHashSlots];
     __shared__ float hv[kHashSlots];
     __shared__ uint64_t s[kMaxK];
-    __shared__ uint32_t hist[256];
+    __shared__ uint32_t hist256[256];
     __shared__ uint32_t st[4];
     __shared__ uint32_t s_n;
     __shared__ int s_last;
+    const Workspace& ws = a.ws;
     const uint32_t y = blockIdx.y;
     const int64_t r = a.q_first + y;
-    const int64_t qb = a.q_indptr[r];
-    const int nt = (int)(a.q_indptr[r + 1] - qb);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t g = min(a.top_count[y], a.top_cap);
-    const uint32_t lo = blockIdx.x * kRerankDocsPerBlock;
-    const uint32_t hi = g < lo + kRerankDocsPerBlock ? g : lo + kRerankDocsPerBlock;
-    if (lo < hi) {
+    const uint32_t g = min(ws.top_count[y], ws.top_cap);
+    uint64_t* rr = ws.rr + (size_t)y * ws.top_cap;
+    if (blockIdx.x * kRerankWarps < g) {
+        const int64_t qb = a.q_indptr[r];
+        const int nt = (int)(a.q_indptr[r + 1] - qb);
         build_query_hash<kRerankThreads>(a.q_indices + qb, a.q_values + qb, nt, a.ix.dim, hk, hv, a.ix.err, false);
-        for (uint32_t idx = lo + warp; idx < hi; idx += kRerankThreads / 32) {
-            const uint64_t key = a.top[(size_t)y * a.top_cap + idx];
+        const uint32_t idx = blockIdx.x * kRerankWarps + warp;
+        if (idx < g) {
+            const uint64_t key = ws.top[(size_t)y * ws.top_cap + idx];
             const uint32_t id = key_id(key);
             const int64_t b = a.ix.indptr[id], e = a.ix.indptr[id + 1];
             float acc = 0.0f;
-            for (int64_t p = b + lane; p < e; p += 32) {
-                const float qw = query_weight(hk, hv, __ldg(a.ix.indices + p));
-                acc = fmaf(__ldg(a.ix.values + p), qw, acc);
+            for (int64_t p0 = b; p0 < e; p0 += 128) {
+                int32_t jj[4];
+                float xx[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int64_t p = p0 + u * 32 + lane;
+                    jj[u] = -1;
+                    xx[u] = 0.0f;
+                    if (p < e) {
+                        jj[u] = __ldg(a.ix.indices + p);
+                        xx[u] = __ldg(a.ix.values + p);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (jj[u] >= 0) acc = fmaf(xx[u], query_weight(hk, hv, jj[u]), acc);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-            if (lane == 0) a.rr[(size_t)y * a.top_cap + idx] = result_key(acc, id);
+            if (lane == 0) rr[idx] = result_key(acc, id);
         }
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(a.done + y, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(ws.rticket + y, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const uint64_t* rr = a.rr + (size_t)y * a.top_cap;
-    const int kk = (int)(a.k < g ? a.k : g);
-    auto key_of = [&](int i) -> uint64_t { return __ldcg(rr + i); };
-    uint64_t T = 0;
-    if ((int)g > kk) T = block_select_threshold<kRerankThreads>(key_of, (int)g, kk, hist, st);
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    for (uint32_t base = 0; base < g; base += kRerankThreads) {
-        const uint32_t i = base + threadIdx.x;
-        uint64_t k = 0;
-        bool ok = false;
-        if (i < g) {
-            k = __ldcg(rr + i);
-            ok = k >= T;
-        }
-        const unsigned bal = __ballot_sync(kFull, ok);
-        uint32_t wb = 0;
-        if (lane == 0 && bal) wb = atomicAdd(&s_n, (uint32_t)__popc(bal));
-        wb = __shfl_sync(kFull, wb, 0);
-        if (ok && wb + __popc(bal & lt) < kMaxK) s[wb + __popc(bal & lt)] = k;
+    if (g <= (uint32_t)kMaxK) {
+        for (uint32_t i = threadIdx.x; i < g; i += kRerankThreads) s[i] = __ldcg(rr + i);
+        if (threadIdx.x == 0) s_n = g;
+        __syncthreads();
+    } else {
+        const uint32_t kk = a.k < g ? a.k : g;
+        auto key_of = [&](int i) -> uint64_t { return __ldcg(rr + i); };
+        const uint64_t T = block_select_threshold<kRerankThreads>(key_of, (int)g, (int)kk, hist256, st);
+        gather_at_least<kRerankThreads>(key_of, g, T, s, kMaxK, &s_n);
     }
-    __syncthreads();
     write_sorted_results<kRerankThreads>(s, (int)min(s_n, (uint32_t)kMaxK), a.k, a.out_ids, a.out_scores, r);
-    if (threadIdx.x == 0) a.done[y] = 0;
+    if (threadIdx.x == 0) ws.rticket[y] = 0;
 }
 
 // Rows of an empty index: every slot is padding.
@@ -457,86 +631,99 @@ static void launch_scan_any(int dt, bool qm, const ScanArgs& a, uint32_t sigma, 
             : launch_scan<SINDI_F8E4M3, false>(a, sigma, nq, smem, s);
 }
 
+// Sizes of one search: candidates per query and the buffers that follow.
+struct Plan {
+    bool final_stage;
+    uint32_t g, win_cap, cand_cap, fcap, top_cap, merge_blocks;
+};
+
+static Plan make_plan(const IndexImpl& ix, const sindi_search_params& prm) {
+    Plan p;
+    p.final_stage = prm.gamma == 0;
+    p.g = (uint32_t)std::min<int64_t>(p.final_stage ? prm.k : prm.gamma, ix.n_docs);
+    const uint32_t gw = std::min<uint32_t>(p.g, ix.lambda);
+    p.win_cap = 2 * gw;
+    p.cand_cap = ix.sigma * p.win_cap;
+    uint32_t f = 4096;
+    while (f < 2 * p.g && f < 16384) f <<= 1;
+    p.fcap = f;
+    p.top_cap = p.final_stage ? 1 : p.g;
+    p.merge_blocks = std::max<uint32_t>(1, std::min<uint32_t>(16, p.cand_cap / 8192));
+    return p;
+}
+
+// The launches of one group of nq queries starting at row q0.
+static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& ws, const int64_t* q_indptr,
+                         const int32_t* q_indices, const float* q_values, int64_t q0, uint32_t nq, bool batched,
+                         uint32_t k, uint32_t* out_ids, float* out_scores, cudaStream_t stream,
+                         cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+    static bool merge_configured = false;
+    if (!merge_configured) {
+        SINDI_CUDA(cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8));
+        merge_configured = true;
+    }
+    const DevIndex dix = ix.dev();
+    const size_t scan_smem = (size_t)ix.lambda * sizeof(float);
+    ScanArgs sa{dix, q_indptr, q_indices, q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, ws};
+    if (ev0) SINDI_CUDA(cudaEventRecord(ev0, stream));
+    // query-major grids put the queries of one window next to each other
+    // (shared lists stay in L2); gridDim.y limits sigma to 65535 there
+    launch_scan_any(ix.dtype, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem, stream);
+    if (ev1) SINDI_CUDA(cudaEventRecord(ev1, stream));
+    MergeArgs ma{dix, q_indptr, q_indices, q_values, q0, pl.g, pl.final_stage ? 1 : 0, k, out_ids, out_scores, ws};
+    merge_kernel<<<dim3(pl.merge_blocks, nq), kMergeThreads, (size_t)pl.fcap * 8, stream>>>(ma);
+    SINDI_CUDA(cudaGetLastError());
+    ix.launches += 2;
+    ix.scan_launches += 1;
+    if (!pl.final_stage) {
+        RerankArgs ra{dix, q_indptr, q_indices, q_values, q0, k, out_ids, out_scores, ws};
+        rerank_kernel<<<dim3(ceil_div_u32(pl.g, kRerankWarps), nq), kRerankThreads, 0, stream>>>(ra);
+        SINDI_CUDA(cudaGetLastError());
+        ix.launches += 1;
+    }
+}
+
 sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
                          const float* q_values, int64_t n_queries, const sindi_search_params& prm,
                          uint32_t* out_ids, float* out_scores, cudaStream_t stream) {
-    const int64_t N = ix.n_docs;
     const uint32_t k = prm.k;
     if (n_queries == 0) return SINDI_OK;
-    if (N == 0) {
+    if (ix.n_docs == 0) {
         pad_results_kernel<<<256, 256, 0, stream>>>(out_ids, out_scores, n_queries * (int64_t)k);
         SINDI_CUDA(cudaGetLastError());
         ix.launches++;
         return SINDI_OK;
     }
-    const bool final_stage = prm.gamma == 0;
-    const uint32_t g = (uint32_t)std::min<int64_t>(final_stage ? k : prm.gamma, N);
-    const uint32_t g_window = std::min<uint32_t>(g, ix.lambda);
-    const uint32_t cand_cap = ix.sigma * g_window;
-    const uint32_t top_cap = final_stage ? 1 : g;
-    const size_t per_query = (size_t)cand_cap * 8 + 4 + 8 + (size_t)top_cap * 16 + 8;
+    const Plan pl = make_plan(ix, prm);
     const bool batched = prm.mode == SINDI_MODE_BATCHED;
     int64_t chunk = 1;
     if (batched) {
-        const size_t budget = (size_t)1 << 31;  // 2 GiB of candidate workspace per launch group
+        const size_t budget = (size_t)1 << 31;  // 2 GiB of workspace per launch group
+        const size_t per_query = workspace_bytes(1, pl.cand_cap, pl.fcap, pl.top_cap);
         chunk = std::max<int64_t>(1, std::min<int64_t>(n_queries, (int64_t)(budget / per_query)));
         chunk = std::min<int64_t>(chunk, 65535);
     }
     Pool P{ix.pool, stream};
-    uint64_t* cand = P.alloc<uint64_t>((size_t)cand_cap * chunk);
-    uint32_t* cand_count = P.alloc<uint32_t>(chunk);
-    unsigned long long* bound = P.alloc<unsigned long long>(chunk);
-    uint64_t* top = P.alloc<uint64_t>((size_t)top_cap * chunk);
-    uint32_t* top_count = P.alloc<uint32_t>(chunk);
-    uint64_t* rr = P.alloc<uint64_t>((size_t)top_cap * chunk);
-    uint32_t* done = P.alloc<uint32_t>(chunk);
-    SINDI_CUDA(cudaMemsetAsync(cand_count, 0, 4 * chunk, stream));
-    SINDI_CUDA(cudaMemsetAsync(bound, 0, 8 * chunk, stream));
-    SINDI_CUDA(cudaMemsetAsync(done, 0, 4 * chunk, stream));
+    unsigned char* mem = P.alloc<unsigned char>(workspace_bytes(chunk, pl.cand_cap, pl.fcap, pl.top_cap));
+    const Workspace ws = carve_workspace(mem, chunk, pl.cand_cap, pl.fcap, pl.top_cap);
+    SINDI_CUDA(cudaMemsetAsync(mem, 0, workspace_counter_bytes(chunk), stream));
 
-    const DevIndex dix = ix.dev();
-    const size_t scan_smem = (size_t)ix.lambda * sizeof(float);
     const bool timing = ix.timing.load() != 0;
     std::vector<cudaEvent_t> evs;
-
     for (int64_t q0 = 0; q0 < n_queries; q0 += chunk) {
         const uint32_t nq = (uint32_t)std::min<int64_t>(chunk, n_queries - q0);
-        ScanArgs sa{dix, q_indptr, q_indices, q_values, q0, g, cand, cand_count, bound, cand_cap};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (timing) {
-            cudaEvent_t e0, e1;
             SINDI_CUDA(cudaEventCreate(&e0));
             SINDI_CUDA(cudaEventCreate(&e1));
             evs.push_back(e0);
             evs.push_back(e1);
-            SINDI_CUDA(cudaEventRecord(e0, stream));
         }
-        // query-major grids put the queries of one window next to each other
-        // (shared segments stay in L2); gridDim.y limits sigma to 65535 there
-        launch_scan_any(ix.dtype, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem, stream);
-        if (timing) SINDI_CUDA(cudaEventRecord(evs.back(), stream));
-        MergeArgs ma{dix, q_indptr, q_indices, q_values, q0, g, cand, cand_count, bound, cand_cap,
-                     final_stage ? 1 : 0, k, out_ids, out_scores, top, top_count, top_cap};
-        merge_kernel<<<nq, kMergeThreads, 0, stream>>>(ma);
-        SINDI_CUDA(cudaGetLastError());
-        ix.launches += 2;
-        ix.scan_launches += 1;
-        if (!final_stage) {
-            RerankArgs ra{dix, q_indptr, q_indices, q_values, q0, top, top_count, top_cap, rr, done, k,
-                          out_ids, out_scores};
-            dim3 grid(ceil_div_u32(g, kRerankDocsPerBlock), nq);
-            rerank_kernel<<<grid, kRerankThreads, 0, stream>>>(ra);
-            SINDI_CUDA(cudaGetLastError());
-            ix.launches += 1;
-        }
+        launch_group(ix, pl, ws, q_indptr, q_indices, q_values, q0, nq, batched, k, out_ids, out_scores, stream, e0,
+                     e1);
     }
     ix.queries += (uint64_t)n_queries;
-    P.free(cand);
-    P.free(cand_count);
-    P.free(bound);
-    P.free(top);
-    P.free(top_count);
-    P.free(rr);
-    P.free(done);
+    P.free(mem);
     if (timing) {
         SINDI_CUDA(cudaStreamSynchronize(stream));
         double ms = 0.0;
@@ -582,8 +769,6 @@ static cudaError_t noalloc_scratch_address(int device, unsigned char** out) {
     return cudaSuccess;
 }
 
-static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
                                  const float* q_values, int64_t n_queries, const sindi_search_params& prm,
                                  uint32_t* out_ids, float* out_scores, cudaStream_t stream) {
@@ -593,27 +778,18 @@ sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, c
         set_last_error(std::string("sindi_search_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(ce));
         return SINDI_ERR_CUDA;
     }
-    const int64_t N = ix.n_docs;
     const uint32_t k = prm.k;
     if (n_queries == 0) return SINDI_OK;
-    if (N == 0) {
+    if (ix.n_docs == 0) {
         pad_results_kernel<<<256, 256, 0, stream>>>(out_ids, out_scores, n_queries * (int64_t)k);
         SINDI_CUDA(cudaGetLastError());
         return SINDI_OK;
     }
-    const bool final_stage = prm.gamma == 0;
-    const uint32_t g = (uint32_t)std::min<int64_t>(final_stage ? k : prm.gamma, N);
-    const uint32_t cand_cap = ix.sigma * std::min<uint32_t>(g, ix.lambda);
-    const uint32_t top_cap = final_stage ? 1 : g;
-    // scratch of a group of c queries: six arrays, each 256-byte aligned
-    auto need = [&](int64_t c) {
-        return align256((size_t)cand_cap * 8 * c) + align256(4 * (size_t)c) + align256(8 * (size_t)c) +
-               align256((size_t)top_cap * 8 * c) + align256(4 * (size_t)c) + align256((size_t)top_cap * 8 * c) +
-               align256(4 * (size_t)c);
-    };
-    if (need(1) > kNoAllocScratchBytes) {
-        set_last_error("sindi_search_noalloc: one query needs " + std::to_string(need(1)) +
-                       " bytes of scratch (n_windows * min(candidates, window) * 8 + ...), more than the " +
+    const Plan pl = make_plan(ix, prm);
+    const size_t one = workspace_bytes(1, pl.cand_cap, pl.fcap, pl.top_cap);
+    if (one > kNoAllocScratchBytes) {
+        set_last_error("sindi_search_noalloc: one query needs " + std::to_string(one) +
+                       " bytes of scratch (n_windows * 2 * min(candidates, window) * 8 + ...), more than the " +
                        std::to_string(kNoAllocScratchBytes) + "-byte static scratch area; use sindi_search");
         return SINDI_ERR_UNSUPPORTED;
     }
@@ -621,46 +797,15 @@ sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, c
     int64_t chunk = 1;
     if (batched) {
         chunk = std::min<int64_t>(n_queries, 65535);
-        while (chunk > 1 && need(chunk) > kNoAllocScratchBytes) chunk = std::max<int64_t>(1, chunk / 2);
+        while (chunk > 1 && workspace_bytes(chunk, pl.cand_cap, pl.fcap, pl.top_cap) > kNoAllocScratchBytes)
+            chunk = std::max<int64_t>(1, chunk / 2);
     }
-    unsigned char* q = base;
-    auto carve = [&](size_t bytes) {
-        unsigned char* r = q;
-        q += align256(bytes);
-        return r;
-    };
-    uint64_t* cand = reinterpret_cast<uint64_t*>(carve((size_t)cand_cap * 8 * chunk));
-    uint32_t* cand_count = reinterpret_cast<uint32_t*>(carve(4 * (size_t)chunk));
-    unsigned long long* bound = reinterpret_cast<unsigned long long*>(carve(8 * (size_t)chunk));
-    uint64_t* top = reinterpret_cast<uint64_t*>(carve((size_t)top_cap * 8 * chunk));
-    uint32_t* top_count = reinterpret_cast<uint32_t*>(carve(4 * (size_t)chunk));
-    uint64_t* rr = reinterpret_cast<uint64_t*>(carve((size_t)top_cap * 8 * chunk));
-    uint32_t* done = reinterpret_cast<uint32_t*>(carve(4 * (size_t)chunk));
+    const Workspace ws = carve_workspace(base, chunk, pl.cand_cap, pl.fcap, pl.top_cap);
     // the array keeps the previous call's contents: clear the counters the kernels start from
-    SINDI_CUDA(cudaMemsetAsync(cand_count, 0, 4 * chunk, stream));
-    SINDI_CUDA(cudaMemsetAsync(bound, 0, 8 * chunk, stream));
-    SINDI_CUDA(cudaMemsetAsync(done, 0, 4 * chunk, stream));
-
-    const DevIndex dix = ix.dev();
-    const size_t scan_smem = (size_t)ix.lambda * sizeof(float);
+    SINDI_CUDA(cudaMemsetAsync(base, 0, workspace_counter_bytes(chunk), stream));
     for (int64_t q0 = 0; q0 < n_queries; q0 += chunk) {
         const uint32_t nq = (uint32_t)std::min<int64_t>(chunk, n_queries - q0);
-        ScanArgs sa{dix, q_indptr, q_indices, q_values, q0, g, cand, cand_count, bound, cand_cap};
-        launch_scan_any(ix.dtype, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem, stream);
-        MergeArgs ma{dix, q_indptr, q_indices, q_values, q0, g, cand, cand_count, bound, cand_cap,
-                     final_stage ? 1 : 0, k, out_ids, out_scores, top, top_count, top_cap};
-        merge_kernel<<<nq, kMergeThreads, 0, stream>>>(ma);
-        SINDI_CUDA(cudaGetLastError());
-        ix.launches += 2;
-        ix.scan_launches += 1;
-        if (!final_stage) {
-            RerankArgs ra{dix, q_indptr, q_indices, q_values, q0, top, top_count, top_cap, rr, done, k,
-                          out_ids, out_scores};
-            dim3 grid(ceil_div_u32(g, kRerankDocsPerBlock), nq);
-            rerank_kernel<<<grid, kRerankThreads, 0, stream>>>(ra);
-            SINDI_CUDA(cudaGetLastError());
-            ix.launches += 1;
-        }
+        launch_group(ix, pl, ws, q_indptr, q_indices, q_values, q0, nq, batched, k, out_ids, out_scores, stream);
     }
     ix.queries += (uint64_t)n_queries;
     return SINDI_OK;
