@@ -40,7 +40,7 @@ namespace sindi {
 constexpr int kScanThreads = 512;
 constexpr int kScanWarps = kScanThreads / 32;
 constexpr int kTermChunk = kScanThreads;   // query terms staged per pass (one per thread)
-constexpr int kChunkU = 4;                 // postings per lane in one warp chunk
+constexpr int kChunkU = 8;                 // postings per lane in one warp chunk
 constexpr int kChunkLen = 32 * kChunkU;    // postings of one warp chunk (one list only)
 constexpr int kHistBits = 12;
 constexpr int kHistBins = 1 << kHistBits;  // bins on the top 12 bits of a score key
@@ -109,6 +109,13 @@ __device__ __forceinline__ float load_value(const void* pval, uint32_t p) {
         return __half2float(__half(__nv_cvt_fp8_to_halfraw(c, __NV_E4M3)));
     }
 }
+
+// Programmatic dependent launch. Kernels after the first of a search call are
+// launched so that they may start while the previous kernel still runs; each
+// waits here before it touches memory the previous kernels write, and lets
+// the next kernel launch early.
+__device__ __forceinline__ void wait_previous_kernels() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_kernel() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 // last t in [0, n) with pre[t] <= f (pre[0] = 0 <= f)
 __device__ __forceinline__ int term_of(const uint32_t* pre, int n, uint32_t f) {
@@ -187,6 +194,7 @@ __global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a
     const uint32_t lambda = ix.lambda;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+    allow_next_kernel();
     const int64_t qb = a.q_indptr[r];
     const int nt = (int)(a.q_indptr[r + 1] - qb);
 
@@ -264,6 +272,7 @@ __global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a
     __syncthreads();
     uint32_t lo = bw;
     uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
+    wait_previous_kernels();  // the workspace is free from here on
     if (a.use_partial) {
         // g slots already emitted at or above bin bp prove the answer lies there
         block_find_bin([&](int b) { return __ldcg(H + b); }, a.g, red, st);
@@ -277,8 +286,8 @@ __global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a
     }
     for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) hist[b] = 0;
     __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
+    // count this thread's slots, reserve the block's range with one atomic, write
+    uint32_t mine = 0;
     for (int base = 0; base < n_eff; base += kScanThreads) {
         const int i = base + threadIdx.x;
         uint64_t k = 0;
@@ -287,20 +296,26 @@ __global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a
             k = key_of(i);
             ok = k >= thr;
         }
-        const unsigned bal = __ballot_sync(kFull, ok);
-        uint32_t wbase = 0;
-        if (lane == 0 && bal) wbase = atomicAdd(a.ws.cand_count + y, (uint32_t)__popc(bal));
-        wbase = __shfl_sync(kFull, wbase, 0);
+        mine += ok ? 1u : 0u;
         const int bin = ok ? (int)(k >> kKeyBinShift) : -1;
         const unsigned peers = __match_any_sync(kFull, bin);
-        if (ok) {
-            const uint32_t pos = wbase + (uint32_t)__popc(bal & lt);
+        if (ok && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    }
+    uint32_t total;
+    uint32_t pos = block_exclusive_sum<uint32_t, kScanThreads>(mine, &total, red);
+    if (threadIdx.x == 0) st[0] = total ? atomicAdd(a.ws.cand_count + y, total) : 0u;
+    __syncthreads();
+    pos += st[0];
+    uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
+    for (int i = threadIdx.x; i < n_eff && mine; i += kScanThreads) {
+        const uint64_t k = key_of(i);
+        if (k >= thr) {
             if (pos < a.ws.cand_cap) cand[pos] = k;
             else atomicOr(ix.err, kErrCandOverflow);
-            if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+            pos++;
+            mine--;
         }
     }
-    __syncthreads();
     for (int b = threadIdx.x; b < kHistBins; b += kScanThreads)
         if (hist[b]) atomicAdd(H + b, hist[b]);
 }
@@ -433,6 +448,8 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
     const Workspace& ws = a.ws;
     const uint32_t y = blockIdx.y;
     const int64_t r = a.q_first + y;
+    wait_previous_kernels();
+    allow_next_kernel();
     const uint32_t C = min(ws.cand_count[y], ws.cand_cap);
     const uint32_t g = a.g < C ? a.g : C;
     const uint64_t* cand = ws.cand + (size_t)y * ws.cand_cap;
@@ -442,12 +459,13 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
     block_find_bin([&](int b) { return H[b]; }, g, red, st);
     const uint32_t bstar = st[0];
     const uint32_t S = st[1] + st[2];  // candidates in bins >= bstar
+    if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
     {
+        // this block's slice: survivors gathered in shared memory, then one
+        // reservation in the query's filter buffer
         const uint32_t per = (C + gridDim.x - 1) / gridDim.x;
         const uint32_t lo = blockIdx.x * per, hi = min(C, lo + per);
-        const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
-        uint64_t* fb = ws.fbuf + (size_t)y * ws.fcap;
         for (uint32_t base = lo; base < hi; base += kMergeThreads * 4) {
             uint64_t kk[4];
 #pragma unroll
@@ -458,17 +476,20 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const uint32_t i = base + (uint32_t)(u * kMergeThreads) + threadIdx.x;
-                const bool ok = i < hi && (uint32_t)(kk[u] >> kKeyBinShift) >= bstar;
-                const unsigned bal = __ballot_sync(kFull, ok);
-                uint32_t wb = 0;
-                if (lane == 0 && bal) wb = atomicAdd(ws.fcount + y, (uint32_t)__popc(bal));
-                wb = __shfl_sync(kFull, wb, 0);
-                if (ok) {
-                    const uint32_t pos = wb + (uint32_t)__popc(bal & lt);
-                    if (pos < ws.fcap) fb[pos] = kk[u];
+                if (i < hi && (uint32_t)(kk[u] >> kKeyBinShift) >= bstar) {
+                    const uint32_t pos = atomicAdd(&s_n, 1u);
+                    if (pos < ws.fcap) sbuf[pos] = kk[u];
                 }
             }
         }
+        __syncthreads();
+        const uint32_t n_local = min(s_n, ws.fcap);
+        if (threadIdx.x == 0) st[0] = n_local ? atomicAdd(ws.fcount + y, n_local) : 0u;
+        __syncthreads();
+        const uint32_t at = st[0];
+        uint64_t* fb = ws.fbuf + (size_t)y * ws.fcap;
+        for (uint32_t i = threadIdx.x; i < n_local; i += kMergeThreads)
+            if (at + i < ws.fcap) fb[at + i] = sbuf[i];
     }
     __threadfence();
     __syncthreads();
@@ -541,39 +562,41 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
     const uint32_t y = blockIdx.y;
     const int64_t r = a.q_first + y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t g = min(ws.top_count[y], ws.top_cap);
-    uint64_t* rr = ws.rr + (size_t)y * ws.top_cap;
-    if (blockIdx.x * kRerankWarps < g) {
+    allow_next_kernel();
+    {
         const int64_t qb = a.q_indptr[r];
         const int nt = (int)(a.q_indptr[r + 1] - qb);
         build_query_hash<kRerankThreads>(a.q_indices + qb, a.q_values + qb, nt, a.ix.dim, hk, hv, a.ix.err, false);
-        const uint32_t idx = blockIdx.x * kRerankWarps + warp;
-        if (idx < g) {
-            const uint64_t key = ws.top[(size_t)y * ws.top_cap + idx];
-            const uint32_t id = key_id(key);
-            const int64_t b = a.ix.indptr[id], e = a.ix.indptr[id + 1];
-            float acc = 0.0f;
-            for (int64_t p0 = b; p0 < e; p0 += 128) {
-                int32_t jj[4];
-                float xx[4];
+    }
+    wait_previous_kernels();
+    const uint32_t g = min(ws.top_count[y], ws.top_cap);
+    uint64_t* rr = ws.rr + (size_t)y * ws.top_cap;
+    const uint32_t idx = blockIdx.x * kRerankWarps + warp;
+    if (idx < g) {
+        const uint64_t key = ws.top[(size_t)y * ws.top_cap + idx];
+        const uint32_t id = key_id(key);
+        const int64_t b = a.ix.indptr[id], e = a.ix.indptr[id + 1];
+        float acc = 0.0f;
+        for (int64_t p0 = b; p0 < e; p0 += 128) {
+            int32_t jj[4];
+            float xx[4];
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int64_t p = p0 + u * 32 + lane;
-                    jj[u] = -1;
-                    xx[u] = 0.0f;
-                    if (p < e) {
-                        jj[u] = __ldg(a.ix.indices + p);
-                        xx[u] = __ldg(a.ix.values + p);
-                    }
+            for (int u = 0; u < 4; u++) {
+                const int64_t p = p0 + u * 32 + lane;
+                jj[u] = -1;
+                xx[u] = 0.0f;
+                if (p < e) {
+                    jj[u] = __ldg(a.ix.indices + p);
+                    xx[u] = __ldg(a.ix.values + p);
                 }
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (jj[u] >= 0) acc = fmaf(xx[u], query_weight(hk, hv, jj[u]), acc);
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-            if (lane == 0) rr[idx] = result_key(acc, id);
+            for (int u = 0; u < 4; u++)
+                if (jj[u] >= 0) acc = fmaf(xx[u], query_weight(hk, hv, jj[u]), acc);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (lane == 0) rr[idx] = result_key(acc, id);
     }
     __threadfence();
     __syncthreads();
@@ -608,29 +631,6 @@ __global__ void pad_results_kernel(uint32_t* out_ids, float* out_scores, int64_t
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <int DT, bool QM>
-static void launch_scan(const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem, cudaStream_t s) {
-    static bool configured = false;  // per instantiation; the attribute is per function
-    if (!configured) {
-        SINDI_CUDA(cudaFuncSetAttribute(scan_window_kernel<DT, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(kMaxWindow * sizeof(float))));
-        configured = true;
-    }
-    dim3 grid = QM ? dim3(nq, sigma) : dim3(sigma, nq);
-    scan_window_kernel<DT, QM><<<grid, kScanThreads, smem, s>>>(a);
-    SINDI_CUDA(cudaGetLastError());
-}
-
-static void launch_scan_any(int dt, bool qm, const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem,
-                            cudaStream_t s) {
-    if (dt == SINDI_F32) qm ? launch_scan<SINDI_F32, true>(a, sigma, nq, smem, s)
-                            : launch_scan<SINDI_F32, false>(a, sigma, nq, smem, s);
-    else if (dt == SINDI_F16) qm ? launch_scan<SINDI_F16, true>(a, sigma, nq, smem, s)
-                                 : launch_scan<SINDI_F16, false>(a, sigma, nq, smem, s);
-    else qm ? launch_scan<SINDI_F8E4M3, true>(a, sigma, nq, smem, s)
-            : launch_scan<SINDI_F8E4M3, false>(a, sigma, nq, smem, s);
-}
-
 // Sizes of one search: candidates per query and the buffers that follow.
 struct Plan {
     bool final_stage;
@@ -652,10 +652,53 @@ static Plan make_plan(const IndexImpl& ix, const sindi_search_params& prm) {
     return p;
 }
 
-// The launches of one group of nq queries starting at row q0.
+// Launches `kern` on `stream`; with `pdl` the launch may begin while the
+// previous kernel on the stream still runs (the kernel waits for it where it
+// must, see wait_previous_kernels).
+template <typename... Params, typename... Args>
+static void launch_kernel(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream, bool pdl,
+                          Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    SINDI_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
+
+template <int DT, bool QM>
+static void launch_scan_t(const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem, cudaStream_t s, bool pdl) {
+    static bool configured = false;  // per instantiation; the attribute is per function
+    if (!configured) {
+        SINDI_CUDA(cudaFuncSetAttribute(scan_window_kernel<DT, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(kMaxWindow * sizeof(float))));
+        configured = true;
+    }
+    dim3 grid = QM ? dim3(nq, sigma) : dim3(sigma, nq);
+    launch_kernel(scan_window_kernel<DT, QM>, grid, dim3(kScanThreads), smem, s, pdl, a);
+}
+
+static void launch_scan_pdl(int dt, bool qm, const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem,
+                            cudaStream_t s, bool pdl) {
+    if (dt == SINDI_F32) qm ? launch_scan_t<SINDI_F32, true>(a, sigma, nq, smem, s, pdl)
+                            : launch_scan_t<SINDI_F32, false>(a, sigma, nq, smem, s, pdl);
+    else if (dt == SINDI_F16) qm ? launch_scan_t<SINDI_F16, true>(a, sigma, nq, smem, s, pdl)
+                                 : launch_scan_t<SINDI_F16, false>(a, sigma, nq, smem, s, pdl);
+    else qm ? launch_scan_t<SINDI_F8E4M3, true>(a, sigma, nq, smem, s, pdl)
+            : launch_scan_t<SINDI_F8E4M3, false>(a, sigma, nq, smem, s, pdl);
+}
+
+// The launches of one group of nq queries starting at row q0. `*chained` is
+// false for the first launch of a search call (it follows the caller's work
+// and must not overlap it) and true afterwards.
 static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& ws, const int64_t* q_indptr,
                          const int32_t* q_indices, const float* q_values, int64_t q0, uint32_t nq, bool batched,
-                         uint32_t k, uint32_t* out_ids, float* out_scores, cudaStream_t stream,
+                         uint32_t k, uint32_t* out_ids, float* out_scores, cudaStream_t stream, bool* chained,
                          cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
     static bool merge_configured = false;
     if (!merge_configured) {
@@ -668,19 +711,21 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
     if (ev0) SINDI_CUDA(cudaEventRecord(ev0, stream));
     // query-major grids put the queries of one window next to each other
     // (shared lists stay in L2); gridDim.y limits sigma to 65535 there
-    launch_scan_any(ix.dtype, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem, stream);
+    launch_scan_pdl(ix.dtype, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem, stream,
+                    *chained && !ev0);
     if (ev1) SINDI_CUDA(cudaEventRecord(ev1, stream));
     MergeArgs ma{dix, q_indptr, q_indices, q_values, q0, pl.g, pl.final_stage ? 1 : 0, k, out_ids, out_scores, ws};
-    merge_kernel<<<dim3(pl.merge_blocks, nq), kMergeThreads, (size_t)pl.fcap * 8, stream>>>(ma);
-    SINDI_CUDA(cudaGetLastError());
+    launch_kernel(merge_kernel, dim3(pl.merge_blocks, nq), dim3(kMergeThreads), (size_t)pl.fcap * 8, stream,
+                  !ev1, ma);
     ix.launches += 2;
     ix.scan_launches += 1;
     if (!pl.final_stage) {
         RerankArgs ra{dix, q_indptr, q_indices, q_values, q0, k, out_ids, out_scores, ws};
-        rerank_kernel<<<dim3(ceil_div_u32(pl.g, kRerankWarps), nq), kRerankThreads, 0, stream>>>(ra);
-        SINDI_CUDA(cudaGetLastError());
+        launch_kernel(rerank_kernel, dim3(ceil_div_u32(pl.g, kRerankWarps), nq), dim3(kRerankThreads), 0, stream,
+                      true, ra);
         ix.launches += 1;
     }
+    *chained = true;
 }
 
 sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
@@ -710,6 +755,7 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
 
     const bool timing = ix.timing.load() != 0;
     std::vector<cudaEvent_t> evs;
+    bool chained = false;
     for (int64_t q0 = 0; q0 < n_queries; q0 += chunk) {
         const uint32_t nq = (uint32_t)std::min<int64_t>(chunk, n_queries - q0);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -719,8 +765,8 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
             evs.push_back(e0);
             evs.push_back(e1);
         }
-        launch_group(ix, pl, ws, q_indptr, q_indices, q_values, q0, nq, batched, k, out_ids, out_scores, stream, e0,
-                     e1);
+        launch_group(ix, pl, ws, q_indptr, q_indices, q_values, q0, nq, batched, k, out_ids, out_scores, stream,
+                     &chained, e0, e1);
     }
     ix.queries += (uint64_t)n_queries;
     P.free(mem);
@@ -803,9 +849,11 @@ sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, c
     const Workspace ws = carve_workspace(base, chunk, pl.cand_cap, pl.fcap, pl.top_cap);
     // the array keeps the previous call's contents: clear the counters the kernels start from
     SINDI_CUDA(cudaMemsetAsync(base, 0, workspace_counter_bytes(chunk), stream));
+    bool chained = false;
     for (int64_t q0 = 0; q0 < n_queries; q0 += chunk) {
         const uint32_t nq = (uint32_t)std::min<int64_t>(chunk, n_queries - q0);
-        launch_group(ix, pl, ws, q_indptr, q_indices, q_values, q0, nq, batched, k, out_ids, out_scores, stream);
+        launch_group(ix, pl, ws, q_indptr, q_indices, q_values, q0, nq, batched, k, out_ids, out_scores, stream,
+                     &chained);
     }
     ix.queries += (uint64_t)n_queries;
     return SINDI_OK;
