@@ -37,14 +37,17 @@
 
 namespace sindi {
 
-constexpr int kScanThreads = 512;
-constexpr int kScanWarps = kScanThreads / 32;
-constexpr int kTermChunk = kScanThreads;   // query terms staged per pass (one per thread)
+constexpr int kScanThreadsPlain = 1024;    // one query: few windows, so more warps per window
+constexpr int kScanThreadsBatched = 512;   // many windows: two blocks per SM overlap their phases
+constexpr int kMaxScanWarps = kScanThreadsPlain / 32;
+constexpr int kChunkTable = 2048;          // chunks mapped to their list by a table (then a search)
 constexpr int kChunkU = 8;                 // postings per lane in one warp chunk
 constexpr int kChunkLen = 32 * kChunkU;    // postings of one warp chunk (one list only)
 constexpr int kHistBits = 12;
 constexpr int kHistBins = 1 << kHistBits;  // bins on the top 12 bits of a score key
 constexpr int kKeyBinShift = 64 - kHistBits;
+constexpr int kSubBits = 8;                // second-level bins inside the cut bin
+constexpr int kSubBins = 1 << kSubBits;
 constexpr int kMergeThreads = 512;
 constexpr int kRerankThreads = 256;
 constexpr int kRerankWarps = kRerankThreads / 32;
@@ -127,21 +130,23 @@ __device__ __forceinline__ int term_of(const uint32_t* pre, int n, uint32_t f) {
     return lo;
 }
 
-// Block-wide (512 threads): the bin holding the g-th largest element of a
-// 4096-bin histogram read through `get`, counting from the top bin. Leaves the
-// bin in st[0] (0 when the total is below g), the count strictly above it in
-// st[1], its own count in st[2] and the histogram total in st[3].
-template <typename Get>
+// Block-wide: the bin holding the g-th largest element of a BINS-bin
+// histogram read through `get`, counting from the top bin. Leaves the bin in
+// st[0] (0 when the total is below g), the count strictly above it in st[1],
+// its own count in st[2] and the histogram total in st[3]. red: [BLOCK/32 + 1].
+template <int BINS, int BLOCK, typename Get>
 __device__ void block_find_bin(const Get& get, uint32_t g, uint32_t* red, uint32_t* st) {
-    uint32_t c8[8];
+    constexpr int BPT = (BINS + BLOCK - 1) / BLOCK;  // bins per thread, from the top
+    uint32_t c[BPT];
     uint32_t s = 0;
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-        c8[j] = get(kHistBins - 1 - 8 * (int)threadIdx.x - j);
-        s += c8[j];
+    for (int j = 0; j < BPT; j++) {
+        const int b = BINS - 1 - BPT * (int)threadIdx.x - j;
+        c[j] = b >= 0 ? get(b) : 0u;
+        s += c[j];
     }
     uint32_t tot;
-    const uint32_t ex = block_exclusive_sum<uint32_t, kScanThreads>(s, &tot, red);
+    const uint32_t ex = block_exclusive_sum<uint32_t, BLOCK>(s, &tot, red);
     if (threadIdx.x == 0) {
         st[0] = 0;
         st[1] = tot;
@@ -152,13 +157,13 @@ __device__ void block_find_bin(const Get& get, uint32_t g, uint32_t* red, uint32
     if (ex < g && g <= ex + s) {
         uint32_t above = ex;
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            if (above < g && g <= above + c8[j]) {
-                st[0] = (uint32_t)(kHistBins - 1 - 8 * (int)threadIdx.x - j);
+        for (int j = 0; j < BPT; j++) {
+            if (above < g && g <= above + c[j]) {
+                st[0] = (uint32_t)(BINS - 1 - BPT * (int)threadIdx.x - j);
                 st[1] = above;
-                st[2] = c8[j];
+                st[2] = c[j];
             }
-            above += c8[j];
+            above += c[j];
         }
     }
     __syncthreads();
@@ -176,14 +181,19 @@ struct ScanArgs {
     Workspace ws;
 };
 
-template <int DT, bool QUERY_MAJOR>
-__global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a) {
+template <int DT, bool QUERY_MAJOR, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanArgs a) {
+    constexpr int kScanThreads = BLOCK;
+    constexpr int kScanWarps = BLOCK / 32;
+    constexpr int kTermChunk = BLOCK;   // query terms staged per pass (one per thread)
     extern __shared__ float A[];                    // [lambda]
     __shared__ uint32_t hist[kHistBins];
+    __shared__ uint32_t hist2[kSubBins];
     __shared__ uint32_t t_start[kTermChunk];
     __shared__ uint32_t t_end[kTermChunk];
     __shared__ uint32_t c_pre[kTermChunk + 1];
     __shared__ float t_w[kTermChunk];
+    __shared__ uint16_t c_term[kChunkTable];
     __shared__ uint32_t red[kScanWarps + 1];
     __shared__ uint32_t st[4];
 
@@ -200,6 +210,7 @@ __global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a
 
     for (uint32_t m = threadIdx.x; m < lambda; m += kScanThreads) A[m] = 0.0f;
     for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) hist[b] = 0;
+    if (threadIdx.x < kSubBins) hist2[threadIdx.x] = 0;
 
     for (int c0 = 0; c0 < nt; c0 += kTermChunk) {
         const int nc = min(kTermChunk, nt - c0);
@@ -225,12 +236,15 @@ __global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a
         }
         uint32_t total;
         const uint32_t excl = block_exclusive_sum<uint32_t, kScanThreads>(nch, &total, red);
-        if ((int)threadIdx.x < nc) c_pre[threadIdx.x] = excl;
+        if ((int)threadIdx.x < nc) {
+            c_pre[threadIdx.x] = excl;
+            for (uint32_t c = excl; c < excl + nch && c < (uint32_t)kChunkTable; c++) c_term[c] = (uint16_t)threadIdx.x;
+        }
         __syncthreads();
 
         // scatter-add: a warp takes chunks of one list, lanes interleaved (coalesced)
         for (uint32_t c = (uint32_t)warp; c < total; c += kScanWarps) {
-            const int t = term_of(c_pre, nc, c);
+            const int t = c < (uint32_t)kChunkTable ? (int)c_term[c] : term_of(c_pre, nc, c);
             const uint32_t p0 = t_start[t] + (c - c_pre[t]) * (uint32_t)kChunkLen;
             const uint32_t pe = t_end[t];
             const float wq = t_w[t];
@@ -259,6 +273,7 @@ __global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a
     const int n_eff = (int)(rest < (int64_t)lambda ? rest : (int64_t)lambda);
     const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
     auto key_of = [&](int i) -> uint64_t { return result_key(A[i], (uint32_t)(gbase + i)); };
+    // level 1: top 12 bits of the score key
     for (int base = 0; base < n_eff; base += kScanThreads) {
         const int i = base + threadIdx.x;
         const int bin = i < n_eff ? (int)(float_order_bits(A[i]) >> (32 - kHistBits)) : -1;
@@ -266,40 +281,48 @@ __global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a
         if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    block_find_bin([&](int b) { return hist[b]; }, g_w, red, st);
+    block_find_bin<kHistBins, kScanThreads>([&](int b) { return hist[b]; }, g_w, red, st);
     const uint32_t bw = st[0];
-    const uint32_t c_bw = st[1] + st[2];  // slots in bins >= bw
+    const uint32_t above_bw = st[1];
     __syncthreads();
-    uint32_t lo = bw;
+    // level 2: the next 8 bits, inside bin bw only
+    for (int i = threadIdx.x; i < n_eff; i += kScanThreads) {
+        const uint32_t k32 = float_order_bits(A[i]);
+        if ((k32 >> (32 - kHistBits)) == bw) atomicAdd(&hist2[(k32 >> (32 - kHistBits - kSubBits)) & (kSubBins - 1)], 1u);
+    }
+    __syncthreads();
+    block_find_bin<kSubBins, kScanThreads>([&](int b) { return hist2[b]; }, g_w - above_bw, red, st);
+    const uint32_t bw2 = st[0];
+    const uint32_t c_cut = above_bw + st[1] + st[2];   // slots at or above the 20-bit cut
+    __syncthreads();
+    // the 20-bit cut as a 64-bit key threshold
+    uint64_t thr = ((uint64_t)((bw << kSubBits) | bw2)) << (64 - kHistBits - kSubBits);
+    bool exact = c_cut > a.win_cap;
     uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
     wait_previous_kernels();  // the workspace is free from here on
     if (a.use_partial) {
-        // g slots already emitted at or above bin bp prove the answer lies there
-        block_find_bin([&](int b) { return __ldcg(H + b); }, a.g, red, st);
-        if (st[3] >= a.g && st[0] > lo) lo = st[0];
+        // g slots already emitted at or above a bin prove the answer lies there
+        block_find_bin<kHistBins, kScanThreads>([&](int b) { return __ldcg(H + b); }, a.g, red, st);
+        const uint32_t bp = st[3] >= a.g ? st[0] : 0u;
         __syncthreads();
+        if (bp > bw) {
+            thr = (uint64_t)bp << kKeyBinShift;
+            exact = false;
+        }
     }
-    uint64_t thr = (uint64_t)lo << kKeyBinShift;
-    if (lo == bw && c_bw > a.win_cap) {
-        // ties crowd the cut bin: exact best g_w of the window
+    if (exact) {
+        // ties crowd the cut: exact best g_w of the window
         thr = block_select_threshold<kScanThreads>(key_of, n_eff, (int)g_w, t_start, st);
     }
-    for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) hist[b] = 0;
-    __syncthreads();
-    // count this thread's slots, reserve the block's range with one atomic, write
-    uint32_t mine = 0;
-    for (int base = 0; base < n_eff; base += kScanThreads) {
-        const int i = base + threadIdx.x;
-        uint64_t k = 0;
-        bool ok = false;
-        if (i < n_eff) {
-            k = key_of(i);
-            ok = k >= thr;
-        }
-        mine += ok ? 1u : 0u;
-        const int bin = ok ? (int)(k >> kKeyBinShift) : -1;
-        const unsigned peers = __match_any_sync(kFull, bin);
-        if (ok && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    // emit keys >= thr: count, reserve the block's range with one atomic, write
+    uint32_t mine = 0, mask = 0;
+    {
+        int j = 0;
+        for (int i = threadIdx.x; i < n_eff; i += kScanThreads, j++)
+            if (key_of(i) >= thr) {
+                mine++;
+                mask |= 1u << j;
+            }
     }
     uint32_t total;
     uint32_t pos = block_exclusive_sum<uint32_t, kScanThreads>(mine, &total, red);
@@ -307,17 +330,27 @@ __global__ void __launch_bounds__(kScanThreads, 2) scan_window_kernel(ScanArgs a
     __syncthreads();
     pos += st[0];
     uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
-    for (int i = threadIdx.x; i < n_eff && mine; i += kScanThreads) {
-        const uint64_t k = key_of(i);
-        if (k >= thr) {
-            if (pos < a.ws.cand_cap) cand[pos] = k;
-            else atomicOr(ix.err, kErrCandOverflow);
-            pos++;
-            mine--;
+    while (mask) {
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int i = (int)threadIdx.x + j * kScanThreads;
+        if (pos < a.ws.cand_cap) cand[pos] = key_of(i);
+        else atomicOr(ix.err, kErrCandOverflow);
+        pos++;
+    }
+    // what was emitted, per 12-bit bin, into the query's histogram: every
+    // bin above the cut bin in full, the rest of the emitted slots in it
+    const uint32_t tb = (uint32_t)(thr >> kKeyBinShift);
+    uint32_t above_mine = 0;
+    for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) {
+        if ((uint32_t)b > tb && hist[b]) {
+            above_mine += hist[b];
+            atomicAdd(H + b, hist[b]);
         }
     }
-    for (int b = threadIdx.x; b < kHistBins; b += kScanThreads)
-        if (hist[b]) atomicAdd(H + b, hist[b]);
+    uint32_t above;
+    (void)block_exclusive_sum<uint32_t, kScanThreads>(above_mine, &above, red);
+    if (threadIdx.x == 0 && total > above) atomicAdd(H + tb, total - above);
 }
 
 // ---------------------------------------------------------------------------
@@ -440,7 +473,7 @@ struct MergeArgs {
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
     extern __shared__ uint64_t sbuf[];          // [fcap]
     __shared__ uint64_t sel[kMaxK];
-    __shared__ uint32_t red[kScanWarps + 1];
+    __shared__ uint32_t red[kMaxScanWarps + 1];
     __shared__ uint32_t st[4];
     __shared__ uint32_t hist256[256];
     __shared__ uint32_t s_n;
@@ -456,7 +489,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
     uint32_t* H = ws.hist + (size_t)y * kHistBins;
 
     // bin of the g-th best candidate; every candidate below it is out
-    block_find_bin([&](int b) { return H[b]; }, g, red, st);
+    block_find_bin<kHistBins, kMergeThreads>([&](int b) { return H[b]; }, g, red, st);
     const uint32_t bstar = st[0];
     const uint32_t S = st[1] + st[2];  // candidates in bins >= bstar
     if (threadIdx.x == 0) s_n = 0;
@@ -671,26 +704,34 @@ static void launch_kernel(void (*kern)(Params...), dim3 grid, dim3 block, size_t
     SINDI_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
 }
 
-template <int DT, bool QM>
+template <int DT, bool QM, int BLOCK>
 static void launch_scan_t(const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem, cudaStream_t s, bool pdl) {
     static bool configured = false;  // per instantiation; the attribute is per function
     if (!configured) {
-        SINDI_CUDA(cudaFuncSetAttribute(scan_window_kernel<DT, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SINDI_CUDA(cudaFuncSetAttribute(scan_window_kernel<DT, QM, BLOCK>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)(kMaxWindow * sizeof(float))));
         configured = true;
     }
     dim3 grid = QM ? dim3(nq, sigma) : dim3(sigma, nq);
-    launch_kernel(scan_window_kernel<DT, QM>, grid, dim3(kScanThreads), smem, s, pdl, a);
+    launch_kernel(scan_window_kernel<DT, QM, BLOCK>, grid, dim3(BLOCK), smem, s, pdl, a);
 }
 
-static void launch_scan_pdl(int dt, bool qm, const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem,
-                            cudaStream_t s, bool pdl) {
-    if (dt == SINDI_F32) qm ? launch_scan_t<SINDI_F32, true>(a, sigma, nq, smem, s, pdl)
-                            : launch_scan_t<SINDI_F32, false>(a, sigma, nq, smem, s, pdl);
-    else if (dt == SINDI_F16) qm ? launch_scan_t<SINDI_F16, true>(a, sigma, nq, smem, s, pdl)
-                                 : launch_scan_t<SINDI_F16, false>(a, sigma, nq, smem, s, pdl);
-    else qm ? launch_scan_t<SINDI_F8E4M3, true>(a, sigma, nq, smem, s, pdl)
-            : launch_scan_t<SINDI_F8E4M3, false>(a, sigma, nq, smem, s, pdl);
+// Plain schedules (one query) take window-major grids of 1024-thread blocks;
+// batched schedules take query-major grids of 512-thread blocks.
+template <int DT>
+static void launch_scan_dt(bool batched, bool qm, const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem,
+                           cudaStream_t s, bool pdl) {
+    if (!batched) launch_scan_t<DT, false, kScanThreadsPlain>(a, sigma, nq, smem, s, pdl);
+    else if (qm) launch_scan_t<DT, true, kScanThreadsBatched>(a, sigma, nq, smem, s, pdl);
+    else launch_scan_t<DT, false, kScanThreadsBatched>(a, sigma, nq, smem, s, pdl);
+}
+
+static void launch_scan_pdl(int dt, bool batched, bool qm, const ScanArgs& a, uint32_t sigma, uint32_t nq,
+                            size_t smem, cudaStream_t s, bool pdl) {
+    if (dt == SINDI_F32) launch_scan_dt<SINDI_F32>(batched, qm, a, sigma, nq, smem, s, pdl);
+    else if (dt == SINDI_F16) launch_scan_dt<SINDI_F16>(batched, qm, a, sigma, nq, smem, s, pdl);
+    else launch_scan_dt<SINDI_F8E4M3>(batched, qm, a, sigma, nq, smem, s, pdl);
 }
 
 // The launches of one group of nq queries starting at row q0. `*chained` is
@@ -711,7 +752,7 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
     if (ev0) SINDI_CUDA(cudaEventRecord(ev0, stream));
     // query-major grids put the queries of one window next to each other
     // (shared lists stay in L2); gridDim.y limits sigma to 65535 there
-    launch_scan_pdl(ix.dtype, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem, stream,
+    launch_scan_pdl(ix.dtype, batched, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem, stream,
                     *chained && !ev0);
     if (ev1) SINDI_CUDA(cudaEventRecord(ev1, stream));
     MergeArgs ma{dix, q_indptr, q_indices, q_values, q0, pl.g, pl.final_stage ? 1 : 0, k, out_ids, out_scores, ws};
