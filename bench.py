@@ -48,7 +48,10 @@ def parse():
     p.add_argument("--window", type=int, default=0, help="0 = the workload's window")
     p.add_argument("--queries", type=int, default=0, help="0 = the workload's query count")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
-    p.add_argument("--no-forms", action="store_true", help="skip the batched / low-precision side lines")
+    p.add_argument("--no-forms", action="store_true", help="skip the batched / low-precision / serving side lines")
+    p.add_argument("--serve-load", type=float, default=0.5,
+                   help="serving leg: offered load as a fraction of the batched schedule's QPS")
+    p.add_argument("--serve-seconds", type=float, default=4.0)
     return p.parse_args()
 
 
@@ -196,6 +199,45 @@ def postings_touched(seg, sigma, dim, qp, qx):
 
 
 # ---------------------------------------------------------------------------
+def serve_open_loop(sindi, idx, rows, k, gamma, offered_qps, seconds, seed=7):
+    """Open-loop Poisson arrivals into the continuous-batching server; latency submit -> results on host."""
+    import threading
+
+    rng = np.random.default_rng(seed)
+    n = max(1, int(offered_qps * seconds))
+    gaps = rng.exponential(1.0 / offered_qps, n)
+    tickets = [None] * n
+    lat = [None] * n
+    with sindi.Server(idx, k=k, gamma=gamma, max_batch=128, max_slots=8, max_wait_us=200) as srv:
+        srv.stats(reset=True)
+
+        def poller():
+            for i in range(n):
+                while tickets[i] is None:
+                    time.sleep(0.0001)
+                res = srv.poll(tickets[i], wait_ms=-1)
+                lat[i] = res[2]
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        due = t0
+        for i in range(n):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                pass
+            qi, qv = rows[i % len(rows)]
+            tickets[i] = srv.submit(qi, qv)
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    l = np.array(lat)
+    return {"offered_qps": offered_qps, "achieved_qps": n / wall, "requests": n,
+            "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99)),
+            "max_ms": float(l.max()), "mean_batch": st["mean_batch"], "slots": st["n_slots"],
+            "peak_in_flight": st["peak_in_flight"]}
+
+
 def cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, budget_s, gpu_ids=None, k=None):
     """The oracle as it stands, single-threaded, on a bounded sample of the workload's queries.
 
@@ -411,6 +453,12 @@ def main():
                 lp.check()
                 forms[dt + "_" + args.mode] = {"qps": qps, "_ids": oi.cpu().numpy().view(np.uint32)}
 
+    serving = None
+    if not args.no_forms and rank == 0:
+        rows = [(qx[qp[r]:qp[r + 1]], qv[qp[r]:qp[r + 1]]) for r in range(nq)]
+        base = forms.get("batched", {}).get("qps", value)
+        serving = serve_open_loop(sindi, idx, rows, w.k, w.gamma, args.serve_load * base, args.serve_seconds)
+
     # ---- CPU baseline (oracle) + recall against FP64 exact, rank 0 only
     cpu = None
     recall = None
@@ -466,6 +514,7 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clocks,
         "forms": forms,
+        "serving": serving,
         "scan_source_sha256": sha,
     }
     print(json.dumps(line), flush=True)

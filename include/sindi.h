@@ -187,6 +187,64 @@ sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_ind
                                   const float* q_values, int64_t n_queries, const sindi_search_params* params,
                                   uint32_t* out_ids, float* out_scores, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving (continuous batching). The paper's algorithm is per query
+ * (Algorithm 4); the server runs it for a stream of independent requests.
+ * A worker thread inside the library takes queued requests in arrival order,
+ * forms micro-batches of at most max_batch queries and starts each batch as
+ * soon as a device slot is free. A slot is one CUDA stream with its own
+ * pinned staging buffers, device query/result buffers and search workspace,
+ * all allocated when the server is created. So requests that arrive while
+ * others run are admitted as slots free up, and up to n_slots batches overlap
+ * on the device. The index stays resident and is shared by all slots.
+ * ------------------------------------------------------------------------- */
+typedef struct sindi_server sindi_server;
+
+typedef struct {
+    uint32_t max_batch;        /* queries per micro-batch, 1..4096 (0 = 256)               */
+    uint32_t max_slots;        /* batches in flight on the device, 1..64 (0 = 4)           */
+    uint32_t max_query_nnz;    /* longest accepted query, 1..2048 (0 = 512)                */
+    uint32_t max_wait_us;      /* how long a partial batch may wait for more requests while
+                                  every slot is busy anyway (0 = do not wait)              */
+    uint64_t memory_budget;    /* device bytes the slots may take (0 = no limit). Slots are
+                                  admitted while they fit: fewer than max_slots if needed;
+                                  SINDI_ERR_OOM if not even one fits                       */
+    sindi_search_params search;/* k, gamma, beta of every request (mode is ignored)        */
+} sindi_server_params;
+
+typedef struct {
+    uint64_t submitted, completed, failed, batches;
+    uint32_t n_slots;          /* slots admitted by the memory budget                      */
+    uint32_t peak_in_flight;   /* most batches seen on the device at once                  */
+    uint64_t slot_bytes;       /* device bytes of one slot                                 */
+    double mean_batch;         /* queries per batch                                        */
+    double p50_ms, p99_ms, max_ms; /* request latency, submit -> results on the host,
+                                  over requests completed since the last stats reset       */
+} sindi_server_stats_t;
+
+/* Create a server over `index` (which must outlive it). */
+sindi_status sindi_server_create(const sindi_index* index, const sindi_server_params* params, sindi_server** out);
+
+/* Queue one query: nnz entries (host arrays, copied before the call returns).
+   *ticket identifies the request for sindi_server_poll. SINDI_ERR_INVALID_ARG
+   if nnz exceeds max_query_nnz or the server is shutting down. */
+sindi_status sindi_server_submit(sindi_server* server, const int32_t* q_indices, const float* q_values, int32_t nnz,
+                                 uint64_t* ticket);
+
+/* Wait up to wait_ms (0 = just look, < 0 = no limit) for a request. When it is
+   done, copies its k ids and scores (as sindi_search writes one row) into the
+   host buffers, sets *latency_ms if not NULL, forgets the ticket and returns
+   SINDI_OK or the request's own error status. Returns SINDI_ERR_TIMEOUT while
+   it is still running, SINDI_ERR_INVALID_ARG for an unknown ticket. */
+sindi_status sindi_server_poll(sindi_server* server, uint64_t ticket, int32_t wait_ms, uint32_t* ids, float* scores,
+                               double* latency_ms);
+
+/* Counters and latency percentiles; reset = 1 clears the latency record and counters. */
+sindi_status sindi_server_stats(sindi_server* server, sindi_server_stats_t* out, int reset);
+
+/* Stop accepting requests, finish the ones queued or in flight, free everything. */
+void sindi_server_destroy(sindi_server* server);
+
 /* Synchronise `stream`, then return (and clear) the device error word of the
    index as a status: SINDI_ERR_INVALID_DATA if a malformed query or document
    was seen since the last check, SINDI_ERR_TIMEOUT if a bounded wait gave up. */

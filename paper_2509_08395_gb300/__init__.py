@@ -7,6 +7,7 @@ from .sindi import (  # noqa: F401
     DTYPES,
     MODES,
     Index,
+    Server,
     SindiError,
     load,
     sindi_build,
@@ -18,6 +19,11 @@ from .sindi import (  # noqa: F401
     sindi_reset_stats,
     sindi_search,
     sindi_search_noalloc,
+    sindi_server_create,
+    sindi_server_destroy,
+    sindi_server_poll,
+    sindi_server_stats,
+    sindi_server_submit,
     sindi_set_timing,
     sindi_version,
 )

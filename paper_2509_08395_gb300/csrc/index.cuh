@@ -79,6 +79,15 @@ sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, c
                                  const float* q_values, int64_t n_queries, const sindi_search_params& prm,
                                  uint32_t* out_ids, float* out_scores, cudaStream_t stream);
 
+// Workspace bytes of a search that launches `queries_per_launch` queries together.
+size_t search_workspace_bytes(const IndexImpl& ix, const sindi_search_params& prm, int64_t queries_per_launch);
+
+// The search of search_impl, with its working memory in [ws_base, ws_base + ws_bytes).
+sindi_status search_in_workspace(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
+                                 const float* q_values, int64_t n_queries, const sindi_search_params& prm,
+                                 uint32_t* out_ids, float* out_scores, cudaStream_t stream, void* ws_base,
+                                 size_t ws_bytes);
+
 }  // namespace sindi
 
 struct sindi_index {

@@ -900,4 +900,48 @@ sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, c
     return SINDI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Search in a workspace the caller owns (the serving loop keeps one per slot).
+// ---------------------------------------------------------------------------
+size_t search_workspace_bytes(const IndexImpl& ix, const sindi_search_params& prm, int64_t queries_per_launch) {
+    const Plan pl = make_plan(ix, prm);
+    return workspace_bytes(std::max<int64_t>(1, queries_per_launch), pl.cand_cap, pl.fcap, pl.top_cap);
+}
+
+sindi_status search_in_workspace(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
+                                 const float* q_values, int64_t n_queries, const sindi_search_params& prm,
+                                 uint32_t* out_ids, float* out_scores, cudaStream_t stream, void* ws_base,
+                                 size_t ws_bytes) {
+    const uint32_t k = prm.k;
+    if (n_queries == 0) return SINDI_OK;
+    if (ix.n_docs == 0) {
+        pad_results_kernel<<<256, 256, 0, stream>>>(out_ids, out_scores, n_queries * (int64_t)k);
+        SINDI_CUDA(cudaGetLastError());
+        return SINDI_OK;
+    }
+    const Plan pl = make_plan(ix, prm);
+    if (workspace_bytes(1, pl.cand_cap, pl.fcap, pl.top_cap) > ws_bytes) {
+        set_last_error("workspace too small for one query");
+        return SINDI_ERR_OOM;
+    }
+    const bool batched = prm.mode == SINDI_MODE_BATCHED;
+    int64_t chunk = 1;
+    if (batched) {
+        chunk = std::min<int64_t>(n_queries, 65535);
+        while (chunk > 1 && workspace_bytes(chunk, pl.cand_cap, pl.fcap, pl.top_cap) > ws_bytes)
+            chunk = std::max<int64_t>(1, chunk / 2);
+    }
+    unsigned char* base = static_cast<unsigned char*>(ws_base);
+    const Workspace ws = carve_workspace(base, chunk, pl.cand_cap, pl.fcap, pl.top_cap);
+    SINDI_CUDA(cudaMemsetAsync(base, 0, workspace_counter_bytes(chunk), stream));
+    bool chained = false;
+    for (int64_t q0 = 0; q0 < n_queries; q0 += chunk) {
+        const uint32_t nq = (uint32_t)std::min<int64_t>(chunk, n_queries - q0);
+        launch_group(ix, pl, ws, q_indptr, q_indices, q_values, q0, nq, batched, k, out_ids, out_scores, stream,
+                     &chained);
+    }
+    ix.queries += (uint64_t)n_queries;
+    return SINDI_OK;
+}
+
 }  // namespace sindi

@@ -54,6 +54,19 @@ class sindi_stats_t(ctypes.Structure):
                 ("scan_ms", ctypes.c_double), ("scan_timed", ctypes.c_uint64)]
 
 
+class sindi_server_params(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("max_slots", ctypes.c_uint32), ("max_query_nnz", ctypes.c_uint32),
+                ("max_wait_us", ctypes.c_uint32), ("memory_budget", ctypes.c_uint64),
+                ("search", sindi_search_params)]
+
+
+class sindi_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("n_slots", ctypes.c_uint32), ("peak_in_flight", ctypes.c_uint32),
+                ("slot_bytes", ctypes.c_uint64), ("mean_batch", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -74,6 +87,14 @@ _SIGS = {
     "sindi_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_stats_t)]),
     "sindi_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "sindi_index_free": (None, [ctypes.c_void_p]),
+    "sindi_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_server_params),
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "sindi_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+    "sindi_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "sindi_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_server_stats_t), ctypes.c_int]),
+    "sindi_server_destroy": (None, [ctypes.c_void_p]),
     "sindi_last_error": (ctypes.c_char_p, []),
     "sindi_version": (ctypes.c_char_p, []),
 }
@@ -250,6 +271,89 @@ class Index:
     def close(self):
         if getattr(self, "handle", None):
             sindi_index_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---- serving (continuous batching) -----------------------------------------------
+def sindi_server_create(index: int, k: int, gamma: int = 0, beta: float = 1.0, max_batch: int = 0,
+                        max_slots: int = 0, max_query_nnz: int = 0, max_wait_us: int = 0,
+                        memory_budget: int = 0) -> int:
+    prm = sindi_server_params(max_batch=max_batch, max_slots=max_slots, max_query_nnz=max_query_nnz,
+                              max_wait_us=max_wait_us, memory_budget=memory_budget,
+                              search=sindi_search_params(k=k, gamma=gamma, beta=beta, mode=SINDI_MODE_BATCHED,
+                                                         reserved=0))
+    out = ctypes.c_void_p()
+    _check(load().sindi_server_create(ctypes.c_void_p(index), ctypes.byref(prm), ctypes.byref(out)),
+           "sindi_server_create")
+    return out.value
+
+
+def sindi_server_submit(server: int, q_indices, q_values) -> int:
+    qi = np.ascontiguousarray(q_indices, dtype=np.int32)
+    qv = np.ascontiguousarray(q_values, dtype=np.float32)
+    t = ctypes.c_uint64()
+    _check(load().sindi_server_submit(ctypes.c_void_p(server), qi.ctypes.data, qv.ctypes.data, len(qi),
+                                      ctypes.byref(t)), "sindi_server_submit")
+    return t.value
+
+
+def sindi_server_poll(server: int, ticket: int, k: int, wait_ms: int = -1):
+    """(ids, scores, latency_ms) once the request is done; None while it is still running."""
+    ids = np.empty(k, np.uint32)
+    sc = np.empty(k, np.float32)
+    lat = ctypes.c_double()
+    st = load().sindi_server_poll(ctypes.c_void_p(server), ctypes.c_uint64(ticket), int(wait_ms), ids.ctypes.data,
+                                  sc.ctypes.data, ctypes.byref(lat))
+    if st == SINDI_ERR_TIMEOUT:
+        return None
+    _check(st, "sindi_server_poll")
+    return ids, sc, lat.value
+
+
+def sindi_server_stats(server: int, reset: bool = False) -> dict:
+    s = sindi_server_stats_t()
+    _check(load().sindi_server_stats(ctypes.c_void_p(server), ctypes.byref(s), 1 if reset else 0),
+           "sindi_server_stats")
+    return {f: getattr(s, f) for f, _ in sindi_server_stats_t._fields_}
+
+
+def sindi_server_destroy(server: int) -> None:
+    if server:
+        load().sindi_server_destroy(ctypes.c_void_p(server))
+
+
+class Server:
+    """Continuous-batching request loop over an Index (owns the C handle)."""
+
+    def __init__(self, index: "Index", k: int, gamma: int = 0, **kw):
+        self.index = index  # keeps the index alive
+        self.k = k
+        self.handle = sindi_server_create(index.handle, k, gamma, **kw)
+
+    def submit(self, q_indices, q_values) -> int:
+        return sindi_server_submit(self.handle, q_indices, q_values)
+
+    def poll(self, ticket: int, wait_ms: int = -1):
+        return sindi_server_poll(self.handle, ticket, self.k, wait_ms)
+
+    def stats(self, reset: bool = False) -> dict:
+        return sindi_server_stats(self.handle, reset)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sindi_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
