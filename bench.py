@@ -442,6 +442,22 @@ def main():
         other = "batched" if args.mode == "plain" else "plain"
         forms[other] = {"qps": timed(lambda: step(other), args.steps)}
         forms[other]["ids_equal_to_main"] = float(np.mean(out_ids.cpu().numpy().view(np.uint32) == gpu_ids))
+        if nq <= 65535:
+            # the batched search captured once as a CUDA graph: one graph launch per step
+            with sindi.Plan(idx, *q_dev, k=w.k, gamma=w.gamma) as plan:
+                forms["batched_graph"] = {"qps": timed(lambda: plan.launch(stream.cuda_stream), args.steps)}
+                gids = plan.out[0].cpu().numpy().view(np.uint32)
+                forms["batched_graph"]["ids_equal_to_main"] = float(np.mean(gids == gpu_ids))
+        # the autotuner on the same documents and queries
+        from paper_2509_08395_gb300 import autotune
+
+        dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
+        tuned = autotune.autotune(dip, dix, dv, w.dim, *q_dev, k=w.k, alpha=w.alpha, recall_target=0.99)
+        del dip, dix, dv
+        forms["autotuned"] = dict(tuned["choice"] or {}, seconds=tuned["seconds"],
+                                  recall_vs="GPU exact search (alpha = 1, gamma = 0)")
+        if not tuned["choice"]:
+            forms["autotuned"]["table"] = tuned["table"]
         for dt in ("f16", "f8"):
             dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
             with sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=w.alpha, value_dtype=dt) as lp:
@@ -451,7 +467,12 @@ def main():
                 qps = timed(lambda: lp.search(*q_dev, k=w.k, gamma=w.gamma, mode=args.mode, out=(oi, os_)),
                             args.steps)
                 lp.check()
-                forms[dt + "_" + args.mode] = {"qps": qps, "_ids": oi.cpu().numpy().view(np.uint32)}
+                # coarse scores alone (gamma = 0) of the first queries, for the quantisation error
+                n_err = min(8, nq)
+                cq = [torch.from_numpy(a).to(dev) for a in (qp[: n_err + 1], qx[: qp[n_err]], qv[: qp[n_err]])]
+                _, csc = lp.search(*cq, k=w.k, gamma=0)
+                forms[dt + "_" + args.mode] = {"qps": qps, "_ids": oi.cpu().numpy().view(np.uint32),
+                                               "_sc": os_.cpu().numpy(), "_coarse": csc.cpu().numpy()}
 
     serving = None
     if not args.no_forms and rank == 0:
@@ -475,10 +496,24 @@ def main():
             Q = oracle.Dataset(qp, qx, qv, w.dim)
             step_r = max(1, nq // 40)
             truth = {r: oracle.brute_force(D, Q, r, w.k)[0] for r in range(0, nq, step_r)}
+            I32 = oracle.Index(D, window=w.window, alpha=w.alpha)
             for name, f in forms.items():
                 if "_ids" in f:
                     f["recall_at_k"] = float(np.mean([oracle.recall(f["_ids"][r], t) for r, t in truth.items()]))
-                    del f["_ids"]
+                    # score error against FP64: coarse (quantised postings vs unquantised FP64 Algorithm 2,
+                    # rank by rank) and final (FP32 reorder vs exact FP64 delta of the same document)
+                    ce, fe = 0.0, 0.0
+                    for r in range(f["_coarse"].shape[0]):
+                        _, osc = I32.search(Q, r, k=w.k, gamma=0)
+                        n = len(osc)
+                        ce = max(ce, float(np.max(np.abs(f["_coarse"][r, :n] - osc) / np.abs(osc))))
+                        for i, sc in zip(f["_ids"][r], f["_sc"][r]):
+                            ex = oracle.inner_product(D, int(i), Q, r)
+                            fe = max(fe, abs(float(sc) - ex) / abs(ex))
+                    f["coarse_max_rel_err_vs_fp64"] = ce
+                    f["final_max_rel_err_vs_fp64"] = fe
+                    for key in ("_ids", "_sc", "_coarse"):
+                        del f[key]
     if rank != 0:
         return
     clocks = clk.summary()

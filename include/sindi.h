@@ -91,7 +91,8 @@ typedef struct {
                               top-k is the answer), else k <= gamma <= 8192        */
     double beta;           /* query pruning ratio in (0, 1]; 1 = off              */
     uint32_t mode;         /* sindi_mode                                           */
-    uint32_t reserved;     /* must be 0                                            */
+    uint32_t block_threads;/* threads per window-scan block: 256, 512 or 1024;
+                              0 = the schedule's default (1024 plain, 512 batched) */
 } sindi_search_params;
 
 typedef struct {
@@ -186,6 +187,25 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
 sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
                                   const float* q_values, int64_t n_queries, const sindi_search_params* params,
                                   uint32_t* out_ids, float* out_scores, void* stream);
+
+/*
+ * Graph-captured batched search. Records the whole search of one query batch
+ * (the batched schedule of sindi_search: every query of the batch in shared
+ * launches) as a CUDA graph, so that each later run is one graph launch.
+ *   The query and output device buffers given here are baked into the graph;
+ *   the caller may change their contents between launches, but not their
+ *   addresses, n_queries or the total number of query entries beyond what the
+ *   buffers hold. Device pointers only; 1 <= n_queries <= 65535.
+ *   The plan owns its workspace (allocated here). Launches of one plan must
+ *   not overlap each other on the GPU.
+ */
+typedef struct sindi_plan sindi_plan;
+sindi_status sindi_plan_create(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
+                               const float* q_values, int64_t n_queries, const sindi_search_params* params,
+                               uint32_t* out_ids, float* out_scores, sindi_plan** out);
+/* Queue one run of the plan on `stream`. */
+sindi_status sindi_plan_launch(sindi_plan* plan, void* stream);
+void sindi_plan_free(sindi_plan* plan);
 
 /* ---------------------------------------------------------------------------
  * Serving (continuous batching). The paper's algorithm is per query

@@ -7,6 +7,7 @@ from .sindi import (  # noqa: F401
     DTYPES,
     MODES,
     Index,
+    Plan,
     Server,
     SindiError,
     load,
@@ -16,6 +17,9 @@ from .sindi import (  # noqa: F401
     sindi_index_export,
     sindi_index_free,
     sindi_index_info,
+    sindi_plan_create,
+    sindi_plan_free,
+    sindi_plan_launch,
     sindi_reset_stats,
     sindi_search,
     sindi_search_noalloc,

@@ -79,6 +79,9 @@ sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, c
                                  const float* q_values, int64_t n_queries, const sindi_search_params& prm,
                                  uint32_t* out_ids, float* out_scores, cudaStream_t stream);
 
+// Sets the shared-memory limits of the search kernels on `device` (once).
+void configure_search_kernels(int device);
+
 // Workspace bytes of a search that launches `queries_per_launch` queries together.
 size_t search_workspace_bytes(const IndexImpl& ix, const sindi_search_params& prm, int64_t queries_per_launch);
 

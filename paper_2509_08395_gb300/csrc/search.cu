@@ -315,28 +315,23 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
         thr = block_select_threshold<kScanThreads>(key_of, n_eff, (int)g_w, t_start, st);
     }
     // emit keys >= thr: count, reserve the block's range with one atomic, write
-    uint32_t mine = 0, mask = 0;
-    {
-        int j = 0;
-        for (int i = threadIdx.x; i < n_eff; i += kScanThreads, j++)
-            if (key_of(i) >= thr) {
-                mine++;
-                mask |= 1u << j;
-            }
-    }
+    uint32_t mine = 0;
+    for (int i = threadIdx.x; i < n_eff; i += kScanThreads)
+        if (key_of(i) >= thr) mine++;
     uint32_t total;
     uint32_t pos = block_exclusive_sum<uint32_t, kScanThreads>(mine, &total, red);
     if (threadIdx.x == 0) st[0] = total ? atomicAdd(a.ws.cand_count + y, total) : 0u;
     __syncthreads();
     pos += st[0];
     uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
-    while (mask) {
-        const int j = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int i = (int)threadIdx.x + j * kScanThreads;
-        if (pos < a.ws.cand_cap) cand[pos] = key_of(i);
-        else atomicOr(ix.err, kErrCandOverflow);
-        pos++;
+    for (int i = threadIdx.x; i < n_eff && mine; i += kScanThreads) {
+        const uint64_t key = key_of(i);
+        if (key >= thr) {
+            if (pos < a.ws.cand_cap) cand[pos] = key;
+            else atomicOr(ix.err, kErrCandOverflow);
+            pos++;
+            mine--;
+        }
     }
     // what was emitted, per 12-bit bin, into the query's histogram: every
     // bin above the cut bin in full, the rest of the emitted slots in it
@@ -667,7 +662,7 @@ __global__ void pad_results_kernel(uint32_t* out_ids, float* out_scores, int64_t
 // Sizes of one search: candidates per query and the buffers that follow.
 struct Plan {
     bool final_stage;
-    uint32_t g, win_cap, cand_cap, fcap, top_cap, merge_blocks;
+    uint32_t g, win_cap, cand_cap, fcap, top_cap, merge_blocks, block;
 };
 
 static Plan make_plan(const IndexImpl& ix, const sindi_search_params& prm) {
@@ -682,6 +677,7 @@ static Plan make_plan(const IndexImpl& ix, const sindi_search_params& prm) {
     p.fcap = f;
     p.top_cap = p.final_stage ? 1 : p.g;
     p.merge_blocks = std::max<uint32_t>(1, std::min<uint32_t>(16, p.cand_cap / 8192));
+    p.block = prm.block_threads;
     return p;
 }
 
@@ -705,33 +701,65 @@ static void launch_kernel(void (*kern)(Params...), dim3 grid, dim3 block, size_t
 }
 
 template <int DT, bool QM, int BLOCK>
+static void allow_window_smem() {
+    SINDI_CUDA(cudaFuncSetAttribute(scan_window_kernel<DT, QM, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kMaxWindow * sizeof(float))));
+}
+
+template <int DT>
+static void allow_window_smem_dt() {
+    allow_window_smem<DT, false, 256>();
+    allow_window_smem<DT, false, 512>();
+    allow_window_smem<DT, false, 1024>();
+    allow_window_smem<DT, true, 256>();
+    allow_window_smem<DT, true, 512>();
+    allow_window_smem<DT, true, 1024>();
+}
+
+// Shared-memory limits of every search kernel, set once per device before the
+// first launch (and before any stream capture, where they cannot be set).
+void configure_search_kernels(int device) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), device) != done.end()) return;
+    allow_window_smem_dt<SINDI_F32>();
+    allow_window_smem_dt<SINDI_F16>();
+    allow_window_smem_dt<SINDI_F8E4M3>();
+    SINDI_CUDA(cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8));
+    done.push_back(device);
+}
+
+template <int DT, bool QM, int BLOCK>
 static void launch_scan_t(const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem, cudaStream_t s, bool pdl) {
-    static bool configured = false;  // per instantiation; the attribute is per function
-    if (!configured) {
-        SINDI_CUDA(cudaFuncSetAttribute(scan_window_kernel<DT, QM, BLOCK>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(kMaxWindow * sizeof(float))));
-        configured = true;
-    }
     dim3 grid = QM ? dim3(nq, sigma) : dim3(sigma, nq);
     launch_kernel(scan_window_kernel<DT, QM, BLOCK>, grid, dim3(BLOCK), smem, s, pdl, a);
 }
 
-// Plain schedules (one query) take window-major grids of 1024-thread blocks;
-// batched schedules take query-major grids of 512-thread blocks.
-template <int DT>
-static void launch_scan_dt(bool batched, bool qm, const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem,
-                           cudaStream_t s, bool pdl) {
-    if (!batched) launch_scan_t<DT, false, kScanThreadsPlain>(a, sigma, nq, smem, s, pdl);
-    else if (qm) launch_scan_t<DT, true, kScanThreadsBatched>(a, sigma, nq, smem, s, pdl);
-    else launch_scan_t<DT, false, kScanThreadsBatched>(a, sigma, nq, smem, s, pdl);
+// Plain schedules (one query) take window-major grids, by default of
+// 1024-thread blocks; batched schedules take query-major grids (window-major
+// when sigma exceeds the grid's y limit), by default of 512-thread blocks.
+template <int DT, bool QM>
+static void launch_scan_block(uint32_t block, const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem,
+                              cudaStream_t s, bool pdl) {
+    if (block == 256) launch_scan_t<DT, QM, 256>(a, sigma, nq, smem, s, pdl);
+    else if (block == 512) launch_scan_t<DT, QM, 512>(a, sigma, nq, smem, s, pdl);
+    else launch_scan_t<DT, QM, 1024>(a, sigma, nq, smem, s, pdl);
 }
 
-static void launch_scan_pdl(int dt, bool batched, bool qm, const ScanArgs& a, uint32_t sigma, uint32_t nq,
-                            size_t smem, cudaStream_t s, bool pdl) {
-    if (dt == SINDI_F32) launch_scan_dt<SINDI_F32>(batched, qm, a, sigma, nq, smem, s, pdl);
-    else if (dt == SINDI_F16) launch_scan_dt<SINDI_F16>(batched, qm, a, sigma, nq, smem, s, pdl);
-    else launch_scan_dt<SINDI_F8E4M3>(batched, qm, a, sigma, nq, smem, s, pdl);
+template <int DT>
+static void launch_scan_dt(uint32_t block, bool batched, bool qm, const ScanArgs& a, uint32_t sigma, uint32_t nq,
+                           size_t smem, cudaStream_t s, bool pdl) {
+    if (block == 0) block = batched ? kScanThreadsBatched : kScanThreadsPlain;
+    if (qm) launch_scan_block<DT, true>(block, a, sigma, nq, smem, s, pdl);
+    else launch_scan_block<DT, false>(block, a, sigma, nq, smem, s, pdl);
+}
+
+static void launch_scan_pdl(int dt, uint32_t block, bool batched, bool qm, const ScanArgs& a, uint32_t sigma,
+                            uint32_t nq, size_t smem, cudaStream_t s, bool pdl) {
+    if (dt == SINDI_F32) launch_scan_dt<SINDI_F32>(block, batched, qm, a, sigma, nq, smem, s, pdl);
+    else if (dt == SINDI_F16) launch_scan_dt<SINDI_F16>(block, batched, qm, a, sigma, nq, smem, s, pdl);
+    else launch_scan_dt<SINDI_F8E4M3>(block, batched, qm, a, sigma, nq, smem, s, pdl);
 }
 
 // The launches of one group of nq queries starting at row q0. `*chained` is
@@ -741,19 +769,15 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
                          const int32_t* q_indices, const float* q_values, int64_t q0, uint32_t nq, bool batched,
                          uint32_t k, uint32_t* out_ids, float* out_scores, cudaStream_t stream, bool* chained,
                          cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
-    static bool merge_configured = false;
-    if (!merge_configured) {
-        SINDI_CUDA(cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8));
-        merge_configured = true;
-    }
+    configure_search_kernels(ix.device);
     const DevIndex dix = ix.dev();
     const size_t scan_smem = (size_t)ix.lambda * sizeof(float);
     ScanArgs sa{dix, q_indptr, q_indices, q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, ws};
     if (ev0) SINDI_CUDA(cudaEventRecord(ev0, stream));
     // query-major grids put the queries of one window next to each other
     // (shared lists stay in L2); gridDim.y limits sigma to 65535 there
-    launch_scan_pdl(ix.dtype, batched, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem, stream,
-                    *chained && !ev0);
+    launch_scan_pdl(ix.dtype, pl.block, batched, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem,
+                    stream, *chained && !ev0);
     if (ev1) SINDI_CUDA(cudaEventRecord(ev1, stream));
     MergeArgs ma{dix, q_indptr, q_indices, q_values, q0, pl.g, pl.final_stage ? 1 : 0, k, out_ids, out_scores, ws};
     launch_kernel(merge_kernel, dim3(pl.merge_blocks, nq), dim3(kMergeThreads), (size_t)pl.fcap * 8, stream,

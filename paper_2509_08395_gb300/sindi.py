@@ -39,7 +39,7 @@ class sindi_build_params(ctypes.Structure):
 
 class sindi_search_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_uint32), ("gamma", ctypes.c_uint32), ("beta", ctypes.c_double),
-                ("mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("mode", ctypes.c_uint32), ("block_threads", ctypes.c_uint32)]
 
 
 class sindi_index_info_t(ctypes.Structure):
@@ -87,6 +87,11 @@ _SIGS = {
     "sindi_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_stats_t)]),
     "sindi_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "sindi_index_free": (None, [ctypes.c_void_p]),
+    "sindi_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.POINTER(sindi_search_params), ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "sindi_plan_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sindi_plan_free": (None, [ctypes.c_void_p]),
     "sindi_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_server_params),
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "sindi_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
@@ -164,10 +169,10 @@ def sindi_build(indptr, indices, values, n_docs: int, dim: int, window: int = 0,
 
 
 def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
-                 gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None) -> None:
+                 gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None, block: int = 0) -> None:
     """Algorithm 4 for every query row; writes out_ids (uint32/int32) and out_scores (float32), [n_queries, k]."""
     lib = load()
-    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], reserved=0)
+    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block))
     st = lib.sindi_search(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                           _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm), _ptr(out_ids, np.uint32),
                           _ptr(out_scores, np.float32), _stream(stream, q_indptr, out_ids))
@@ -175,11 +180,12 @@ def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_
 
 
 def sindi_search_noalloc(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
-                         gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None) -> None:
+                         gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None,
+                         block: int = 0) -> None:
     """sindi_search for callers that cannot allocate device memory: all working memory comes from the library's
     static 8 MiB device array. Device tensors only; calls that overlap on the GPU race on that array."""
     lib = load()
-    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], reserved=0)
+    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block))
     st = lib.sindi_search_noalloc(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                                   _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm),
                                   _ptr(out_ids, np.uint32), _ptr(out_scores, np.float32),
@@ -248,7 +254,7 @@ class Index:
         self.info = sindi_index_info(self.handle)
 
     def search(self, q_indptr, q_indices, q_values, k: int, gamma: int = 0, beta: float = 1.0,
-               mode: str = "plain", out=None, stream=None):
+               mode: str = "plain", out=None, stream=None, block: int = 0):
         """Returns (ids, scores) of shape [n_queries, k]; device tensors for device queries."""
         n_q = (q_indptr.shape[0] if hasattr(q_indptr, "shape") else len(q_indptr)) - 1
         if out is None:
@@ -259,7 +265,8 @@ class Index:
                 dev = q_indptr.device
                 out = (torch.empty((n_q, k), dtype=torch.int32, device=dev),
                        torch.empty((n_q, k), dtype=torch.float32, device=dev))
-        sindi_search(self.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma, beta, mode, stream)
+        sindi_search(self.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma, beta, mode, stream,
+                     block)
         return out
 
     def check(self, stream=None):
@@ -286,6 +293,68 @@ class Index:
         self.close()
 
 
+# ---- graph-captured batched search -------------------------------------------------
+def sindi_plan_create(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
+                      gamma: int = 0, beta: float = 1.0, block: int = 0) -> int:
+    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=SINDI_MODE_BATCHED, block_threads=int(block))
+    out = ctypes.c_void_p()
+    _check(load().sindi_plan_create(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
+                                    _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm),
+                                    _ptr(out_ids, np.uint32), _ptr(out_scores, np.float32), ctypes.byref(out)),
+           "sindi_plan_create")
+    return out.value
+
+
+def sindi_plan_launch(plan: int, stream=None) -> None:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().sindi_plan_launch(ctypes.c_void_p(plan), stream), "sindi_plan_launch")
+
+
+def sindi_plan_free(plan: int) -> None:
+    if plan:
+        load().sindi_plan_free(ctypes.c_void_p(plan))
+
+
+class Plan:
+    """A batched search of fixed device buffers, captured once as a CUDA graph."""
+
+    def __init__(self, index: "Index", q_indptr, q_indices, q_values, k: int, gamma: int = 0, out=None,
+                 block: int = 0):
+        import torch
+        self.index = index
+        n_q = q_indptr.shape[0] - 1
+        self.inputs = (q_indptr, q_indices, q_values)
+        if out is None:
+            out = (torch.empty((n_q, k), dtype=torch.int32, device=q_indptr.device),
+                   torch.empty((n_q, k), dtype=torch.float32, device=q_indptr.device))
+        self.out = out
+        self.handle = sindi_plan_create(index.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma,
+                                        block=block)
+
+    def launch(self, stream=None):
+        sindi_plan_launch(self.handle, stream)
+        return self.out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sindi_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 # ---- serving (continuous batching) -----------------------------------------------
 def sindi_server_create(index: int, k: int, gamma: int = 0, beta: float = 1.0, max_batch: int = 0,
                         max_slots: int = 0, max_query_nnz: int = 0, max_wait_us: int = 0,
@@ -293,7 +362,7 @@ def sindi_server_create(index: int, k: int, gamma: int = 0, beta: float = 1.0, m
     prm = sindi_server_params(max_batch=max_batch, max_slots=max_slots, max_query_nnz=max_query_nnz,
                               max_wait_us=max_wait_us, memory_budget=memory_budget,
                               search=sindi_search_params(k=k, gamma=gamma, beta=beta, mode=SINDI_MODE_BATCHED,
-                                                         reserved=0))
+                                                         block_threads=0))
     out = ctypes.c_void_p()
     _check(load().sindi_server_create(ctypes.c_void_p(index), ctypes.byref(prm), ctypes.byref(out)),
            "sindi_server_create")

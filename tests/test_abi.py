@@ -52,7 +52,7 @@ def test_calls_without_device_fail_cleanly(lib):
     L = sindi.load()
     out = ctypes.c_void_p()
     assert L.sindi_build(None, None, None, 10, 4, None, None, ctypes.byref(out)) == sindi.SINDI_ERR_INVALID_ARG
-    prm = sindi.sindi_search_params(k=0, gamma=0, beta=1.0, mode=0, reserved=0)
+    prm = sindi.sindi_search_params(k=0, gamma=0, beta=1.0, mode=0, block_threads=0)
     assert L.sindi_search(None, None, None, None, 1, ctypes.byref(prm), None, None, None) == \
         sindi.SINDI_ERR_INVALID_ARG
     assert b"NULL" in L.sindi_last_error()

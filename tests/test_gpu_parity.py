@@ -120,6 +120,24 @@ def test_pruned_coarse_topk_parity(pruned_small, window, mode):
         check_ranked(ids[r], sc[r], oi, os_, 100, D.n, what=f"query {r}")
 
 
+@pytest.mark.parametrize("block", [256, 512, 1024])
+def test_largest_window_every_block_shape(block):
+    """lambda = 32,768 (the largest window): a window spans up to 128 passes of a 256-thread block."""
+    w = datagen.WORKLOADS["pruned-1m"].scaled(n_docs=70_000, n_queries=12)
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    D, Q = oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+    I = oracle.Index(D, window=32768, alpha=0.5)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=32768, alpha=0.5) as idx:
+        for mode in ("plain", "batched"):
+            ids, sc = idx.search(dev(qp), dev(qx), dev(qv), k=100, gamma=0, mode=mode, block=block)
+            idx.check()
+            ids, sc = ids.cpu().numpy().view(np.uint32).astype(np.int64), sc.cpu().numpy()
+            for r in range(Q.n):
+                oi, os_ = I.search(Q, r, k=164, gamma=0)
+                check_ranked(ids[r], sc[r], oi, os_, 100, D.n, what=f"{mode} block {block} query {r}")
+
+
 @pytest.mark.parametrize("window,gamma,k,mode", [(2048, 200, 10, "plain"), (8192, 500, 50, "plain"),
                                                  (4096, 500, 50, "batched"), (1024, 1000, 100, "batched")])
 def test_pruned_rerank_parity(pruned_small, window, gamma, k, mode):
