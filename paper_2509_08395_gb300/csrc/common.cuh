@@ -8,7 +8,7 @@
 #include <cstring>
 #include <string>
 
-#include "../../include/sindi.h"
+#include "sindi.h"
 
 namespace sindi {
 

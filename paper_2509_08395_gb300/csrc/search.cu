@@ -48,6 +48,7 @@ constexpr int kHistBins = 1 << kHistBits;  // bins on the top 12 bits of a score
 constexpr int kKeyBinShift = 64 - kHistBits;
 constexpr int kSubBits = 8;                // second-level bins inside the cut bin
 constexpr int kSubBins = 1 << kSubBits;
+constexpr int kRelBins = 256;              // window histogram bins below the window's top bin
 constexpr int kMergeThreads = 512;
 constexpr int kRerankThreads = 256;
 constexpr int kRerankWarps = kRerankThreads / 32;
@@ -186,16 +187,27 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     constexpr int kScanThreads = BLOCK;
     constexpr int kScanWarps = BLOCK / 32;
     constexpr int kTermChunk = BLOCK;   // query terms staged per pass (one per thread)
+    // Shared memory: the window's scores, two histograms, and one region that
+    // holds the term tables while postings are added and the staged
+    // candidates of the window afterwards.
+    constexpr int kTableBytes = ((4 * kTermChunk + 1) * 4 + kChunkTable * 2 + 15) & ~15;
+    constexpr int kPrivBytes = kScanWarps * kRelBins * 4;
+    constexpr int kRegionBytes = kTableBytes > kPrivBytes ? kTableBytes : kPrivBytes;
+    constexpr int kStageCap = kRegionBytes / 8;
     extern __shared__ float A[];                    // [lambda]
     __shared__ uint32_t hist[kHistBins];
     __shared__ uint32_t hist2[kSubBins];
-    __shared__ uint32_t t_start[kTermChunk];
-    __shared__ uint32_t t_end[kTermChunk];
-    __shared__ uint32_t c_pre[kTermChunk + 1];
-    __shared__ float t_w[kTermChunk];
-    __shared__ uint16_t c_term[kChunkTable];
+    __shared__ __align__(16) unsigned char region[kRegionBytes];
+    __shared__ uint32_t warp_off[kScanWarps];
     __shared__ uint32_t red[kScanWarps + 1];
     __shared__ uint32_t st[4];
+    __shared__ uint32_t s_staged;
+    uint32_t* t_start = reinterpret_cast<uint32_t*>(region);
+    uint32_t* t_end = t_start + kTermChunk;
+    uint32_t* c_pre = t_end + kTermChunk;
+    float* t_w = reinterpret_cast<float*>(c_pre + kTermChunk + 1);
+    uint16_t* c_term = reinterpret_cast<uint16_t*>(t_w + kTermChunk);
+    uint64_t* stage = reinterpret_cast<uint64_t*>(region);
 
     const DevIndex& ix = a.ix;
     const uint32_t w = QUERY_MAJOR ? blockIdx.y : blockIdx.x;
@@ -273,59 +285,141 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     const int n_eff = (int)(rest < (int64_t)lambda ? rest : (int64_t)lambda);
     const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
     auto key_of = [&](int i) -> uint64_t { return result_key(A[i], (uint32_t)(gbase + i)); };
-    // level 1: top 12 bits of the score key
-    for (int base = 0; base < n_eff; base += kScanThreads) {
-        const int i = base + threadIdx.x;
-        const int bin = i < n_eff ? (int)(float_order_bits(A[i]) >> (32 - kHistBits)) : -1;
-        const unsigned peers = __match_any_sync(kFull, bin);
-        if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    // level 1: 12-bit bins of the score key. Each warp counts its slots in a
+    // private histogram of the 256 bins below the window's top bin (no
+    // contention between warps); the window histogram is their sum. When the
+    // cut falls below that range, a full 4096-bin histogram is used instead.
+    uint32_t* priv = reinterpret_cast<uint32_t*>(region) + warp * kRelBins;
+    uint32_t top_key = 0;
+    for (int i = threadIdx.x; i < n_eff; i += kScanThreads) top_key = max(top_key, float_order_bits(A[i]));
+    top_key = __reduce_max_sync(kFull, top_key);
+    if (lane == 0) red[warp] = top_key;
+    __syncthreads();  // (also: the term tables are dead from here on)
+    if (threadIdx.x == 0) {
+        uint32_t m = 0;
+        for (int i = 0; i < kScanWarps; i++) m = max(m, red[i]);
+        st[0] = m;
     }
+    for (int b = lane; b < kRelBins; b += 32) priv[b] = 0;
     __syncthreads();
-    block_find_bin<kHistBins, kScanThreads>([&](int b) { return hist[b]; }, g_w, red, st);
-    const uint32_t bw = st[0];
-    const uint32_t above_bw = st[1];
-    __syncthreads();
-    // level 2: the next 8 bits, inside bin bw only
+    const uint32_t top_bin = st[0] >> (32 - kHistBits);
     for (int i = threadIdx.x; i < n_eff; i += kScanThreads) {
-        const uint32_t k32 = float_order_bits(A[i]);
-        if ((k32 >> (32 - kHistBits)) == bw) atomicAdd(&hist2[(k32 >> (32 - kHistBits - kSubBits)) & (kSubBins - 1)], 1u);
+        const uint32_t rel = top_bin - (float_order_bits(A[i]) >> (32 - kHistBits));
+        atomicAdd(&priv[rel < (uint32_t)kRelBins ? rel : kRelBins - 1], 1u);
     }
     __syncthreads();
-    block_find_bin<kSubBins, kScanThreads>([&](int b) { return hist2[b]; }, g_w - above_bw, red, st);
-    const uint32_t bw2 = st[0];
-    const uint32_t c_cut = above_bw + st[1] + st[2];   // slots at or above the 20-bit cut
+    for (int b = threadIdx.x; b < kRelBins; b += kScanThreads) {
+        uint32_t c = 0;
+        for (int k = 0; k < kScanWarps; k++) c += reinterpret_cast<uint32_t*>(region)[k * kRelBins + b];
+        hist[b] = c;  // hist[rel] = slots in bin top_bin - rel (rel 255: that bin and all below)
+    }
     __syncthreads();
-    // the 20-bit cut as a 64-bit key threshold
-    uint64_t thr = ((uint64_t)((bw << kSubBits) | bw2)) << (64 - kHistBits - kSubBits);
-    bool exact = c_cut > a.win_cap;
+    block_find_bin<kRelBins, kScanThreads>([&](int b) { return hist[kRelBins - 1 - b]; }, g_w, red, st);
+    const uint32_t rel_cut = kRelBins - 1 - st[0];
+    uint32_t bw = top_bin - rel_cut;
+    uint32_t above_bw = st[1];
+    uint32_t c_bw = st[1] + st[2];  // slots in bins >= bw
+    __syncthreads();
+    const bool relative = rel_cut < (uint32_t)kRelBins - 1;
+    if (!relative) {
+        for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) hist[b] = 0;
+        __syncthreads();
+        for (int base = 0; base < n_eff; base += kScanThreads) {
+            const int i = base + threadIdx.x;
+            const int bin = i < n_eff ? (int)(float_order_bits(A[i]) >> (32 - kHistBits)) : -1;
+            const unsigned peers = __match_any_sync(kFull, bin);
+            if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        block_find_bin<kHistBins, kScanThreads>([&](int b) { return hist[b]; }, g_w, red, st);
+        bw = st[0];
+        above_bw = st[1];
+        c_bw = st[1] + st[2];
+        __syncthreads();
+    }
+    // slots of the window in 12-bit bin b (b within the histogram kept above)
+    auto bin_count = [&](uint32_t b) -> uint32_t {
+        if (!relative) return hist[b];
+        const uint32_t rel = top_bin - b;
+        return rel < (uint32_t)kRelBins - 1 ? hist[rel] : 0u;
+    };
     uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
     wait_previous_kernels();  // the workspace is free from here on
+    uint32_t lo = bw;
     if (a.use_partial) {
         // g slots already emitted at or above a bin prove the answer lies there
         block_find_bin<kHistBins, kScanThreads>([&](int b) { return __ldcg(H + b); }, a.g, red, st);
-        const uint32_t bp = st[3] >= a.g ? st[0] : 0u;
+        if (st[3] >= a.g && st[0] > lo) lo = st[0];
         __syncthreads();
-        if (bp > bw) {
-            thr = (uint64_t)bp << kKeyBinShift;
-            exact = false;
+    }
+    const bool staged = relative && c_bw <= (uint32_t)kStageCap;  // slots >= bin lo fit in the staging area
+    uint32_t n_src = (uint32_t)n_eff;
+    if (staged) {
+        // per-warp counts of slots at or above bin lo (from the private
+        // histograms) give every warp its staging range: no atomics below
+        uint32_t mine_w = 0;
+        for (int b = lane; b < kRelBins - 1; b += 32)
+            if (top_bin - (uint32_t)b >= lo) mine_w += priv[b];
+        mine_w = __reduce_add_sync(kFull, mine_w);
+        if (lane == 0) warp_off[warp] = mine_w;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (int k = 0; k < kScanWarps; k++) {
+                const uint32_t c = warp_off[k];
+                warp_off[k] = acc;
+                acc += c;
+            }
+            s_staged = acc;
         }
+        __syncthreads();  // the private histograms are dead from here on
+        uint32_t at = warp_off[warp];
+        const unsigned lt = (1u << lane) - 1u;
+        for (int base = warp * 32; base < n_eff; base += kScanThreads) {
+            const int i = base + lane;
+            const bool ok = i < n_eff && (float_order_bits(A[i]) >> (32 - kHistBits)) >= lo;
+            const unsigned bal = __ballot_sync(kFull, ok);
+            if (ok) stage[at + __popc(bal & lt)] = key_of(i);
+            at += __popc(bal);
+        }
+        __syncthreads();
+        n_src = s_staged;
+    }
+    // candidates: the staged keys, or the whole window
+    auto src_key = [&](int i) -> uint64_t { return staged ? stage[i] : key_of(i); };
+    uint64_t thr = (uint64_t)lo << kKeyBinShift;
+    bool exact = false;
+    if (lo == bw) {
+        // level 2: the next 8 bits, inside bin bw only
+        for (int i = threadIdx.x; i < (int)n_src; i += kScanThreads) {
+            const uint64_t k = src_key(i);
+            if ((uint32_t)(k >> kKeyBinShift) == bw)
+                atomicAdd(&hist2[(uint32_t)(k >> (kKeyBinShift - kSubBits)) & (kSubBins - 1)], 1u);
+        }
+        __syncthreads();
+        block_find_bin<kSubBins, kScanThreads>([&](int b) { return hist2[b]; }, g_w - above_bw, red, st);
+        const uint32_t bw2 = st[0];
+        const uint32_t c_cut = above_bw + st[1] + st[2];   // slots at or above the 20-bit cut
+        __syncthreads();
+        thr = ((uint64_t)((bw << kSubBits) | bw2)) << (kKeyBinShift - kSubBits);
+        exact = c_cut > a.win_cap;
     }
     if (exact) {
         // ties crowd the cut: exact best g_w of the window
-        thr = block_select_threshold<kScanThreads>(key_of, n_eff, (int)g_w, t_start, st);
+        thr = block_select_threshold<kScanThreads>(src_key, (int)n_src, (int)g_w, hist2, st);
     }
     // emit keys >= thr: count, reserve the block's range with one atomic, write
     uint32_t mine = 0;
-    for (int i = threadIdx.x; i < n_eff; i += kScanThreads)
-        if (key_of(i) >= thr) mine++;
+    for (int i = threadIdx.x; i < (int)n_src; i += kScanThreads)
+        if (src_key(i) >= thr) mine++;
     uint32_t total;
     uint32_t pos = block_exclusive_sum<uint32_t, kScanThreads>(mine, &total, red);
     if (threadIdx.x == 0) st[0] = total ? atomicAdd(a.ws.cand_count + y, total) : 0u;
     __syncthreads();
     pos += st[0];
     uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
-    for (int i = threadIdx.x; i < n_eff && mine; i += kScanThreads) {
-        const uint64_t key = key_of(i);
+    for (int i = threadIdx.x; i < (int)n_src && mine; i += kScanThreads) {
+        const uint64_t key = src_key(i);
         if (key >= thr) {
             if (pos < a.ws.cand_cap) cand[pos] = key;
             else atomicOr(ix.err, kErrCandOverflow);
@@ -338,9 +432,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     const uint32_t tb = (uint32_t)(thr >> kKeyBinShift);
     uint32_t above_mine = 0;
     for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) {
-        if ((uint32_t)b > tb && hist[b]) {
-            above_mine += hist[b];
-            atomicAdd(H + b, hist[b]);
+        const uint32_t c = (uint32_t)b > tb ? bin_count((uint32_t)b) : 0u;
+        if (c) {
+            above_mine += c;
+            atomicAdd(H + b, c);
         }
     }
     uint32_t above;
