@@ -248,19 +248,56 @@ inline void radix_sort_triples(uint32_t* key_a, uint32_t* doc_a, uint32_t* val_a
 
 // ---------------------------------------------------------------------------
 // Block radix selection. Given n distinct 64-bit keys (key_of(i), i < n) and
-// 1 <= g <= n, returns T such that exactly g keys are >= T. Works from the
-// most significant byte down; a pass that finds the whole remainder inside
-// one digit bucket ends the search early.
+// 1 <= g <= n, returns T such that exactly g keys are >= T. The leading bits
+// all keys share are found first (one max/min reduction) and skipped; 8-bit
+// digits then go from the highest differing bit down, and a digit bucket that
+// holds exactly the remainder ends the search early.
 //   hist: shared uint32[256]; st: shared uint32[4].
 // Every thread of the block must call it (it synchronises).
 // ---------------------------------------------------------------------------
 template <int BLOCK, typename KeyOf>
 __device__ uint64_t block_select_threshold(const KeyOf& key_of, int n, int g, uint32_t* hist, uint32_t* st) {
+    constexpr int W = BLOCK / 32;
+    static_assert(2 * W * 2 <= 256, "scratch for the reduction lives in hist");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t prefix = 0, mask = 0;
+    // shared prefix: highest bit where the largest and smallest key differ
+    uint64_t mx = 0, mn = ~0ull;
+    for (int i = threadIdx.x; i < n; i += BLOCK) {
+        const uint64_t k = key_of(i);
+        mx = k > mx ? k : mx;
+        mn = k < mn ? k : mn;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t a = __shfl_xor_sync(kFull, mx, o), b = __shfl_xor_sync(kFull, mn, o);
+        mx = a > mx ? a : mx;
+        mn = b < mn ? b : mn;
+    }
+    uint64_t* red64 = reinterpret_cast<uint64_t*>(hist);
+    __syncthreads();  // hist may still be read by the caller's previous use
+    if (lane == 0) {
+        red64[warp] = mx;
+        red64[W + warp] = mn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t a = 0, b = ~0ull;
+        for (int i = 0; i < W; i++) {
+            a = red64[i] > a ? red64[i] : a;
+            b = red64[W + i] < b ? red64[W + i] : b;
+        }
+        red64[0] = a;
+        red64[1] = b;
+    }
+    __syncthreads();
+    const uint64_t kmax = red64[0], diff = kmax ^ red64[1];
+    __syncthreads();
+    if (diff == 0) return kmax;  // a single key
+    const int hb = 63 - __clzll((long long)diff);
+    uint64_t mask = hb >= 63 ? 0ull : ~((2ull << hb) - 1ull);  // bits every key shares
+    uint64_t prefix = kmax & mask;
     uint32_t remaining = (uint32_t)g;
-    for (int pass = 0; pass < 8; pass++) {
-        const int shift = 56 - 8 * pass;
+    for (int shift = hb - 7 > 0 ? hb - 7 : 0;; shift = shift - 8 > 0 ? shift - 8 : 0) {
         for (int b = threadIdx.x; b < 256; b += BLOCK) hist[b] = 0;
         __syncthreads();
         for (int base = 0; base < n; base += BLOCK) {
@@ -309,11 +346,12 @@ __device__ uint64_t block_select_threshold(const KeyOf& key_of, int n, int g, ui
         const uint32_t bin = st[0], above = st[1], cnt = st[2];
         __syncthreads();
         remaining -= above;
-        prefix |= (uint64_t)bin << shift;
+        prefix = (prefix & ~((uint64_t)0xFF << shift)) | ((uint64_t)bin << shift);
         mask |= (uint64_t)0xFF << shift;
-        if (cnt == remaining) return prefix;  // the whole bucket is in; lower bits are zero
+        // the whole bucket is in: the threshold is the bucket's lowest key
+        if (cnt == remaining) return prefix;
+        if (shift == 0) return prefix;
     }
-    return prefix;
 }
 
 // Bitonic sort of n (power of two) 64-bit keys in shared memory, descending.

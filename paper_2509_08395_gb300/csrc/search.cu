@@ -729,14 +729,11 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
     __threadfence();
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
-    if (g <= (uint32_t)kMaxK) {
-        for (uint32_t i = threadIdx.x; i < g; i += kRerankThreads) s[i] = __ldcg(rr + i);
-        if (threadIdx.x == 0) s_n = g;
-        __syncthreads();
-    } else {
+    {
+        // the best k of the g exact scores, then sort only those
         const uint32_t kk = a.k < g ? a.k : g;
         auto key_of = [&](int i) -> uint64_t { return __ldcg(rr + i); };
-        const uint64_t T = block_select_threshold<kRerankThreads>(key_of, (int)g, (int)kk, hist256, st);
+        const uint64_t T = g > kk ? block_select_threshold<kRerankThreads>(key_of, (int)g, (int)kk, hist256, st) : 0ull;
         gather_at_least<kRerankThreads>(key_of, g, T, s, kMaxK, &s_n);
     }
     write_sorted_results<kRerankThreads>(s, (int)min(s_n, (uint32_t)kMaxK), a.k, a.out_ids, a.out_scores, r);
