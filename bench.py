@@ -325,10 +325,17 @@ def main():
         w = w.scaled(window=args.window)
     if args.queries:
         w = w.scaled(n_queries=args.queries)
-    # each rank its own queries (weak scaling); rank 0 gets the workload's seed
-    wq = w.scaled(query_seed=w.query_seed + 7919 * rank)
+    # weak scaling: the global query set holds the workload's queries once per rank, and every rank
+    # searches its contiguous share (rank 0's share is the workload's own query set)
+    from paper_2509_08395_gb300.shard import shard_range
+
+    per_rank = w.queries.n_rows
     ip, ix, v = datagen.docs(w)
-    qp, qx, qv = datagen.queries(wq)
+    gqp, gqx, gqv = datagen.queries(w.scaled(n_queries=per_rank * ws))
+    q_lo, q_hi = shard_range(per_rank * ws, rank, ws)
+    qp = gqp[q_lo: q_hi + 1] - gqp[q_lo]
+    qx = np.ascontiguousarray(gqx[gqp[q_lo]: gqp[q_hi]])
+    qv = np.ascontiguousarray(gqv[gqp[q_lo]: gqp[q_hi]])
     nq = len(qp) - 1
 
     t_b0 = time.perf_counter()
@@ -394,9 +401,27 @@ def main():
     # algorithmic bytes of one scan launch: postings (uint16 id + value) + the two offsets of every
     # (term, window) + the query's terms; a plain launch covers one query, a batched launch all of them
     per_query_bytes = touched * (2 + vbytes) + nterms * sigma * 8 + nterms * 8
-    queries_per_launch = 1 if args.mode == "plain" else nq
-    alg_bytes_per_launch = float(per_query_bytes.mean()) * queries_per_launch
+    scan_launches_per_step = max(1, st2["scan_timed"] // max(1, args.steps))
+    if args.mode == "plain":
+        # one query per launch: its lists are the bytes the launch must read
+        alg_bytes_per_launch = float(per_query_bytes.mean())
+    else:
+        # a launch group reads each list it touches from HBM at least once (queries holding the same term
+        # share it through L2): the union of the group's lists, plus the per-query offsets and terms
+        group = -(-nq // scan_launches_per_step)
+        j = np.arange(w.dim, dtype=np.int64)
+        list_bytes = (ex["seg"][(j + 1) * sigma].astype(np.int64) - ex["seg"][j * sigma].astype(np.int64)) * (2 + vbytes)
+        per_group = []
+        for g0 in range(0, nq, group):
+            terms = np.unique(qx[qp[g0]:qp[min(nq, g0 + group)]])
+            per_group.append(float(list_bytes[terms].sum()) +
+                             float((nterms[g0:g0 + group] * (sigma * 8 + 8)).sum()))
+        alg_bytes_per_launch = float(np.mean(per_group))
     achieved_gbs = alg_bytes_per_launch / (scan_ms_per_launch / 1000.0) / 1e9
+    # scatter-adds (one shared-memory atomic per posting and query) against the shared-memory bound:
+    # 152 SMs x 32 banks x the max SM clock, one 4-byte atomic per bank per clock
+    adds_per_s = float(touched.sum()) * args.steps / (st2["scan_ms"] / 1000.0)
+    adds_peak = 152 * 32 * 2.07e9
     peak, peak_kind = measured_hbm_peak()
     sha = source_sha()
 
@@ -545,7 +570,11 @@ def main():
                      "frac_of_nominal_8tbs": achieved_gbs / NOMINAL_HBM_GBS,
                      "traffic": profile_traffic(sha), "kernel": "scan_window_kernel",
                      "alg_bytes_per_launch": alg_bytes_per_launch, "ms_per_launch": scan_ms_per_launch,
-                     "postings_per_query": float(touched.mean())},
+                     "postings_per_query": float(touched.mean()),
+                     "logical_gbs": float(per_query_bytes.sum()) * args.steps / (st2["scan_ms"] / 1000.0) / 1e9,
+                     "scatter_adds": {"per_s": adds_per_s, "peak": adds_peak, "frac": adds_per_s / adds_peak,
+                                      "unit": "posting updates/s",
+                                      "peak_from": "152 SMs x 32 shared-memory banks x 2.07 GHz"}},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "forms": forms,

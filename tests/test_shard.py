@@ -1,0 +1,89 @@
+"""Multi-rank paths on CPU ranks (gloo, world size 2): query shards and document shards + top-k merge.
+
+The per-shard searches here are the FP64 oracle's brute force on each rank's
+documents; what is under test is the sharding and the all-gather merge.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import datagen
+import oracle
+from paper_2509_08395_gb300.shard import PAD_ID, merge_topk, shard_range
+
+
+def test_shard_ranges_cover_everything_once():
+    for n in (0, 1, 7, 1000, 1_000_003):
+        for world in (1, 2, 3, 8):
+            for align in (1, 4096):
+                parts = [shard_range(n, r, world, align) for r in range(world)]
+                assert parts[0][0] == 0 and parts[-1][1] == n
+                for (a, b), (c, d) in zip(parts, parts[1:]):
+                    assert b == c and a <= b
+                assert all(lo % align == 0 for lo, _ in parts if lo < n)
+
+
+def test_merge_topk_order_and_padding():
+    ids = np.array([[[5, 1, PAD_ID]], [[9, 2, 3]]], np.uint32)
+    sc = np.array([[[3.0, 2.0, -np.inf]], [[3.0, 2.0, 1.0]]], np.float32)
+    mi, ms = merge_topk(ids, sc, 4)
+    assert mi.tolist() == [[5, 9, 1, 2]] and ms.tolist() == [[3.0, 3.0, 2.0, 2.0]]
+    mi, ms = merge_topk(ids[:1], sc[:1], 4)
+    assert mi.tolist() == [[5, 1, PAD_ID, PAD_ID]] and np.isneginf(ms[0, 2:]).all()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, result_path):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2509_08395_gb300.shard import gather_merge
+
+    ip, ix, v = datagen.random_csr(3001, 200, 15.0, seed=5, zipf_s=1.0)
+    qp, qx, qv = datagen.random_csr(12, 200, 10.0, seed=6, zipf_s=1.0, nnz_min=1)
+    k = 20
+    # document shard of this rank (window-aligned ranges)
+    lo, hi = shard_range(3001, rank, world, align=256)
+    sip = ip[lo: hi + 1] - ip[lo]
+    D = oracle.Dataset(sip, ix[ip[lo]: ip[hi]], v[ip[lo]: ip[hi]], 200)
+    Q = oracle.Dataset(qp, qx, qv, 200)
+    ids = np.full((Q.n, k), PAD_ID, np.uint32)
+    sc = np.full((Q.n, k), -np.inf, np.float32)
+    for r in range(Q.n):
+        a, b = oracle.brute_force(D, Q, r, k)
+        ids[r, : len(a)] = a
+        sc[r, : len(a)] = b.astype(np.float32)
+    mi, ms = gather_merge(ids, sc, lo, k)
+    # query shard of this rank, gathered back
+    qlo, qhi = shard_range(Q.n, rank, world)
+    import torch
+    mine = torch.tensor([qlo, qhi], dtype=torch.int64)
+    allq = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(allq, mine)
+    if rank == 0:
+        np.savez(result_path, ids=mi, sc=ms, qranges=np.stack([a.numpy() for a in allq]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_document_shards_merge_to_the_global_topk(tmp_path):
+    path = str(tmp_path / "merged.npz")
+    mp.spawn(_worker, args=(2, _free_port(), path), nprocs=2, join=True)
+    out = np.load(path)
+    ip, ix, v = datagen.random_csr(3001, 200, 15.0, seed=5, zipf_s=1.0)
+    qp, qx, qv = datagen.random_csr(12, 200, 10.0, seed=6, zipf_s=1.0, nnz_min=1)
+    D, Q = oracle.Dataset(ip, ix, v, 200), oracle.Dataset(qp, qx, qv, 200)
+    for r in range(Q.n):
+        a, b = oracle.brute_force(D, Q, r, 20)
+        assert out["ids"][r].tolist() == a.tolist()
+        np.testing.assert_array_equal(out["sc"][r], b.astype(np.float32))
+    qr = out["qranges"]
+    assert qr[0][0] == 0 and qr[-1][1] == Q.n and qr[0][1] == qr[1][0]
