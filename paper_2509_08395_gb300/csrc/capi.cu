@@ -249,10 +249,7 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
         set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; block_threads 0, 256, 512 or 1024");
         return SINDI_ERR_INVALID_ARG;
     }
-    if (prm.beta < 1.0) {
-        set_last_error("query pruning (beta < 1) is not in this build");
-        return SINDI_ERR_UNSUPPORTED;
-    }
+
     if (n_queries < 0 || n_queries > (int64_t)1 << 31) {
         set_last_error("n_queries out of range");
         return SINDI_ERR_INVALID_ARG;
@@ -363,7 +360,7 @@ sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_ind
         return SINDI_ERR_INVALID_ARG;
     }
     if (prm.beta < 1.0) {
-        set_last_error("query pruning (beta < 1) is not in this build");
+        set_last_error("query pruning (beta < 1) allocates its pruned queries: use sindi_search");
         return SINDI_ERR_UNSUPPORTED;
     }
     if (n_queries < 0 || n_queries > (int64_t)1 << 31) {

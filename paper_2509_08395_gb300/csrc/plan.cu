@@ -57,7 +57,7 @@ sindi_status sindi_plan_create(const sindi_index* index, const int64_t* q_indptr
         return SINDI_ERR_INVALID_ARG;
     }
     if (prm.beta < 1.0) {
-        set_last_error("query pruning (beta < 1) is not in this build");
+        set_last_error("query pruning (beta < 1) allocates its pruned queries: use sindi_search");
         return SINDI_ERR_UNSUPPORTED;
     }
     prm.mode = SINDI_MODE_BATCHED;

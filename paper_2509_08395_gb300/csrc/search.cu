@@ -33,6 +33,7 @@
 
 #include "common.cuh"
 #include "index.cuh"
+#include "mass.cuh"
 #include "primitives.cuh"
 
 namespace sindi {
@@ -740,6 +741,70 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
     if (threadIdx.x == 0) ws.rticket[y] = 0;
 }
 
+// beta-mass of every query (Alg. 4: q' = beta-mass(q), the alpha-mass rule
+// with beta): one warp per query. Its kept entries go to the query's own
+// positions of (pidx, pval), their count to kept[q]. Entries the scan would
+// skip anyway (dim out of range, non-finite, zero) are not entries here.
+constexpr int kPruneQueryWarps = 4;
+__global__ void __launch_bounds__(kPruneQueryWarps * 32) prune_queries_kernel(
+    const int64_t* qp, const int32_t* qi, const float* qv, int64_t nq, int32_t dim, double beta, uint32_t* kept,
+    int32_t* pidx, float* pval) {
+    extern __shared__ uint64_t qsm[];  // [warps][kQueryTermLimit]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* s = qsm + (size_t)warp * kQueryTermLimit;
+    for (int64_t q = (int64_t)blockIdx.x * kPruneQueryWarps + warp; q < nq;
+         q += (int64_t)gridDim.x * kPruneQueryWarps) {
+        const int64_t b = qp[q];
+        const int64_t m = qp[q + 1] - b;
+        if (m > kQueryTermLimit) {  // refused: merge reports the query as too long
+            if (lane == 0) kept[q] = 0;
+            continue;
+        }
+        int p2 = 32;
+        while (p2 < m) p2 <<= 1;
+        int nz = 0;
+        for (int t = lane; t < p2; t += 32) {
+            uint64_t key = ~0ull;
+            if (t < m) {
+                const int32_t j = qi[b + t];
+                const float v = qv[b + t];
+                if (j >= 0 && j < dim && isfinite(v) && v != 0.0f) {
+                    key = mass_key(j, v);
+                    nz++;
+                }
+            }
+            s[t] = key;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(kFull, nz, o);
+        __syncwarp();
+        warp_bitonic_sort_asc(s, p2);
+        int r = 0;
+        if (lane == 0) r = alpha_mass_count(s, nz, beta);
+        r = __shfl_sync(kFull, r, 0);
+        for (int t = lane; t < r; t += 32) {
+            pidx[b + t] = mass_key_dim(s[t]);
+            pval[b + t] = mass_key_value(s[t]);
+        }
+        if (lane == 0) kept[q] = (uint32_t)r;
+        __syncwarp();
+    }
+}
+
+// Kept query entries -> compact CSR.
+__global__ void compact_queries_kernel(const int64_t* qp, const int64_t* off, const int32_t* pidx, const float* pval,
+                                       int64_t nq, int32_t* oidx, float* oval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nq; q += warps) {
+        const int64_t b = qp[q], o = off[q], r = off[q + 1] - o;
+        for (int64_t t = lane; t < r; t += 32) {
+            oidx[o + t] = pidx[b + t];
+            oval[o + t] = pval[b + t];
+        }
+    }
+}
+
 // Rows of an empty index: every slot is padding.
 __global__ void pad_results_kernel(uint32_t* out_ids, float* out_scores, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -857,14 +922,23 @@ static void launch_scan_pdl(int dt, uint32_t block, bool batched, bool qm, const
 // The launches of one group of nq queries starting at row q0. `*chained` is
 // false for the first launch of a search call (it follows the caller's work
 // and must not overlap it) and true afterwards.
+struct QueryCsr {
+    const int64_t* indptr;
+    const int32_t* indices;
+    const float* values;
+};
+
 static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& ws, const int64_t* q_indptr,
                          const int32_t* q_indices, const float* q_values, int64_t q0, uint32_t nq, bool batched,
                          uint32_t k, uint32_t* out_ids, float* out_scores, cudaStream_t stream, bool* chained,
-                         cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+                         cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, const QueryCsr* scan_q = nullptr) {
     configure_search_kernels(ix.device);
     const DevIndex dix = ix.dev();
     const size_t scan_smem = (size_t)ix.lambda * sizeof(float);
-    ScanArgs sa{dix, q_indptr, q_indices, q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, ws};
+    // the coarse scan reads the beta-pruned queries when there are any (Alg. 4, line 3);
+    // merge and rerank check and reorder with the full queries
+    ScanArgs sa{dix, scan_q ? scan_q->indptr : q_indptr, scan_q ? scan_q->indices : q_indices,
+                scan_q ? scan_q->values : q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, ws};
     if (ev0) SINDI_CUDA(cudaEventRecord(ev0, stream));
     // query-major grids put the queries of one window next to each other
     // (shared lists stay in L2); gridDim.y limits sigma to 65535 there
@@ -909,6 +983,43 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
     unsigned char* mem = P.alloc<unsigned char>(workspace_bytes(chunk, pl.cand_cap, pl.fcap, pl.top_cap));
     const Workspace ws = carve_workspace(mem, chunk, pl.cand_cap, pl.fcap, pl.top_cap);
     SINDI_CUDA(cudaMemsetAsync(mem, 0, workspace_counter_bytes(chunk), stream));
+    QueryCsr pruned{nullptr, nullptr, nullptr};
+    int64_t* pq_indptr = nullptr;
+    int32_t* pq_idx = nullptr;
+    float* pq_val = nullptr;
+    int32_t* tq_idx = nullptr;
+    float* tq_val = nullptr;
+    uint32_t* pq_kept = nullptr;
+    if (prm.beta < 1.0) {
+        int64_t nnz = 0;
+        SINDI_CUDA(cudaMemcpyAsync(&nnz, q_indptr + n_queries, 8, cudaMemcpyDeviceToHost, stream));
+        SINDI_CUDA(cudaStreamSynchronize(stream));
+        pq_kept = P.alloc<uint32_t>(n_queries);
+        tq_idx = P.alloc<int32_t>(nnz);
+        tq_val = P.alloc<float>(nnz);
+        pq_indptr = P.alloc<int64_t>(n_queries + 1);
+        pq_idx = P.alloc<int32_t>(nnz);
+        pq_val = P.alloc<float>(nnz);
+        const size_t qsmem = (size_t)kPruneQueryWarps * kQueryTermLimit * sizeof(uint64_t);
+        static bool qconf = false;
+        if (!qconf) {
+            SINDI_CUDA(cudaFuncSetAttribute(prune_queries_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)qsmem));
+            qconf = true;
+        }
+        const unsigned blocks = (unsigned)std::min<int64_t>((n_queries + kPruneQueryWarps - 1) / kPruneQueryWarps,
+                                                            152 * 16);
+        prune_queries_kernel<<<blocks, kPruneQueryWarps * 32, qsmem, stream>>>(q_indptr, q_indices, q_values,
+                                                                               n_queries, ix.dim, prm.beta, pq_kept,
+                                                                               tq_idx, tq_val);
+        SINDI_CUDA(cudaGetLastError());
+        exclusive_scan<uint32_t, int64_t>(pq_kept, pq_indptr, n_queries, P);
+        compact_queries_kernel<<<blocks, 256, 0, stream>>>(q_indptr, pq_indptr, tq_idx, tq_val, n_queries, pq_idx,
+                                                           pq_val);
+        SINDI_CUDA(cudaGetLastError());
+        ix.launches += 3;
+        pruned = QueryCsr{pq_indptr, pq_idx, pq_val};
+    }
 
     const bool timing = ix.timing.load() != 0;
     std::vector<cudaEvent_t> evs;
@@ -923,10 +1034,16 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
             evs.push_back(e1);
         }
         launch_group(ix, pl, ws, q_indptr, q_indices, q_values, q0, nq, batched, k, out_ids, out_scores, stream,
-                     &chained, e0, e1);
+                     &chained, e0, e1, pruned.indptr ? &pruned : nullptr);
     }
     ix.queries += (uint64_t)n_queries;
     P.free(mem);
+    P.free(pq_kept);
+    P.free(tq_idx);
+    P.free(tq_val);
+    P.free(pq_indptr);
+    P.free(pq_idx);
+    P.free(pq_val);
     if (timing) {
         SINDI_CUDA(cudaStreamSynchronize(stream));
         double ms = 0.0;

@@ -240,7 +240,7 @@ sindi_status sindi_server_create(const sindi_index* index, const sindi_server_pa
         return SINDI_ERR_INVALID_ARG;
     }
     if (sp.beta < 1.0) {
-        set_last_error("query pruning (beta < 1) is not in this build");
+        set_last_error("query pruning (beta < 1) allocates its pruned queries: use sindi_search");
         return SINDI_ERR_UNSUPPORTED;
     }
     const IndexImpl& ix = index->impl;

@@ -55,7 +55,7 @@ def check_ranked(gids, gsc, oids, osc, k, n_docs, tol=REL_TOL, what=""):
             assert got <= want, f"{what}: boundary ranks [{a},{n}) gpu {sorted(got)} not in oracle group"
 
 
-def check_reranked(gids, gsc, D, Q, r, I, k, gamma, tol=REL_TOL, what=""):
+def check_reranked(gids, gsc, D, Q, r, I, k, gamma, tol=REL_TOL, what="", beta=1.0):
     """GPU results of Algorithm 4 (pruned coarse stage + exact reorder of gamma candidates).
 
     The GPU's coarse scores are FP32, so its candidate set may differ from the
@@ -65,12 +65,18 @@ def check_reranked(gids, gsc, D, Q, r, I, k, gamma, tol=REL_TOL, what=""):
     Returns the number of ambiguous documents that touched the answer."""
     n = min(k, D.n)
     g = min(gamma, D.n)
-    cids, csc = I.search(Q, r, k=min(g + 256, D.n), gamma=0)
+    cids, csc = I.search(Q, r, k=min(g + 256, D.n), gamma=0, beta=beta)
     s_g = csc[g - 1]
-    amb = set(int(c) for c, s in zip(cids, csc) if _close(s, s_g, tol))
-    robust = set(int(c) for c in cids[:g]) - amb
-    if len(cids) > g and _close(csc[-1], s_g, tol) and len(cids) < D.n:
-        raise AssertionError(f"{what}: coarse tie group at rank gamma longer than the probe")
+    if s_g == 0.0:
+        # fewer than gamma documents score above zero: zero scores are exact on both sides (no rounding)
+        # and both fill the pool with the lowest ids, so the candidate set is the oracle's
+        amb = set()
+        robust = set(int(c) for c in cids[:g])
+    else:
+        amb = set(int(c) for c, s in zip(cids, csc) if _close(s, s_g, tol))
+        robust = set(int(c) for c in cids[:g]) - amb
+        if len(cids) > g and _close(csc[-1], s_g, tol) and len(cids) < D.n:
+            raise AssertionError(f"{what}: coarse tie group at rank gamma longer than the probe")
     gids = np.asarray(gids).astype(np.int64) & 0xFFFFFFFF
     gsc = np.asarray(gsc, np.float64)
     assert np.all(gids[n:] == PAD_ID), f"{what}: padding"
@@ -94,7 +100,7 @@ def check_reranked(gids, gsc, D, Q, r, I, k, gamma, tol=REL_TOL, what=""):
         if ex(c) > kth * (1 + tol) + 1e-30:
             assert c in gotset, f"{what}: robust candidate {c} (exact {ex(c)}) beats the k-th {kth} but is missing"
     touched = len(amb & gotset)
-    oi, osc = I.search(Q, r, k=k, gamma=gamma)
+    oi, osc = I.search(Q, r, k=k, gamma=gamma, beta=beta)
     if not (amb & (gotset | set(int(x) for x in oi))):
         # no ambiguity reached the answer: the tie-group rule against the oracle itself
         full = sorted(((ex(c) if c in exact else oracle.inner_product(D, c, Q, r), c) for c in

@@ -21,11 +21,11 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def run_search(idx, qp, qx, qv, k, gamma=0, mode="plain", host=False):
+def run_search(idx, qp, qx, qv, k, gamma=0, mode="plain", host=False, beta=1.0):
     if host:
-        ids, sc = idx.search(qp, qx, qv, k=k, gamma=gamma, mode=mode)
+        ids, sc = idx.search(qp, qx, qv, k=k, gamma=gamma, mode=mode, beta=beta)
         return ids.astype(np.int64), sc
-    ids, sc = idx.search(dev(qp), dev(qx), dev(qv), k=k, gamma=gamma, mode=mode)
+    ids, sc = idx.search(dev(qp), dev(qx), dev(qv), k=k, gamma=gamma, mode=mode, beta=beta)
     idx.check()
     return ids.cpu().numpy().view(np.uint32).astype(np.int64), sc.cpu().numpy()
 
@@ -152,6 +152,24 @@ def test_pruned_rerank_parity(pruned_small, window, gamma, k, mode):
     assert touched <= 2
 
 
+@pytest.mark.parametrize("beta,mode", [(0.3, "plain"), (0.6, "batched")])
+def test_beta_query_pruning_parity(pruned_small, beta, mode):
+    """Alg. 4 with beta < 1: the coarse scan uses beta-mass(q), the reorder the full q."""
+    w, (ip, ix, v), (qp, qx, qv), D, Q = pruned_small
+    I = oracle.Index(D, window=4096, alpha=0.5)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=4096, alpha=0.5) as idx:
+        ids, sc = run_search(idx, qp, qx, qv, k=50, gamma=0, mode=mode, beta=beta)
+        rids, rsc = run_search(idx, qp, qx, qv, k=10, gamma=300, mode=mode, beta=beta)
+        hids, hsc = run_search(idx, qp, qx, qv, k=10, gamma=300, mode=mode, beta=beta, host=True)
+    np.testing.assert_array_equal(rids, hids)
+    touched = 0
+    for r in range(Q.n):
+        oi, os_ = I.search(Q, r, k=114, gamma=0, beta=beta)
+        check_ranked(ids[r], sc[r], oi, os_, 50, D.n, what=f"coarse query {r}")
+        touched += check_reranked(rids[r], rsc[r], D, Q, r, I, 10, 300, what=f"query {r}", beta=beta)
+    assert touched <= 2
+
+
 @pytest.mark.parametrize("dtype", ["f16", "f8"])
 def test_reduced_precision_coarse_parity(pruned_small, dtype):
     """FP16 / E4M3 postings: GPU coarse scores vs the oracle on the same dequantised values."""
@@ -251,8 +269,8 @@ def test_invalid_documents_and_queries():
         qp, qx, qv = _csr([[(1, 1.0)]], 4)
         with pytest.raises(sindi.SindiError, match="INVALID_ARG"):
             idx.search(dev(qp), dev(qx), dev(qv), k=3, gamma=2)      # gamma < k
-        with pytest.raises(sindi.SindiError, match="UNSUPPORTED"):
-            idx.search(dev(qp), dev(qx), dev(qv), k=1, beta=0.5)
+        with pytest.raises(sindi.SindiError, match="INVALID_ARG"):
+            idx.search(dev(qp), dev(qx), dev(qv), k=1, beta=1.5)
         ids, sc = idx.search(dev(qp), dev(qx), dev(qv), k=2)          # the index still works after errors
         idx.check()
         assert ids.cpu().tolist() == [[0, 1]]
