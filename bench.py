@@ -48,10 +48,14 @@ def parse():
     p.add_argument("--window", type=int, default=0, help="0 = the workload's window")
     p.add_argument("--queries", type=int, default=0, help="0 = the workload's query count")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
+    p.add_argument("--value-dtype", choices=["f32", "f16", "f8"], default=None,
+                   help="posting value type of the main index (default: the workload's)")
     p.add_argument("--no-forms", action="store_true", help="skip the batched / low-precision / serving side lines")
     p.add_argument("--serve-load", type=float, default=0.5,
                    help="serving leg: offered load as a fraction of the batched schedule's QPS")
     p.add_argument("--serve-seconds", type=float, default=4.0)
+    p.add_argument("--serve-sweep", default=None,
+                   help="comma-separated offered loads (fractions of batched QPS) for the serving leg")
     return p.parse_args()
 
 
@@ -342,7 +346,8 @@ def main():
     dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
     torch.cuda.synchronize()
     t_b1 = time.perf_counter()
-    idx = sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=w.alpha, value_dtype="f32")
+    main_dtype = args.value_dtype or w.value_dtype
+    idx = sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=w.alpha, value_dtype=main_dtype)
     torch.cuda.synchronize()
     build_ms = 1000 * (time.perf_counter() - t_b1)
     h2d_docs_ms = 1000 * (t_b1 - t_b0)
@@ -500,16 +505,41 @@ def main():
                                                "_sc": os_.cpu().numpy(), "_coarse": csc.cpu().numpy()}
 
     serving = None
-    if not args.no_forms and rank == 0:
+    if rank == 0 and (args.serve_sweep or not args.no_forms):
         rows = [(qx[qp[r]:qp[r + 1]], qv[qp[r]:qp[r + 1]]) for r in range(nq)]
-        base = forms.get("batched", {}).get("qps", value)
-        serving = serve_open_loop(sindi, idx, rows, w.k, w.gamma, args.serve_load * base, args.serve_seconds)
+        base = value if args.mode == "batched" else forms.get("batched", {}).get("qps", value)
+        if args.serve_sweep:
+            serving = [serve_open_loop(sindi, idx, rows, w.k, w.gamma, float(f) * base, args.serve_seconds)
+                       for f in args.serve_sweep.split(",")]
+        else:
+            serving = serve_open_loop(sindi, idx, rows, w.k, w.gamma, args.serve_load * base, args.serve_seconds)
 
     # ---- CPU baseline (oracle) + recall against FP64 exact, rank 0 only
     cpu = None
     recall = None
+    score_error = None
     if rank == 0:
         qps_cpu, n_cpu, recalls = cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, args.cpu_seconds, gpu_ids, w.k)
+        if main_dtype != "f32":
+            # score error of the reduced-precision main index against FP64 (coarse and final)
+            import oracle
+
+            D = oracle.Dataset(ip, ix, v, w.dim)
+            Q = oracle.Dataset(qp, qx, qv, w.dim)
+            I32 = oracle.Index(D, window=w.window, alpha=w.alpha)
+            n_err = min(8, nq)
+            cq = [torch.from_numpy(a).to(dev) for a in (qp[: n_err + 1], qx[: qp[n_err]], qv[: qp[n_err]])]
+            _, csc = idx.search(*cq, k=w.k, gamma=0)
+            csc = csc.cpu().numpy()
+            fsc = out_sc.cpu().numpy()
+            ce = fe = 0.0
+            for r in range(n_err):
+                _, osc = I32.search(Q, r, k=w.k, gamma=0)
+                ce = max(ce, float(np.max(np.abs(csc[r, : len(osc)] - osc) / np.abs(osc))))
+                for i, sc in zip(gpu_ids[r], fsc[r]):
+                    ex = oracle.inner_product(D, int(i), Q, r)
+                    fe = max(fe, abs(float(sc) - ex) / abs(ex))
+            score_error = {"coarse_max_rel_err_vs_fp64": ce, "final_max_rel_err_vs_fp64": fe, "queries": n_err}
         recall = float(np.mean(recalls)) if recalls else None
         cpu = {"value": qps_cpu, "unit": "queries/s", "cores": 1, "kind": "oracle",
                "sample": f"first {n_cpu} of {nq} queries of {w.name} (Algorithm 4, FP64, single thread, "
@@ -554,6 +584,7 @@ def main():
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
+        "posting_dtype": main_dtype,
         "data": "synthetic",
         "config": {"workload": w.name, "n_docs": w.docs.n_rows, "dim": w.dim, "queries_per_rank": nq,
                    "k": w.k, "gamma": w.gamma, "alpha": w.alpha, "window": info["window"],
@@ -561,6 +592,7 @@ def main():
                    "batch": 1 if args.mode == "plain" else nq,
                    "l2": "flushed between steps (256 MiB write)"},
         "recall_at_k": recall,
+        "score_error": score_error,
         "build_ms": build_ms,
         "h2d_docs_ms": h2d_docs_ms,
         "gpu_launches": launches,
