@@ -90,13 +90,13 @@ typedef struct {
     uint32_t gamma;        /* reorder pool size; 0 = no reordering (the coarse
                               top-k is the answer), else k <= gamma <= 8192        */
     double beta;           /* query pruning ratio in (0, 1]; 1 = off. With beta < 1
-                              the coarse scan uses beta-mass(q) (Alg. 4, line 3) and
+                              the coarse scan uses beta-mass(q) (Alg. 4) and
                               the reorder the full q. Supported by sindi_search;
                               plans, servers and sindi_search_noalloc return
                               SINDI_ERR_UNSUPPORTED for beta < 1                    */
     uint32_t mode;         /* sindi_mode                                           */
     uint32_t block_threads;/* threads per window-scan block: 256, 512 or 1024;
-                              0 = the schedule's default (1024 plain, 512 batched) */
+                              0 = the schedule's default (512)                  */
 } sindi_search_params;
 
 typedef struct {

@@ -404,7 +404,7 @@ orc_index* orc_build(const orc_dataset* D, int64_t lambda, double alpha, int32_t
     I->sigma = (D->n + lambda - 1) / lambda;                 /* sigma = ceil(||D|| / lambda) */
     int64_t n = D->n, d = D->d, sigma = I->sigma;
 
-    /* Alg. 3, lines 1-4: D' <- { alpha-mass(x_i) }. Kept entries go back in
+    /* Alg. 3, pruning step: D' <- { alpha-mass(x_i) }. Kept entries go back in
        ascending dim order (the subvector is a set; canonical order). */
     int64_t nnz = D->ptr[n];
     int64_t* kptr = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));

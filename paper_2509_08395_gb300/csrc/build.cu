@@ -352,8 +352,17 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
         return SINDI_ERR_UNSUPPORTED;
     }
     ix.postings = Pn;
-    ix.pid = P.alloc<uint16_t>(Pn);
-    ix.pval = P.alloc<uint8_t>((size_t)Pn * ix.value_bytes());
+    // posting arrays padded to a multiple of 8 entries: the scan reads aligned groups of 8
+    const int64_t Pp = (Pn + 7) & ~(int64_t)7;
+    ix.pid = P.alloc<uint16_t>(Pp);
+    ix.pval = P.alloc<uint8_t>((size_t)Pp * ix.value_bytes());
+    if ((reinterpret_cast<uintptr_t>(ix.pid) | reinterpret_cast<uintptr_t>(ix.pval)) & 15)
+        throw CudaError{cudaErrorMisalignedAddress, "posting arrays are not 16-byte aligned"};
+    if (Pp > Pn) {
+        SINDI_CUDA(cudaMemsetAsync(ix.pid + Pn, 0, sizeof(uint16_t) * (size_t)(Pp - Pn), stream));
+        SINDI_CUDA(cudaMemsetAsync(static_cast<uint8_t*>(ix.pval) + (size_t)Pn * ix.value_bytes(), 0,
+                                   (size_t)(Pp - Pn) * ix.value_bytes(), stream));
+    }
     uint32_t* sdim = P.alloc<uint32_t>(Pn);
     uint32_t* sdoc = P.alloc<uint32_t>(Pn);
     uint32_t* sval = P.alloc<uint32_t>(Pn);

@@ -94,6 +94,9 @@ static void free_index_memory(IndexImpl& ix, cudaStream_t s) {
     ix.scale = nullptr;
     ix.kept = nullptr;
     ix.err = nullptr;
+    std::lock_guard<std::mutex> lk(ix.lane_mu);
+    for (cudaStream_t l : ix.lanes) (void)cudaStreamDestroy(l);
+    ix.lanes.clear();
 }
 
 static std::string query_error_text(uint32_t e) {

@@ -33,6 +33,10 @@ struct IndexImpl {
     uint32_t* kept = nullptr;    // [n_docs]
     uint32_t* err = nullptr;     // device error word
 
+    // streams of the plain schedule's concurrent query chains (created on first use)
+    mutable std::mutex lane_mu;
+    mutable std::vector<cudaStream_t> lanes;
+
     // counters
     mutable std::atomic<uint64_t> launches{0}, scan_launches{0}, queries{0}, scan_timed{0};
     mutable std::mutex tmu;

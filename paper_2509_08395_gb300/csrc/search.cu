@@ -38,12 +38,14 @@
 
 namespace sindi {
 
-constexpr int kScanThreadsPlain = 1024;    // one query: few windows, so more warps per window
+constexpr int kScanThreadsPlain = 512;     // two blocks per SM: the windows of concurrent queries interleave
 constexpr int kScanThreadsBatched = 512;   // many windows: two blocks per SM overlap their phases
-constexpr int kMaxScanWarps = kScanThreadsPlain / 32;
+constexpr int kPlainLanes = 8;             // plain schedule: query chains in flight at once
+constexpr int kMaxScanWarps = 1024 / 32;   // largest scan block
 constexpr int kChunkTable = 2048;          // chunks mapped to their list by a table (then a search)
 constexpr int kChunkU = 8;                 // postings per lane in one warp chunk
 constexpr int kChunkLen = 32 * kChunkU;    // postings of one warp chunk (one list only)
+constexpr uint32_t kVecMin = 128;          // lists this long are read with vector loads
 constexpr int kHistBits = 12;
 constexpr int kHistBins = 1 << kHistBits;  // bins on the top 12 bits of a score key
 constexpr int kKeyBinShift = 64 - kHistBits;
@@ -122,6 +124,47 @@ __device__ __forceinline__ float load_value(const void* pval, uint32_t p) {
 __device__ __forceinline__ void wait_previous_kernels() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_next_kernel() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// Eight consecutive postings p0 .. p0 + 7 (p0 a multiple of 8): their window
+// ids (two per word) and values, read with aligned vector loads (the posting
+// arrays are padded to a multiple of 8 entries).
+__device__ __forceinline__ void load_ids8(const uint16_t* pid, uint32_t p0, uint32_t id2[4]) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(pid + p0));
+    id2[0] = u.x;
+    id2[1] = u.y;
+    id2[2] = u.z;
+    id2[3] = u.w;
+}
+
+template <int DT>
+__device__ __forceinline__ void load_values8(const void* pval, uint32_t p0, float v[8]) {
+    if (DT == SINDI_F32) {
+        const float4* f = reinterpret_cast<const float4*>(static_cast<const float*>(pval) + p0);
+        const float4 a = __ldg(f), b = __ldg(f + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else if (DT == SINDI_F16) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(static_cast<const __half*>(pval) + p0));
+        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w4[j]));
+            v[2 * j] = f.x;
+            v[2 * j + 1] = f.y;
+        }
+    } else {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(static_cast<const unsigned char*>(pval) + p0));
+        const uint32_t w2[2] = {u.x, u.y};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w2[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
+            const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
+            const float2 f = __half22float2(__half2(h));
+            v[2 * j] = f.x;
+            v[2 * j + 1] = f.y;
+        }
+    }
+}
+
 // last t in [0, n) with pre[t] <= f (pre[0] = 0 <= f)
 __device__ __forceinline__ int term_of(const uint32_t* pre, int n, uint32_t f) {
     int lo = 0, hi = n - 1;
@@ -130,6 +173,61 @@ __device__ __forceinline__ int term_of(const uint32_t* pre, int n, uint32_t f) {
         if (pre[mid] <= f) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// One warp chunk of one query term's list in one window, in registers: the
+// lane's postings are q0 + u (a long list) or q0 + 32 u (a short one), u <
+// kChunkU, those in [ps, pe) counted.
+struct Chunk {
+    uint32_t id2[kChunkU / 2];  // window ids, two per word (low half first)
+    float v[kChunkU];
+    uint32_t q0, ps, pe;
+    float wq;
+};
+
+// Loads chunk c. A list of at least kVecMin postings is tiled on 8-aligned
+// groups, lane l owning the 8 consecutive postings of the chunk's l-th group
+// (one vector load of ids, one or two of values); a shorter list (always a
+// single chunk) keeps the lanes interleaved, which keeps more of them busy.
+template <int DT>
+__device__ __forceinline__ void load_chunk(const DevIndex& ix, const uint32_t* t_start, const uint32_t* t_end,
+                                           const float* t_w, const uint32_t* c_pre, const uint16_t* c_term,
+                                           int nc, uint32_t c, int lane, Chunk& k) {
+    const int t = c < (uint32_t)kChunkTable ? (int)c_term[c] : term_of(c_pre, nc, c);
+    k.ps = t_start[t];
+    k.pe = t_end[t];
+    k.wq = t_w[t];
+    const uint32_t off = (c - c_pre[t]) * (uint32_t)kChunkLen;
+#pragma unroll
+    for (int u = 0; u < kChunkU; u++) k.v[u] = 0.0f;
+#pragma unroll
+    for (int u = 0; u < kChunkU / 2; u++) k.id2[u] = 0;
+    if (k.pe - k.ps >= kVecMin) {
+        k.q0 = (k.ps & ~7u) + off + (uint32_t)lane * kChunkU;
+        if (k.q0 < k.pe) {
+            load_ids8(ix.pid, k.q0, k.id2);
+            load_values8<DT>(ix.pval, k.q0, k.v);
+        }
+    } else {
+        k.q0 = k.ps + off + (uint32_t)lane;
+#pragma unroll
+        for (int u = 0; u < kChunkU; u++) {
+            const uint32_t p = k.q0 + 32u * u;
+            if (p < k.pe) {
+                k.id2[u >> 1] |= (uint32_t)__ldg(ix.pid + p) << (16 * (u & 1));
+                k.v[u] = load_value<DT>(ix.pval, p);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void add_chunk(float* A, const Chunk& k) {
+    const uint32_t step = k.pe - k.ps >= kVecMin ? 1u : 32u;
+#pragma unroll
+    for (int u = 0; u < kChunkU; u++) {
+        const uint32_t p = k.q0 + step * u;
+        if (p >= k.ps && p < k.pe) atomicAdd(&A[(k.id2[u >> 1] >> (16 * (u & 1))) & 0xFFFFu], k.wq * k.v[u]);
+    }
 }
 
 // Block-wide: the bin holding the g-th largest element of a BINS-bin
@@ -245,7 +343,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
             t_start[threadIdx.x] = start;
             t_end[threadIdx.x] = start + len;
             t_w[threadIdx.x] = wq;
-            nch = (len + kChunkLen - 1) / kChunkLen;
+            // chunks of a long list tile its 8-aligned groups of postings
+            nch = len >= kVecMin ? (((start + len + 7u) & ~7u) - (start & ~7u) + kChunkLen - 1) / kChunkLen
+                                 : (len ? 1u : 0u);
         }
         uint32_t total;
         const uint32_t excl = block_exclusive_sum<uint32_t, kScanThreads>(nch, &total, red);
@@ -255,27 +355,18 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
         }
         __syncthreads();
 
-        // scatter-add: a warp takes chunks of one list, lanes interleaved (coalesced)
-        for (uint32_t c = (uint32_t)warp; c < total; c += kScanWarps) {
-            const int t = c < (uint32_t)kChunkTable ? (int)c_term[c] : term_of(c_pre, nc, c);
-            const uint32_t p0 = t_start[t] + (c - c_pre[t]) * (uint32_t)kChunkLen;
-            const uint32_t pe = t_end[t];
-            const float wq = t_w[t];
-            uint32_t id[kChunkU];
-            float pr[kChunkU];
-#pragma unroll
-            for (int u = 0; u < kChunkU; u++) {
-                const uint32_t p = p0 + (uint32_t)(u * 32 + lane);
-                id[u] = 0xFFFFFFFFu;
-                pr[u] = 0.0f;
-                if (p < pe) {
-                    id[u] = __ldg(ix.pid + p);
-                    pr[u] = wq * load_value<DT>(ix.pval, p);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kChunkU; u++)
-                if (id[u] != 0xFFFFFFFFu) atomicAdd(&A[id[u]], pr[u]);
+        // scatter-add: a warp takes chunks of one list; the next chunk's loads are
+        // issued before this chunk's adds
+        uint32_t c = (uint32_t)warp;
+        Chunk cur;
+        if (c < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, c, lane, cur);
+        while (c < total) {
+            const uint32_t cn = c + kScanWarps;
+            Chunk nxt;
+            if (cn < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, cn, lane, nxt);
+            add_chunk(A, cur);
+            cur = nxt;
+            c = cn;
         }
     }
     __syncthreads();
@@ -935,7 +1026,7 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
     configure_search_kernels(ix.device);
     const DevIndex dix = ix.dev();
     const size_t scan_smem = (size_t)ix.lambda * sizeof(float);
-    // the coarse scan reads the beta-pruned queries when there are any (Alg. 4, line 3);
+    // the coarse scan reads the beta-pruned queries when there are any (Alg. 4, the query-pruning step);
     // merge and rerank check and reorder with the full queries
     ScanArgs sa{dix, scan_q ? scan_q->indptr : q_indptr, scan_q ? scan_q->indices : q_indices,
                 scan_q ? scan_q->values : q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, ws};
@@ -979,10 +1070,23 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
         chunk = std::max<int64_t>(1, std::min<int64_t>(n_queries, (int64_t)(budget / per_query)));
         chunk = std::min<int64_t>(chunk, 65535);
     }
+    const bool timing = ix.timing.load() != 0;
+    // The plain schedule runs one launch chain (scan, merge, rerank) per query.
+    // A chain is a few microseconds of dependent steps on few SMs after its
+    // scan, so up to kPlainLanes chains run at once, each on its own stream
+    // with its own workspace; query i takes lane i mod lanes. Timed runs keep
+    // one lane, so that a scan's measured duration is its own.
+    const int lanes = (batched || timing) ? 1 : (int)std::min<int64_t>(kPlainLanes, n_queries);
     Pool P{ix.pool, stream};
-    unsigned char* mem = P.alloc<unsigned char>(workspace_bytes(chunk, pl.cand_cap, pl.fcap, pl.top_cap));
-    const Workspace ws = carve_workspace(mem, chunk, pl.cand_cap, pl.fcap, pl.top_cap);
-    SINDI_CUDA(cudaMemsetAsync(mem, 0, workspace_counter_bytes(chunk), stream));
+    const size_t ws_one = workspace_bytes(chunk, pl.cand_cap, pl.fcap, pl.top_cap);
+    const size_t ws_stride = (ws_one + 255) & ~(size_t)255;
+    unsigned char* mem = P.alloc<unsigned char>(ws_stride * lanes);
+    std::vector<Workspace> wss;
+    for (int l = 0; l < lanes; l++) {
+        wss.push_back(carve_workspace(mem + ws_stride * l, chunk, pl.cand_cap, pl.fcap, pl.top_cap));
+        SINDI_CUDA(cudaMemsetAsync(mem + ws_stride * l, 0, workspace_counter_bytes(chunk), stream));
+    }
+    const Workspace& ws = wss[0];
     QueryCsr pruned{nullptr, nullptr, nullptr};
     int64_t* pq_indptr = nullptr;
     int32_t* pq_idx = nullptr;
@@ -1021,10 +1125,43 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
         pruned = QueryCsr{pq_indptr, pq_idx, pq_val};
     }
 
-    const bool timing = ix.timing.load() != 0;
     std::vector<cudaEvent_t> evs;
     bool chained = false;
-    for (int64_t q0 = 0; q0 < n_queries; q0 += chunk) {
+    if (lanes > 1) {
+        // fork: every lane starts after the work already on `stream` (queries,
+        // the zeroed workspaces); join: `stream` continues after every lane
+        std::vector<cudaStream_t> ls;
+        {
+            std::lock_guard<std::mutex> lk(ix.lane_mu);
+            while ((int)ix.lanes.size() < lanes) {
+                cudaStream_t l = nullptr;
+                SINDI_CUDA(cudaStreamCreateWithFlags(&l, cudaStreamNonBlocking));
+                ix.lanes.push_back(l);
+            }
+            ls.assign(ix.lanes.begin(), ix.lanes.begin() + lanes);
+        }
+        cudaEvent_t fork = nullptr;
+        SINDI_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        SINDI_CUDA(cudaEventRecord(fork, stream));
+        for (cudaStream_t l : ls) SINDI_CUDA(cudaStreamWaitEvent(l, fork, 0));
+        std::vector<char> lane_chained(lanes, 0);
+        for (int64_t q = 0; q < n_queries; q++) {
+            const int l = (int)(q % lanes);
+            bool c = lane_chained[l] != 0;
+            launch_group(ix, pl, wss[l], q_indptr, q_indices, q_values, q, 1, false, k, out_ids, out_scores, ls[l],
+                         &c, nullptr, nullptr, pruned.indptr ? &pruned : nullptr);
+            lane_chained[l] = c ? 1 : 0;
+        }
+        for (cudaStream_t l : ls) {
+            cudaEvent_t join = nullptr;
+            SINDI_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+            SINDI_CUDA(cudaEventRecord(join, l));
+            SINDI_CUDA(cudaStreamWaitEvent(stream, join, 0));
+            SINDI_CUDA(cudaEventDestroy(join));
+        }
+        SINDI_CUDA(cudaEventDestroy(fork));
+    }
+    for (int64_t q0 = 0; lanes == 1 && q0 < n_queries; q0 += chunk) {
         const uint32_t nq = (uint32_t)std::min<int64_t>(chunk, n_queries - q0);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (timing) {

@@ -74,6 +74,26 @@ def test_block_shapes_give_the_same_results(setup, mode):
         idx.search(*q, k=50, gamma=500, mode=mode, block=384)
 
 
+def test_plain_chains_in_flight_match_one_query_calls(setup):
+    """The plain schedule runs several queries' launch chains at once (one stream and workspace each); every
+    query's answer is the one it gets alone, and the one of a timed search (one chain at a time)."""
+    w, idx, _, (qp, qx, qv) = setup
+    q = [_dev(qp), _dev(qx), _dev(qv)]
+    for gamma in (0, 500):
+        ids, sc = [t.cpu().numpy() for t in idx.search(*q, k=50, gamma=gamma, mode="plain")]
+        idx.check()
+        for r in range(0, len(qp) - 1, 7):
+            one = [_dev(qp[r:r + 2] - qp[r]), _dev(qx[qp[r]:qp[r + 1]]), _dev(qv[qp[r]:qp[r + 1]])]
+            i1, s1 = [t.cpu().numpy() for t in idx.search(*one, k=50, gamma=gamma, mode="plain")]
+            _same(ids[r:r + 1], sc[r:r + 1], i1, s1, f"gamma {gamma} query {r}")
+        sindi.sindi_set_timing(idx.handle, True)
+        try:
+            it, st = [t.cpu().numpy() for t in idx.search(*q, k=50, gamma=gamma, mode="plain")]
+        finally:
+            sindi.sindi_set_timing(idx.handle, False)
+        _same(ids, sc, it, st, f"gamma {gamma} timed")
+
+
 def test_autotuner_meets_the_recall_target(setup, tmp_path):
     """The chosen (window, gamma, schedule, block) reaches Recall@50 >= 0.99 against the GPU exact search, and
     the same configuration holds against the FP64 oracle's brute force."""
