@@ -85,12 +85,12 @@ static size_t workspace_bytes(int64_t c, uint32_t cand_cap, uint32_t fcap, uint3
 static Workspace carve_workspace(unsigned char* base, int64_t c, uint32_t cand_cap, uint32_t fcap, uint32_t top_cap) {
     Workspace w;
     uint32_t* u = reinterpret_cast<uint32_t*>(base);
-    w.cand_count = u;
-    w.fcount = u + c;
-    w.mticket = u + 2 * c;
-    w.rticket = u + 3 * c;
-    w.top_count = u + 4 * c;
-    w.hist = u + 5 * c;
+    w.hist = u;  // first: every query's row starts 16-byte aligned
+    w.cand_count = u + c * kHistBins;
+    w.fcount = w.cand_count + c;
+    w.mticket = w.cand_count + 2 * c;
+    w.rticket = w.cand_count + 3 * c;
+    w.top_count = w.cand_count + 4 * c;
     unsigned char* q = base + workspace_counter_bytes(c);
     w.cand = reinterpret_cast<uint64_t*>(q);
     q += align256((size_t)c * cand_cap * 8);
@@ -269,6 +269,15 @@ __device__ void block_find_bin(const Get& get, uint32_t g, uint32_t* red, uint32
     __syncthreads();
 }
 
+// 16-byte asynchronous copy global -> shared (through L2), and its completion.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 struct ScanArgs {
     DevIndex ix;
     const int64_t* q_indptr;
@@ -316,11 +325,19 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     allow_next_kernel();
+    uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
+    if (a.use_partial) {
+        // the query's histogram of what its earlier windows emitted, copied
+        // while the window accumulates (a snapshot: H only grows during the
+        // launch, so any snapshot bounds the answer)
+        wait_previous_kernels();  // the workspace is free from here on
+        for (int c = threadIdx.x; c < kHistBins / 4; c += kScanThreads) cp_async16(hist + 4 * c, H + 4 * c);
+        cp_async_commit();
+    }
     const int64_t qb = a.q_indptr[r];
     const int nt = (int)(a.q_indptr[r + 1] - qb);
 
     for (uint32_t m = threadIdx.x; m < lambda; m += kScanThreads) A[m] = 0.0f;
-    for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) hist[b] = 0;
     if (threadIdx.x < kSubBins) hist2[threadIdx.x] = 0;
 
     for (int c0 = 0; c0 < nt; c0 += kTermChunk) {
@@ -377,6 +394,61 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     const int n_eff = (int)(rest < (int64_t)lambda ? rest : (int64_t)lambda);
     const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
     auto key_of = [&](int i) -> uint64_t { return result_key(A[i], (uint32_t)(gbase + i)); };
+    uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
+    uint32_t pbin = 0;  // bin of the g-th emitted candidate, when g have been emitted
+    bool bounded = false;
+    if (a.use_partial) {
+        cp_async_wait_all();
+        __syncthreads();
+        block_find_bin<kHistBins, kScanThreads>([&](int b) { return hist[b]; }, a.g, red, st);
+        bounded = st[3] >= a.g;
+        pbin = st[0];
+        __syncthreads();
+    }
+    if (bounded) {
+        // g candidates at or above bin pbin already exist, so only slots in
+        // bins >= pbin can be in the answer. When they fit the window's
+        // budget, emit all of them: no window histogram, no cut.
+        const unsigned lt = (1u << lane) - 1u;
+        uint32_t cnt = 0;
+        for (int base = warp * 32; base < n_eff; base += kScanThreads) {
+            const int i = base + lane;
+            const bool ok = i < n_eff && (float_order_bits(A[i]) >> (32 - kHistBits)) >= pbin;
+            cnt += (uint32_t)__popc(__ballot_sync(kFull, ok));
+        }
+        if (lane == 0) warp_off[warp] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (int k = 0; k < kScanWarps; k++) {
+                const uint32_t c = warp_off[k];
+                warp_off[k] = acc;
+                acc += c;
+            }
+            s_staged = acc;
+            st[0] = acc && acc <= a.win_cap ? atomicAdd(a.ws.cand_count + y, acc) : 0u;
+        }
+        __syncthreads();
+        const uint32_t n_hi = s_staged;
+        if (n_hi <= a.win_cap) {
+            uint32_t at = st[0] + warp_off[warp];
+            for (int base = warp * 32; base < n_eff && n_hi; base += kScanThreads) {
+                const int i = base + lane;
+                const uint32_t bin = i < n_eff ? float_order_bits(A[i]) >> (32 - kHistBits) : 0u;
+                const bool ok = i < n_eff && bin >= pbin;
+                const unsigned bal = __ballot_sync(kFull, ok);
+                if (ok) {
+                    const uint32_t pos = at + (uint32_t)__popc(bal & lt);
+                    if (pos < a.ws.cand_cap) cand[pos] = key_of(i);
+                    else atomicOr(ix.err, kErrCandOverflow);
+                    atomicAdd(H + bin, 1u);
+                }
+                at += (uint32_t)__popc(bal);
+            }
+            return;
+        }
+        // too many: the cut below decides (block-uniform)
+    }
     // level 1: 12-bit bins of the score key. Each warp counts its slots in a
     // private histogram of the 256 bins below the window's top bin (no
     // contention between warps); the window histogram is their sum. When the
@@ -435,15 +507,10 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
         const uint32_t rel = top_bin - b;
         return rel < (uint32_t)kRelBins - 1 ? hist[rel] : 0u;
     };
-    uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
     wait_previous_kernels();  // the workspace is free from here on
     uint32_t lo = bw;
-    if (a.use_partial) {
-        // g slots already emitted at or above a bin prove the answer lies there
-        block_find_bin<kHistBins, kScanThreads>([&](int b) { return __ldcg(H + b); }, a.g, red, st);
-        if (st[3] >= a.g && st[0] > lo) lo = st[0];
-        __syncthreads();
-    }
+    // g slots already emitted at or above a bin prove the answer lies there
+    if (bounded && pbin > lo) lo = pbin;
     const bool staged = relative && c_bw <= (uint32_t)kStageCap;  // slots >= bin lo fit in the staging area
     uint32_t n_src = (uint32_t)n_eff;
     if (staged) {
@@ -509,7 +576,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     if (threadIdx.x == 0) st[0] = total ? atomicAdd(a.ws.cand_count + y, total) : 0u;
     __syncthreads();
     pos += st[0];
-    uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
     for (int i = threadIdx.x; i < (int)n_src && mine; i += kScanThreads) {
         const uint64_t key = src_key(i);
         if (key >= thr) {
