@@ -23,6 +23,7 @@ _lock = threading.Lock()
 _lib = None
 
 F32, F16, E4M3 = 0, 1, 2
+PRUNES = {"mass": 0, "vector_number": 1, "list": 2, "mass_list": 3}
 _DTYPES = {"f32": F32, "f16": F16, "f8": E4M3, "e4m3": E4M3}
 
 _i64p = ctypes.c_void_p
@@ -61,6 +62,8 @@ def _load():
     L.orc_alpha_mass.restype = i64
     L.orc_build.argtypes = [vp, i64, dbl, i32, ctypes.POINTER(ctypes.c_int)]
     L.orc_build.restype = vp
+    L.orc_build_ex.argtypes = [vp, i64, dbl, i32, i32, i64, ctypes.POINTER(ctypes.c_int)]
+    L.orc_build_ex.restype = vp
     L.orc_index_free.argtypes = [vp]
     L.orc_index_sigma.argtypes = [vp]
     L.orc_index_sigma.restype = i64
@@ -166,14 +169,20 @@ class Index:
     Lists I_{j,w} (Sec. 3.3.1) hold (global id, value) in ascending id; the
     unpruned dataset stays attached for reordering (Algorithm 3 returns it)."""
 
-    def __init__(self, D: Dataset, window: int, alpha: float = 1.0, dtype: str = "f32"):
+    def __init__(self, D: Dataset, window: int, alpha: float = 1.0, dtype: str = "f32", prune: str = "mass",
+                 prune_n: int = 0):
+        """prune: "mass" (alpha-mass, Sec. 4.1), "vector_number" (prune_n entries per document),
+        "list" (prune_n entries per list I_j) or "mass_list" (alpha-mass, then list pruning)."""
         L = _load()
         self.D = D
         self.window = int(window)
         self.alpha = float(alpha)
         self.dtype = dtype
+        self.prune = prune
+        self.prune_n = int(prune_n)
         err = ctypes.c_int(0)
-        self._h = L.orc_build(D._h, self.window, self.alpha, _DTYPES[dtype], ctypes.byref(err))
+        self._h = L.orc_build_ex(D._h, self.window, self.alpha, _DTYPES[dtype], PRUNES[prune], self.prune_n,
+                                 ctypes.byref(err))
         if not self._h:
             raise ValueError(f"oracle build failed (code {err.value})")
         self.sigma = int(L.orc_index_sigma(self._h))

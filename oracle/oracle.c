@@ -15,6 +15,9 @@
  *                                                       Subvector" (Sec. 4.1)
  *   - value-storing inverted lists I_{j,w} ............ Sec. 3.1, 3.3.1, Algorithm 1
  *   - pruned construction (keeps D for reordering) .... Algorithm 3
+ *   - the other pruning methods the paper compares ...... Sec. 4.1 (List
+ *     Pruning, Vector Number Pruning) and the ablation of Sec. 5 (List
+ *     Pruning combined with Mass Ratio Pruning)
  *   - window-accumulation search with a min-heap ...... Algorithm 2
  *   - beta-mass query + gamma candidates + reorder .... Algorithm 4, Sec. 4.2
  *   - FP16 / FP8-E4M3 posting values (reduced-precision form; the paper has
@@ -30,7 +33,12 @@
  *   - explicit zeros in the input are not entries (Definition 1) and are
  *     dropped; duplicate dims in a row and dims outside [0, d) are errors;
  *   - the terms of a query are visited in ascending dim order;
- *   - within a list I_{j,w}, postings are kept in ascending document id.
+ *   - within a list I_{j,w}, postings are kept in ascending document id;
+ *   - Vector Number Pruning keeps the first vn entries in the alpha-mass
+ *     order pi (|x| desc, equal |x| by lower dim); List Pruning keeps the
+ *     l' entries of largest |x| of each list I_j over all windows, equal |x|
+ *     by lower document id; the combination applies alpha-mass first and
+ *     List Pruning to the lists it leaves.
  *
  * Arithmetic: every input is FP32 and is widened exactly to FP64; all sums,
  * products and comparisons below are FP64, evaluated in the order written
@@ -276,6 +284,28 @@ static int64_t alpha_mass(const int32_t* dim, const double* val, int64_t n, doub
     return r;
 }
 
+/* Vector Number Pruning (Sec. 4.1): the first min(vn, n) entries of the row
+   in pi order. kept_pos receives their positions, in that order. */
+static int64_t vector_number(const int32_t* dim, const double* val, int64_t n, int64_t vn, int64_t* kept_pos,
+                             orc_mag* work) {
+    if (n == 0) return 0;
+    for (int64_t t = 0; t < n; t++) { work[t].a = fabs(val[t]); work[t].j = dim[t]; work[t].pos = t; }
+    qsort(work, (size_t)n, sizeof(orc_mag), cmp_mag);
+    int64_t r = n < vn ? n : vn;
+    for (int64_t t = 0; t < r; t++) kept_pos[t] = work[t].pos;
+    return r;
+}
+
+/* List Pruning order: |x| descending, then lower document id. */
+typedef struct { double a; int64_t doc; int64_t pos; } orc_lmag;
+static int cmp_lmag(const void* pa, const void* pb) {
+    const orc_lmag* a = (const orc_lmag*)pa;
+    const orc_lmag* b = (const orc_lmag*)pb;
+    if (a->a > b->a) return -1;
+    if (a->a < b->a) return 1;
+    return (a->doc < b->doc) ? -1 : (a->doc > b->doc);
+}
+
 /* alpha-mass of one raw row (FP32 values), positions refer to the input row. */
 int64_t orc_alpha_mass(const int32_t* dim, const float* val, int64_t n, double alpha, int64_t* kept_pos) {
     double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -393,11 +423,25 @@ void orc_index_free(orc_index* I) {
     free(I->seg); free(I->pid); free(I->pval); free(I->scale); free(I->kept_count); free(I);
 }
 
+#define ORC_PRUNE_MASS 0
+#define ORC_PRUNE_VECTOR_NUMBER 1
+#define ORC_PRUNE_LIST 2
+#define ORC_PRUNE_MASS_LIST 3
+
 /* Algorithm 3 (ApproximateSindiConstruction) with Algorithm 1 inside it.
-   lambda in [1, ...]; alpha in (0, 1]; dtype ORC_F32 | ORC_F16 | ORC_E4M3. */
-orc_index* orc_build(const orc_dataset* D, int64_t lambda, double alpha, int32_t dtype, int* err) {
+   lambda in [1, ...]; alpha in (0, 1]; dtype ORC_F32 | ORC_F16 | ORC_E4M3.
+   prune selects the document pruning (Sec. 4.1): MASS (alpha-mass, the
+   method's own), VECTOR_NUMBER (n_keep entries per document), LIST (n_keep
+   entries per list I_j) or MASS_LIST (alpha-mass, then LIST). alpha is
+   used by MASS and MASS_LIST only; n_keep >= 1 by the other three. */
+orc_index* orc_build_ex(const orc_dataset* D, int64_t lambda, double alpha, int32_t dtype, int32_t prune,
+                        int64_t n_keep, int* err) {
     *err = ORC_OK;
     if (!D || lambda <= 0 || !(alpha > 0.0 && alpha <= 1.0) || dtype < 0 || dtype > 2) { *err = ORC_EINVAL; return NULL; }
+    if (prune < ORC_PRUNE_MASS || prune > ORC_PRUNE_MASS_LIST || (prune != ORC_PRUNE_MASS && n_keep < 1)) {
+        *err = ORC_EINVAL; return NULL;
+    }
+    const double doc_alpha = (prune == ORC_PRUNE_MASS || prune == ORC_PRUNE_MASS_LIST) ? alpha : 1.0;
     orc_index* I = (orc_index*)calloc(1, sizeof(orc_index));
     if (!I) { *err = ORC_ENOMEM; return NULL; }
     I->D = D; I->lambda = lambda; I->d = D->d; I->dtype = dtype;
@@ -423,7 +467,8 @@ orc_index* orc_build(const orc_dataset* D, int64_t lambda, double alpha, int32_t
     kptr[0] = 0;
     for (int64_t i = 0; i < n; i++) {
         int64_t b = D->ptr[i], m = D->ptr[i + 1] - b;
-        int64_t r = alpha_mass(D->dim + b, D->val + b, m, alpha, kpos, work);
+        int64_t r = prune == ORC_PRUNE_VECTOR_NUMBER ? vector_number(D->dim + b, D->val + b, m, n_keep, kpos, work)
+                                                     : alpha_mass(D->dim + b, D->val + b, m, doc_alpha, kpos, work);
         I->kept_count[i] = r;
         memset(keep, 0, (size_t)(m > 0 ? m : 1));
         for (int64_t t = 0; t < r; t++) keep[kpos[t]] = 1;
@@ -463,6 +508,37 @@ orc_index* orc_build(const orc_dataset* D, int64_t lambda, double alpha, int32_t
         free(fill);
     }
     free(kptr); free(kdim); free(kval);
+
+    /* List Pruning (Sec. 4.1): list I_j (all windows) keeps its n_keep
+       entries of largest |x|, equal |x| by lower document id; the kept ones
+       stay in ascending document order. */
+    if (prune == ORC_PRUNE_LIST || prune == ORC_PRUNE_MASS_LIST) {
+        int64_t maxlen = 0;
+        for (int64_t j = 0; j < d; j++) if (xptr[j + 1] - xptr[j] > maxlen) maxlen = xptr[j + 1] - xptr[j];
+        orc_lmag* lw = (orc_lmag*)malloc(sizeof(orc_lmag) * (size_t)(maxlen > 0 ? maxlen : 1));
+        char* lkeep = (char*)malloc((size_t)(maxlen > 0 ? maxlen : 1));
+        if (!lw || !lkeep) {
+            free(lw); free(lkeep); free(xptr); free(xdoc); free(xval); orc_index_free(I);
+            *err = ORC_ENOMEM; return NULL;
+        }
+        int64_t wpos = 0;
+        for (int64_t j = 0; j < d; j++) {
+            const int64_t b = xptr[j], e = xptr[j + 1], len = e - b;
+            for (int64_t t = 0; t < len; t++) {
+                lw[t].a = fabs(xval[b + t]); lw[t].doc = xdoc[b + t]; lw[t].pos = t; lkeep[t] = 0;
+            }
+            qsort(lw, (size_t)len, sizeof(orc_lmag), cmp_lmag);
+            for (int64_t t = 0; t < len; t++) {
+                if (t < n_keep) lkeep[lw[t].pos] = 1;
+                else I->kept_count[lw[t].doc]--;
+            }
+            xptr[j] = wpos;
+            for (int64_t t = 0; t < len; t++)
+                if (lkeep[t]) { xdoc[wpos] = xdoc[b + t]; xval[wpos] = xval[b + t]; wpos++; }
+        }
+        xptr[d] = wpos;
+        free(lw); free(lkeep);
+    }
 
     /* lengths of every I_{j,w}, then appends in (j, ascending i) order */
     for (int64_t j = 0; j < d; j++)
@@ -506,6 +582,10 @@ orc_index* orc_build(const orc_dataset* D, int64_t lambda, double alpha, int32_t
     }
     free(xptr); free(xdoc); free(xval);
     return I;
+}
+
+orc_index* orc_build(const orc_dataset* D, int64_t lambda, double alpha, int32_t dtype, int* err) {
+    return orc_build_ex(D, lambda, alpha, dtype, ORC_PRUNE_MASS, 0, err);
 }
 
 int64_t orc_index_sigma(const orc_index* I) { return I->sigma; }

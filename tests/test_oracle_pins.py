@@ -265,6 +265,94 @@ def test_pruned_lists_hold_exactly_the_alpha_mass_entries():
     assert got == want and I.postings == sum(kept)
 
 
+def _entries(I):
+    """(doc, dim, stored value) of every posting of an oracle index, and its kept counts."""
+    seg, pid, pval, scale, kept = I.export()
+    out = set()
+    for j in range(I.D.dim):
+        for t in range(seg[j * I.sigma], seg[(j + 1) * I.sigma]):
+            out.add((int(pid[t]), j, float(pval[t])))
+    return out, kept
+
+
+def _doc_rows(ip, ix, v):
+    return [{(i, int(ix[t]), float(v[t])) for t in range(ip[i], ip[i + 1])} for i in range(len(ip) - 1)]
+
+
+def test_pruning_methods_hand_example():
+    """Vector Number, List and Mass+List pruning (Sec. 4.1, ablation of Sec. 5) on a 3 x 4 example worked
+    by hand: doc0 = {0: .5, 1: 2, 3: 1}, doc1 = {1: 3, 2: .25}, doc2 = {0: 4, 1: 2, 2: 2}."""
+    ip = np.array([0, 3, 5, 8], np.int64)
+    ix = np.array([0, 1, 3, 1, 2, 0, 1, 2], np.int32)
+    v = np.array([.5, 2, 1, 3, .25, 4, 2, 2], np.float32)
+    D = oracle.Dataset(ip, ix, v, 4)
+    cases = {
+        # two largest |x| per doc; doc2's tie at |x| = 2 goes to the lower dim (1)
+        ("vector_number", 2, 1.0): ({(0, 1, 2.0), (0, 3, 1.0), (1, 1, 3.0), (1, 2, .25), (2, 0, 4.0), (2, 1, 2.0)},
+                                    [2, 2, 2]),
+        # largest |x| per list: dim0 doc2, dim1 doc1, dim2 doc2, dim3 doc0
+        ("list", 1, 1.0): ({(2, 0, 4.0), (1, 1, 3.0), (2, 2, 2.0), (0, 3, 1.0)}, [1, 1, 2]),
+        # two per list: dim1 keeps doc1 (3) and, of the tie at 2 between doc0 and doc2, doc0
+        ("list", 2, 1.0): ({(0, 0, .5), (2, 0, 4.0), (1, 1, 3.0), (0, 1, 2.0), (1, 2, .25), (2, 2, 2.0),
+                            (0, 3, 1.0)}, [3, 2, 2]),
+        # alpha 0.5 keeps {1: 2}, {1: 3}, {0: 4} (4 >= 0.5 * 8 exactly); then dim1 keeps doc1 only
+        ("mass_list", 1, 0.5): ({(1, 1, 3.0), (2, 0, 4.0)}, [0, 1, 1]),
+    }
+    for (prune, n, alpha), (want, want_kept) in cases.items():
+        I = oracle.Index(D, window=2, alpha=alpha, prune=prune, prune_n=n)
+        got, kept = _entries(I)
+        assert got == want, (prune, n, sorted(got))
+        assert kept.tolist() == want_kept, (prune, n)
+        assert I.postings == len(want)
+
+
+def test_vector_number_pruning_invariants():
+    """Every document keeps min(vn, nnz) entries, none smaller in |x| than one it drops (equal |x|: the lower
+    dim stays); vn >= every nnz leaves the unpruned index."""
+    ip, ix, v = datagen.random_csr(400, 60, 10.0, seed=41)
+    v = np.round(v * 4) / 4 + 0.25  # coarse values: many equal |x| within a row
+    v = v.astype(np.float32)
+    D = oracle.Dataset(ip, ix, v, 60)
+    rows = _doc_rows(ip, ix, v)
+    full, _ = _entries(oracle.Index(D, window=32, alpha=1.0))
+    for vn in (1, 3, 7, 1000):
+        got, kept = _entries(oracle.Index(D, window=32, prune="vector_number", prune_n=vn))
+        for i, row in enumerate(rows):
+            mine = {e for e in got if e[0] == i}
+            assert mine <= row and len(mine) == min(vn, len(row)) == kept[i]
+            for (_, jk, xk) in mine:
+                for (_, jd, xd) in row - mine:
+                    assert abs(xk) > abs(xd) or (abs(xk) == abs(xd) and jk < jd)
+        if vn == 1000:
+            assert got == full
+
+
+def test_list_pruning_invariants():
+    """Every list I_j keeps min(l', |I_j|) entries, none smaller in |x| than one it drops (equal |x|: the
+    lower doc stays); the kept counts per document add up; l' >= every list length leaves the unpruned
+    index; alpha-mass followed by list pruning is list pruning of the alpha-mass lists."""
+    ip, ix, v = datagen.random_csr(500, 30, 9.0, seed=43)
+    v = (np.round(v * 4) / 4 + 0.25).astype(np.float32)
+    D = oracle.Dataset(ip, ix, v, 30)
+    full, _ = _entries(oracle.Index(D, window=64, alpha=1.0))
+    mass, _ = _entries(oracle.Index(D, window=64, alpha=0.6))
+    for base, prune, alpha in ((full, "list", 1.0), (mass, "mass_list", 0.6)):
+        for lp in (1, 4, 25, 10**6):
+            got, kept = _entries(oracle.Index(D, window=64, alpha=alpha, prune=prune, prune_n=lp))
+            assert got <= base
+            for j in range(30):
+                lst = {e for e in base if e[1] == j}
+                mine = {e for e in got if e[1] == j}
+                assert len(mine) == min(lp, len(lst))
+                for (ik, _, xk) in mine:
+                    for (idr, _, xd) in lst - mine:
+                        assert abs(xk) > abs(xd) or (abs(xk) == abs(xd) and ik < idr)
+            for i in range(500):
+                assert kept[i] == sum(1 for e in got if e[0] == i)
+            if lp == 10**6:
+                assert got == base
+
+
 # --------------------------------------------------------------------------
 # Algorithms 2 and 4: search
 # --------------------------------------------------------------------------
