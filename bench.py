@@ -15,6 +15,7 @@ the data path); the barrier and the max over ranks use torch.distributed.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -51,6 +52,10 @@ def parse():
     p.add_argument("--value-dtype", choices=["f32", "f16", "f8"], default=None,
                    help="posting value type of the main index (default: the workload's)")
     p.add_argument("--no-forms", action="store_true", help="skip the batched / low-precision / serving side lines")
+    p.add_argument("--ablation", action="store_true",
+                   help="add the pruning-method ablation (mass / vector-number / list / mass+list) of the workload")
+    p.add_argument("--sparsity-sweep", action="store_true",
+                   help="add the uniform-random sparsity sweep (1M docs x d in 10k..100k), autotuned to recall 0.99")
     p.add_argument("--serve-load", type=float, default=0.5,
                    help="serving leg: offered load as a fraction of the batched schedule's QPS")
     p.add_argument("--serve-seconds", type=float, default=4.0)
@@ -182,6 +187,91 @@ def profile_traffic(kernel_src_sha):
     if m and t and m.group(1) == kernel_src_sha:
         return float(t.group(1))
     return None
+
+
+def scatter_peak(window: int, block: int = 512):
+    """Measured FP32 shared-memory atomicAdd rate (adds/s) of this GPU: the probe library fills every SM with
+    `block`-thread blocks that each add at random slots of a `window`-float shared array, as the scan does."""
+    path = os.path.join(ROOT, "paper_2509_08395_gb300", "lib", "libsindi_probe.so")
+    if not os.path.exists(path):
+        return None
+    lib = ctypes.CDLL(path)
+    f = lib.sindi_probe_scatter_peak
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_double)]
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = f(window, block, 256, ctypes.byref(rate), ctypes.byref(ms))
+    return rate.value if rc == 0 else None
+
+
+def _timed_qps(torch, fn, nq, reps, flush, stream):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return nq * reps / (tot / 1000.0)
+
+
+def _recall_rows(ids, truth):
+    return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / max(1, len(b)) for a, b in zip(ids, truth)]))
+
+
+def pruning_ablation(sindi, torch, dev, w, ip, ix, v, q_dev, nq, steps, flush, stream):
+    """The pruning methods of Sec. 4.1 on the workload (ablation of Sec. 5): postings kept, Recall@k with the
+    workload's reorder depth against the exact GPU search (alpha = 1, no reorder), and plain-schedule QPS."""
+    grid = ([("mass", 0, a) for a in (0.4, 0.5, 0.6)] + [("vector_number", n, 1.0) for n in (15, 25, 40)] +
+            [("list", n, 1.0) for n in (2000, 5000, 10000)] + [("mass_list", n, w.alpha) for n in (2000, 5000)])
+    dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
+    with sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=1.0) as exact:
+        truth, _ = exact.search(*q_dev, k=w.k, gamma=0, mode="batched")
+        truth = truth.cpu().numpy().view(np.uint32)
+    rows = []
+    for prune, n, a in grid:
+        with sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=a, prune=prune, prune_n=n) as idx:
+            ids = torch.empty((nq, w.k), dtype=torch.int32, device=dev)
+            sc = torch.empty((nq, w.k), dtype=torch.float32, device=dev)
+            qps = _timed_qps(torch, lambda: idx.search(*q_dev, k=w.k, gamma=w.gamma, mode="plain", out=(ids, sc)),
+                             nq, steps, flush, stream)
+            idx.check()
+            rows.append({"prune": prune, "prune_n": n, "alpha": a, "postings": idx.info["postings"],
+                         "recall_at_k": _recall_rows(ids.cpu().numpy().view(np.uint32), truth), "qps": qps,
+                         "gamma": w.gamma})
+    return {"rows": rows, "recall_vs": "GPU exact search (alpha = 1, gamma = 0)", "schedule": "plain"}
+
+
+def sparsity_sweep(sindi, torch, dev, steps, flush, stream):
+    """Sec. 5's uniform-random sparsity sweep: for each d, the autotuned (alpha, window, gamma, schedule) with
+    the highest QPS at Recall@50 >= 0.99 against the exact GPU search, and that exact search's own QPS."""
+    import datagen
+    from paper_2509_08395_gb300 import autotune
+
+    out = []
+    for d in (10, 30, 50, 70, 100):
+        w = datagen.WORKLOADS[f"uniform-1m-d{d}k"]
+        ip, ix, v = datagen.docs(w)
+        qp, qx, qv = datagen.queries(w)
+        dd = [torch.from_numpy(a).to(dev) for a in (ip, ix, v)]
+        qd = [torch.from_numpy(a).to(dev) for a in (qp, qx, qv)]
+        nq = len(qp) - 1
+        t0 = time.perf_counter()
+        tuned = autotune.autotune(*dd, w.dim, *qd, k=w.k, alpha=w.alpha, alphas=(0.3, 0.5, 0.7, 0.9),
+                                  recall_target=0.99, blocks=(512,))
+        with sindi.Index(*dd, w.dim, window=w.window, alpha=1.0) as exact:
+            exact_qps = _timed_qps(torch, lambda: exact.search(*qd, k=w.k, gamma=0, mode="batched"), nq, steps,
+                                   flush, stream)
+            postings_exact = exact.info["postings"]
+        out.append({"workload": w.name, "dim": w.dim, "choice": tuned["choice"], "exact_batched_qps": exact_qps,
+                    "postings_unpruned": postings_exact, "seconds": time.perf_counter() - t0})
+        del dd, qd
+    return out
 
 
 def source_sha():
@@ -423,10 +513,11 @@ def main():
                              float((nterms[g0:g0 + group] * (sigma * 8 + 8)).sum()))
         alg_bytes_per_launch = float(np.mean(per_group))
     achieved_gbs = alg_bytes_per_launch / (scan_ms_per_launch / 1000.0) / 1e9
-    # scatter-adds (one shared-memory atomic per posting and query) against the shared-memory bound:
-    # 152 SMs x 32 banks x the max SM clock, one 4-byte atomic per bank per clock
+    # scatter-adds (one FP32 shared-memory atomicAdd per posting and query): the scan kernel's own rate
+    # (timed pass), the whole step's rate, and the probe's measured rate of that operation on this GPU
     adds_per_s = float(touched.sum()) * args.steps / (st2["scan_ms"] / 1000.0)
-    adds_peak = 152 * 32 * 2.07e9
+    adds_per_s_step = float(touched.sum()) * args.steps / (dev_ms_max / 1000.0)
+    adds_peak = scatter_peak(int(info["window"]))
     peak, peak_kind = measured_hbm_peak()
     sha = source_sha()
 
@@ -503,6 +594,13 @@ def main():
                 _, csc = lp.search(*cq, k=w.k, gamma=0)
                 forms[dt + "_" + args.mode] = {"qps": qps, "_ids": oi.cpu().numpy().view(np.uint32),
                                                "_sc": os_.cpu().numpy(), "_coarse": csc.cpu().numpy()}
+
+    ablation = None
+    if args.ablation and rank == 0:
+        ablation = pruning_ablation(sindi, torch, dev, w, ip, ix, v, q_dev, nq, args.steps, flush, stream)
+    sweep = None
+    if args.sparsity_sweep and rank == 0:
+        sweep = sparsity_sweep(sindi, torch, dev, args.steps, flush, stream)
 
     serving = None
     if rank == 0 and (args.serve_sweep or not args.no_forms):
@@ -604,12 +702,17 @@ def main():
                      "alg_bytes_per_launch": alg_bytes_per_launch, "ms_per_launch": scan_ms_per_launch,
                      "postings_per_query": float(touched.mean()),
                      "logical_gbs": float(per_query_bytes.sum()) * args.steps / (st2["scan_ms"] / 1000.0) / 1e9,
-                     "scatter_adds": {"per_s": adds_per_s, "peak": adds_peak, "frac": adds_per_s / adds_peak,
+                     "scatter_adds": {"per_s": adds_per_s, "per_s_in_step": adds_per_s_step, "peak": adds_peak,
+                                      "frac": adds_per_s / adds_peak if adds_peak else None,
+                                      "frac_in_step": adds_per_s_step / adds_peak if adds_peak else None,
                                       "unit": "posting updates/s",
-                                      "peak_from": "152 SMs x 32 shared-memory banks x 2.07 GHz"}},
+                                      "peak_from": "measured: FP32 shared-memory atomicAdd probe at random slots "
+                                                   "of a window-sized array, every SM full (libsindi_probe)"}},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "forms": forms,
+        "pruning_ablation": ablation,
+        "sparsity_sweep": sweep,
         "serving": serving,
         "scan_source_sha256": sha,
     }

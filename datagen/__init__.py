@@ -157,6 +157,19 @@ WORKLOADS: dict[str, Workload] = {
 }
 
 
+# the sparsity sweep of Sec. 5 (RANDOM-1M): 1M documents of 120 entries, dims and values uniform at
+# random, d from 10k to 100k; queries from the same generator
+for _d in (10_000, 30_000, 50_000, 70_000, 100_000):
+    _n = f"uniform-1m-d{_d // 1000}k"
+    WORKLOADS[_n] = Workload(
+        name=_n, dim=_d, zipf_s=0.0,
+        docs=RowDist(1_000_000, NNZ_UNIFORM, 120, 120, 120, 120, val_kind=VAL_UNIFORM),
+        queries=RowDist(1_000, NNZ_UNIFORM, 120, 120, 120, 120, val_kind=VAL_UNIFORM),
+        k=50, gamma=500, alpha=0.5, window=8192, doc_seed=1006, query_seed=2006,
+    )
+del _d, _n
+
+
 def generate(dist: RowDist, dim: int, zipf_s: float, seed: int):
     """Draw one CSR matrix. Returns (indptr int64[n+1], indices int32[nnz], values float32[nnz])."""
     lib = _load()

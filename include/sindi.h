@@ -75,13 +75,38 @@ typedef enum {
     SINDI_MODE_BATCHED = 1   /* all queries of the call in shared launches             */
 } sindi_mode;
 
-/* Parameters of Algorithm 3. */
+/* Which entries of the documents become postings (Sec. 4.1 names three
+   pruning methods and the ablation of Sec. 5 also combines two):
+   - MASS (Mass Ratio Pruning, the method's own): every document keeps its
+     alpha-mass subvector, the shortest prefix of its entries in pi order
+     (|x| descending; equal |x|: lower dim first) whose |x| sum reaches
+     alpha * mass(x).
+   - VECTOR_NUMBER (Vector Number Pruning): every document keeps the first
+     min(prune_n, nnz) entries in pi order.
+   - LIST (List Pruning): every list I_j (all windows) keeps its prune_n
+     entries of largest |x|; equal |x|: lower document id first.
+   - MASS_LIST: MASS first, then LIST on the lists MASS leaves.
+   The unpruned documents are kept for reordering in every case. */
+typedef enum {
+    SINDI_PRUNE_MASS = 0,
+    SINDI_PRUNE_VECTOR_NUMBER = 1,
+    SINDI_PRUNE_LIST = 2,
+    SINDI_PRUNE_MASS_LIST = 3
+} sindi_prune;
+
+/* Parameters of Algorithm 3. A zero-filled struct with alpha = 1 is the
+   unpruned index. */
 typedef struct {
     uint32_t window;       /* lambda, documents per window (Sec. 3.3.1); 1..32768.
                               0 picks a default. A window's FP32 score array lives
                               in one thread block's shared memory.                */
     int32_t value_dtype;   /* sindi_dtype                                          */
-    double alpha;          /* document pruning ratio in (0, 1]; 1 = no pruning     */
+    double alpha;          /* document pruning ratio in (0, 1]; 1 = no pruning.
+                              Used by MASS and MASS_LIST, ignored otherwise      */
+    int32_t prune;         /* sindi_prune                                          */
+    uint32_t prune_n;      /* VECTOR_NUMBER: entries kept per document; LIST and
+                              MASS_LIST: entries kept per list; >= 1 for those,
+                              ignored by MASS                                     */
 } sindi_build_params;
 
 /* Parameters of Algorithm 4. */
@@ -110,6 +135,8 @@ typedef struct {
     int64_t index_bytes;   /* device bytes of lists + offsets + scales            */
     int64_t doc_bytes;     /* device bytes of the unpruned documents              */
     double alpha;
+    int32_t prune;         /* sindi_prune of the build                            */
+    uint32_t prune_n;      /* its prune_n (0 for MASS)                            */
 } sindi_index_info_t;
 
 /* Counters of the calling index (for benchmarks). */

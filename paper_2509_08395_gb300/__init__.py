@@ -6,6 +6,7 @@ The computation lives in hand-written CUDA kernels behind the C ABI of
 from .sindi import (  # noqa: F401
     DTYPES,
     MODES,
+    PRUNES,
     Index,
     Plan,
     Server,

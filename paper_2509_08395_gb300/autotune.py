@@ -66,16 +66,18 @@ def default_windows(n_docs: int, sm_count: int):
 def autotune(indptr, indices, values, dim: int, q_indptr, q_indices, q_values, k: int, alpha: float,
              recall_target: float = 0.99, windows=None, gammas=(100, 200, 300, 500, 750, 1000, 1500, 2000, 4000),
              blocks=(256, 512, 1024), modes=("plain", "batched"), value_dtype: str = "f32", repeats: int = 3,
-             cache: str | None = None) -> dict:
-    """Tune (window, gamma, schedule, block) on device tensors of documents and sample queries.
+             cache: str | None = None, alphas=None) -> dict:
+    """Tune (window, gamma, schedule, block) on device tensors of documents and sample queries; with
+    `alphas`, the pruning ratio too (each alpha is tried at every window).
 
     Returns the chosen configuration and the table of every measurement."""
+    alphas = [float(alpha)] if alphas is None else [float(a) for a in alphas]
     import torch
 
     dev = q_indptr.device
     props = torch.cuda.get_device_properties(dev)
     n_docs = int(indptr.shape[0] - 1)
-    key = json.dumps([n_docs, int(dim), int(indices.shape[0]), float(alpha), int(k), float(recall_target),
+    key = json.dumps([n_docs, int(dim), int(indices.shape[0]), alphas, int(k), float(recall_target),
                       value_dtype, props.name, int(q_indptr.shape[0] - 1)])
     if cache and os.path.exists(cache):
         with open(cache) as f:
@@ -91,28 +93,30 @@ def autotune(indptr, indices, values, dim: int, q_indptr, q_indices, q_values, k
         truth = truth.cpu().numpy().view(np.uint32)
     table = []
     best = None
-    for w in windows:
-        with sindi.Index(indptr, indices, values, dim, window=w, alpha=alpha, value_dtype=value_dtype) as idx:
-            chosen = None
-            for g in gammas:
-                if g < k:
+    for a in alphas:
+        for w in windows:
+            with sindi.Index(indptr, indices, values, dim, window=w, alpha=a, value_dtype=value_dtype) as idx:
+                chosen = None
+                for g in gammas:
+                    if g < k:
+                        continue
+                    ids, _ = idx.search(*q, k=k, gamma=g, mode="batched")
+                    r = _recall(ids.cpu().numpy().view(np.uint32), truth)
+                    table.append({"alpha": a, "window": w, "gamma": g, "recall": r})
+                    if r >= recall_target:
+                        chosen = (g, r)
+                        break
+                if chosen is None:
                     continue
-                ids, _ = idx.search(*q, k=k, gamma=g, mode="batched")
-                r = _recall(ids.cpu().numpy().view(np.uint32), truth)
-                table.append({"window": w, "gamma": g, "recall": r})
-                if r >= recall_target:
-                    chosen = (g, r)
-                    break
-            if chosen is None:
-                continue
-            g, r = chosen
-            for mode in modes:
-                for b in blocks:
-                    qps, _ = _time_search(idx, q, k, g, mode, b, repeats)
-                    row = {"window": w, "gamma": g, "recall": r, "mode": mode, "block": b, "qps": qps}
-                    table.append(row)
-                    if best is None or qps > best["qps"]:
-                        best = dict(row)
+                g, r = chosen
+                for mode in modes:
+                    for b in blocks:
+                        qps, _ = _time_search(idx, q, k, g, mode, b, repeats)
+                        row = {"alpha": a, "window": w, "gamma": g, "recall": r, "mode": mode, "block": b,
+                               "qps": qps}
+                        table.append(row)
+                        if best is None or qps > best["qps"]:
+                            best = dict(row)
     result = {"choice": best, "recall_target": recall_target, "table": table,
               "seconds": time.perf_counter() - t0, "gpu": props.name}
     if cache:

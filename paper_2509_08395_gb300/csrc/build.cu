@@ -38,11 +38,12 @@ void launch_validate_indptr(const int64_t* indptr, int64_t n, uint32_t* err, cud
 }
 
 // One warp per document. Validates the row (dims in range, finite values, no
-// duplicate dim), computes r_i = |alpha-mass(x_i)| and writes the kept
-// entries (in pi order) to kdim/kval at the row's own input positions.
+// duplicate dim), computes r_i = |alpha-mass(x_i)| (or, when vn > 0, r_i =
+// min(vn, nnz): Vector Number Pruning) and writes the kept entries (in pi
+// order) to kdim/kval at the row's own input positions.
 __global__ void __launch_bounds__(kPruneWarps * 32) prune_rows_kernel(
     const int64_t* indptr, const int32_t* indices, const float* values, int64_t n, int32_t dim, double alpha,
-    uint32_t* kept, int32_t* kdim, float* kval, uint32_t* long_rows, uint32_t* n_long, uint32_t* err) {
+    uint32_t vn, uint32_t* kept, int32_t* kdim, float* kval, uint32_t* long_rows, uint32_t* n_long, uint32_t* err) {
     __shared__ uint64_t sm[kPruneWarps][kPruneRowCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t* s = sm[warp];
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(kPruneWarps * 32) prune_rows_kernel(
         __syncwarp();
         warp_bitonic_sort_asc(s, p2);
         int r = 0;
-        if (lane == 0) r = alpha_mass_count(s, nz, alpha);
+        if (lane == 0) r = vn ? (nz < (int)vn ? nz : (int)vn) : alpha_mass_count(s, nz, alpha);
         r = __shfl_sync(kFull, r, 0);
         for (int t = lane; t < r; t += 32) {
             kdim[b + t] = mass_key_dim(s[t]);
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kPruneWarps * 32) prune_rows_kernel(
 constexpr int kLongBlock = 512;
 __global__ void __launch_bounds__(kLongBlock) prune_long_rows_kernel(
     const int64_t* indptr, const int32_t* indices, const float* values, const uint32_t* rows, int32_t dim,
-    double alpha, uint32_t* kept, int32_t* kdim, float* kval, uint32_t* err) {
+    double alpha, uint32_t vn, uint32_t* kept, int32_t* kdim, float* kval, uint32_t* err) {
     extern __shared__ uint64_t s[];
     __shared__ int flags[2];
     __shared__ int s_r;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kLongBlock) prune_long_rows_kernel(
     block_bitonic_sort_desc<kLongBlock>(s, p2);
     for (int t = threadIdx.x; t < p2; t += kLongBlock) s[t] = ~s[t];
     __syncthreads();
-    if (threadIdx.x == 0) s_r = alpha_mass_count(s, s_nz, alpha);
+    if (threadIdx.x == 0) s_r = vn ? (s_nz < (int)vn ? s_nz : (int)vn) : alpha_mass_count(s, s_nz, alpha);
     __syncthreads();
     const int r = s_r;
     for (int t = threadIdx.x; t < r; t += kLongBlock) {
@@ -260,6 +261,46 @@ __global__ void pack_kernel(const uint32_t* sdim, const uint32_t* sdoc, const ui
     }
 }
 
+// List Pruning (Sec. 4.1): every list I_j keeps its `lp` entries of largest
+// |x|, equal |x| by lower document id. Postings arrive in (dim, doc) order;
+// a stable sort by (dim, |x| descending) then ranks every entry in its list.
+// Sort keys: 0x7FFFFFFF - |x| bits (ascending = |x| descending), and the
+// entry's position.
+__global__ void lp_keys_kernel(const uint32_t* sval, int64_t P, uint32_t* inv, uint32_t* pos) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        inv[p] = 0x7FFFFFFFu - (sval[p] & 0x7FFFFFFFu);
+        pos[p] = (uint32_t)p;
+    }
+}
+
+// Entry t of the (dim, |x| desc, doc asc) order has rank t - start(list) in
+// its list; the first lp survive. A dropped entry leaves its document's count.
+__global__ void lp_mark_kernel(const uint32_t* dim_sorted, const uint32_t* pos_sorted, int64_t P, const uint32_t* seg,
+                               uint32_t sigma, uint32_t lp, const uint32_t* sdoc, uint32_t* keep, uint32_t* kept) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < P; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = dim_sorted[t];
+        const uint32_t p = pos_sorted[t];
+        const bool k = (uint64_t)t - seg[(uint64_t)j * sigma] < lp;
+        keep[p] = k ? 1u : 0u;
+        if (!k) atomicSub(&kept[sdoc[p]], 1u);
+    }
+}
+
+// Entries with keep[p] = 1 move to off[p] (exclusive scan of keep); the
+// (dim, doc) order is kept.
+__global__ void lp_compact_kernel(const uint32_t* keep, const uint32_t* off, int64_t P, const uint32_t* sdim,
+                                  const uint32_t* sdoc, const uint32_t* sval, uint32_t* odim, uint32_t* odoc,
+                                  uint32_t* oval) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        if (keep[p]) {
+            const uint32_t o = off[p];
+            odim[o] = sdim[p];
+            odoc[o] = sdoc[p];
+            oval[o] = sval[p];
+        }
+    }
+}
+
 __global__ void fill_u32_kernel(float* p, int64_t n, float v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
@@ -307,6 +348,10 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     const uint32_t lambda = ix.lambda;
     const uint32_t sigma = ix.sigma;
     uint32_t e = 0;
+    // the document stage: Vector Number Pruning keeps vn entries per row,
+    // otherwise alpha-mass (alpha = 1 keeps every entry)
+    const uint32_t vn = ix.prune == SINDI_PRUNE_VECTOR_NUMBER ? ix.prune_n : 0u;
+    const uint32_t lp = (ix.prune == SINDI_PRUNE_LIST || ix.prune == SINDI_PRUNE_MASS_LIST) ? ix.prune_n : 0u;
     SINDI_TRACE_MSG("build_lists: enter");
     ix.kept = P.alloc<uint32_t>(n > 0 ? n : 1);
     ix.scale = P.alloc<float>(d);
@@ -321,7 +366,7 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     SINDI_TRACE_MSG("build_lists: launching prune_rows");
     if (n > 0) {
         prune_rows_kernel<<<grid_for(n, kPruneWarps, 152 * 32), kPruneWarps * 32, 0, stream>>>(
-            ix.indptr, ix.indices, ix.values, n, d, ix.alpha, kept, kdim, kval, long_rows, n_long, ix.err);
+            ix.indptr, ix.indices, ix.values, n, d, ix.alpha, vn, kept, kdim, kval, long_rows, n_long, ix.err);
         SINDI_CUDA(cudaGetLastError());
     }
     uint32_t nl = n > 0 ? read_u32(n_long, stream) : 0;
@@ -329,7 +374,7 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
         size_t sm = (size_t)kMaxRowNnz * sizeof(uint64_t);
         SINDI_CUDA(cudaFuncSetAttribute(prune_long_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         prune_long_rows_kernel<<<nl, kLongBlock, sm, stream>>>(ix.indptr, ix.indices, ix.values, long_rows, d,
-                                                                ix.alpha, kept, kdim, kval, ix.err);
+                                                                ix.alpha, vn, kept, kdim, kval, ix.err);
         SINDI_CUDA(cudaGetLastError());
     }
     e = read_u32(ix.err, stream);
@@ -345,24 +390,13 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     // --- compact kept entries (document order)
     int64_t* kept_off = P.alloc<int64_t>(n + 1);
     exclusive_scan<uint32_t, int64_t>(kept, kept_off, n, P);
-    const int64_t Pn = read_i64(kept_off + n, stream);
-    if (Pn >= (int64_t)0xFFFFFFFFLL) {
+    const int64_t Pn0 = read_i64(kept_off + n, stream);
+    if (Pn0 >= (int64_t)0xFFFFFFFFLL) {
         P.free(kdim); P.free(kval); P.free(kept_off);
         set_last_error("more than 2^32 - 1 kept entries");
         return SINDI_ERR_UNSUPPORTED;
     }
-    ix.postings = Pn;
-    // posting arrays padded to a multiple of 8 entries: the scan reads aligned groups of 8
-    const int64_t Pp = (Pn + 7) & ~(int64_t)7;
-    ix.pid = P.alloc<uint16_t>(Pp);
-    ix.pval = P.alloc<uint8_t>((size_t)Pp * ix.value_bytes());
-    if ((reinterpret_cast<uintptr_t>(ix.pid) | reinterpret_cast<uintptr_t>(ix.pval)) & 15)
-        throw CudaError{cudaErrorMisalignedAddress, "posting arrays are not 16-byte aligned"};
-    if (Pp > Pn) {
-        SINDI_CUDA(cudaMemsetAsync(ix.pid + Pn, 0, sizeof(uint16_t) * (size_t)(Pp - Pn), stream));
-        SINDI_CUDA(cudaMemsetAsync(static_cast<uint8_t*>(ix.pval) + (size_t)Pn * ix.value_bytes(), 0,
-                                   (size_t)(Pp - Pn) * ix.value_bytes(), stream));
-    }
+    int64_t Pn = Pn0;
     uint32_t* sdim = P.alloc<uint32_t>(Pn);
     uint32_t* sdoc = P.alloc<uint32_t>(Pn);
     uint32_t* sval = P.alloc<uint32_t>(Pn);
@@ -400,6 +434,60 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     }
 
     SINDI_TRACE_MSG("build_lists: sort done");
+    if (lp > 0 && Pn > 0) {
+        // --- List Pruning on the lists built so far, then their offsets again
+        uint32_t* inv = P.alloc<uint32_t>(Pn);
+        uint32_t* dcp = P.alloc<uint32_t>(Pn);
+        uint32_t* pos = P.alloc<uint32_t>(Pn);
+        uint32_t* kb = P.alloc<uint32_t>(Pn);
+        uint32_t* db = P.alloc<uint32_t>(Pn);
+        uint32_t* vb = P.alloc<uint32_t>(Pn);
+        lp_keys_kernel<<<grid_for(Pn, 256), 256, 0, stream>>>(sval, Pn, inv, pos);
+        SINDI_CUDA(cudaGetLastError());
+        SINDI_CUDA(cudaMemcpyAsync(dcp, sdim, sizeof(uint32_t) * (size_t)Pn, cudaMemcpyDeviceToDevice, stream));
+        radix_sort_triples(inv, dcp, pos, kb, db, vb, Pn, 31, P);  // by |x| descending (stable)
+        int bits = 0;
+        while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)d) bits++;
+        radix_sort_triples(dcp, inv, pos, kb, db, vb, Pn, bits, P);  // then by dim (stable)
+        uint32_t* keep = kb;  // scratch reuse
+        uint32_t* off = P.alloc<uint32_t>(Pn + 1);
+        lp_mark_kernel<<<grid_for(Pn, 256), 256, 0, stream>>>(dcp, pos, Pn, ix.seg, sigma, lp, sdoc, keep, kept);
+        SINDI_CUDA(cudaGetLastError());
+        exclusive_scan<uint32_t, uint32_t>(keep, off, Pn, P);
+        const int64_t Pk = read_u32(off + Pn, stream);
+        uint32_t* odim = P.alloc<uint32_t>(Pk > 0 ? Pk : 1);
+        uint32_t* odoc = P.alloc<uint32_t>(Pk > 0 ? Pk : 1);
+        uint32_t* oval = P.alloc<uint32_t>(Pk > 0 ? Pk : 1);
+        lp_compact_kernel<<<grid_for(Pn, 256), 256, 0, stream>>>(keep, off, Pn, sdim, sdoc, sval, odim, odoc, oval);
+        SINDI_CUDA(cudaGetLastError());
+        P.free(inv); P.free(dcp); P.free(pos); P.free(kb); P.free(db); P.free(vb); P.free(off);
+        P.free(sdim); P.free(sdoc); P.free(sval);
+        sdim = odim;
+        sdoc = odoc;
+        sval = oval;
+        Pn = Pk;
+        uint32_t* cnt2 = P.alloc<uint32_t>(S > 0 ? S : 1);
+        SINDI_CUDA(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * (size_t)(S > 0 ? S : 1), stream));
+        if (Pn > 0) {
+            list_count_kernel<<<grid_for(Pn, 256), 256, 0, stream>>>(sdim, sdoc, Pn, lambda, sigma, cnt2);
+            SINDI_CUDA(cudaGetLastError());
+        }
+        exclusive_scan<uint32_t, uint32_t>(cnt2, ix.seg, S, P);
+        P.free(cnt2);
+        SINDI_TRACE_MSG("build_lists: list pruning kept %lld postings", (long long)Pn);
+    }
+    ix.postings = Pn;
+    // posting arrays padded to a multiple of 8 entries: the scan reads aligned groups of 8
+    const int64_t Pp = (Pn + 7) & ~(int64_t)7;
+    ix.pid = P.alloc<uint16_t>(Pp);
+    ix.pval = P.alloc<uint8_t>((size_t)Pp * ix.value_bytes());
+    if ((reinterpret_cast<uintptr_t>(ix.pid) | reinterpret_cast<uintptr_t>(ix.pval)) & 15)
+        throw CudaError{cudaErrorMisalignedAddress, "posting arrays are not 16-byte aligned"};
+    if (Pp > Pn) {
+        SINDI_CUDA(cudaMemsetAsync(ix.pid + Pn, 0, sizeof(uint16_t) * (size_t)(Pp - Pn), stream));
+        SINDI_CUDA(cudaMemsetAsync(static_cast<uint8_t*>(ix.pval) + (size_t)Pn * ix.value_bytes(), 0,
+                                   (size_t)(Pp - Pn) * ix.value_bytes(), stream));
+    }
     // --- values and window-local ids
     if (ix.dtype == SINDI_F8E4M3) {
         if (d > 0) {

@@ -135,7 +135,7 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
         set_last_error("out is NULL");
         return SINDI_ERR_INVALID_ARG;
     }
-    sindi_build_params prm = params ? *params : sindi_build_params{0, SINDI_F32, 1.0};
+    sindi_build_params prm = params ? *params : sindi_build_params{0, SINDI_F32, 1.0, SINDI_PRUNE_MASS, 0};
     if (n_docs < 0 || n_docs >= (int64_t)0xFFFFFFFFLL || dim <= 0 || !indptr) {
         set_last_error("n_docs must be in [0, 2^32 - 1), dim > 0, indptr not NULL");
         return SINDI_ERR_INVALID_ARG;
@@ -143,6 +143,11 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
     if (!(prm.alpha > 0.0 && prm.alpha <= 1.0) || prm.window > kMaxWindow || prm.value_dtype < SINDI_F32 ||
         prm.value_dtype > SINDI_F8E4M3) {
         set_last_error("alpha must be in (0, 1], window in [0, 32768], value_dtype a sindi_dtype");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    if (prm.prune < SINDI_PRUNE_MASS || prm.prune > SINDI_PRUNE_MASS_LIST ||
+        (prm.prune != SINDI_PRUNE_MASS && prm.prune_n == 0)) {
+        set_last_error("prune must be a sindi_prune; prune_n >= 1 for VECTOR_NUMBER, LIST and MASS_LIST");
         return SINDI_ERR_INVALID_ARG;
     }
     if ((uint64_t)dim * (uint64_t)std::max<int64_t>(1, (n_docs + std::max<uint32_t>(prm.window, 1) - 1) /
@@ -171,7 +176,10 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
         ix.lambda = prm.window ? prm.window : kDefaultWindow;
         ix.sigma = (uint32_t)((n_docs + ix.lambda - 1) / ix.lambda);
         ix.dtype = prm.value_dtype;
-        ix.alpha = prm.alpha;
+        ix.prune = prm.prune;
+        ix.prune_n = prm.prune == SINDI_PRUNE_MASS ? 0u : prm.prune_n;
+        // alpha applies to the mass-ratio methods only
+        ix.alpha = (prm.prune == SINDI_PRUNE_MASS || prm.prune == SINDI_PRUNE_MASS_LIST) ? prm.alpha : 1.0;
         Pool P{ix.pool, s};
         ix.err = P.alloc<uint32_t>(1);
         SINDI_CUDA(cudaMemsetAsync(ix.err, 0, 4, s));
@@ -422,6 +430,8 @@ sindi_status sindi_index_info(const sindi_index* index, sindi_index_info_t* out)
                                  (int64_t)ix.dim * 4);
     out->doc_bytes = (ix.n_docs + 1) * 8 + ix.doc_nnz * 8;
     out->alpha = ix.alpha;
+    out->prune = ix.prune;
+    out->prune_n = ix.prune_n;
     return SINDI_OK;
 }
 

@@ -17,6 +17,8 @@ struct IndexImpl {
     uint32_t sigma = 0;
     int32_t dtype = SINDI_F32;
     double alpha = 1.0;
+    int32_t prune = SINDI_PRUNE_MASS;
+    uint32_t prune_n = 0;
     int64_t doc_nnz = 0;
     int64_t postings = 0;
     cudaMemPool_t pool = nullptr;

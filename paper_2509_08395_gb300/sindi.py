@@ -23,6 +23,9 @@ SINDI_F32, SINDI_F16, SINDI_F8E4M3 = 0, 1, 2
 SINDI_MODE_PLAIN, SINDI_MODE_BATCHED = 0, 1
 DTYPES = {"f32": SINDI_F32, "f16": SINDI_F16, "f8": SINDI_F8E4M3, "e4m3": SINDI_F8E4M3}
 MODES = {"plain": SINDI_MODE_PLAIN, "batched": SINDI_MODE_BATCHED}
+SINDI_PRUNE_MASS, SINDI_PRUNE_VECTOR_NUMBER, SINDI_PRUNE_LIST, SINDI_PRUNE_MASS_LIST = 0, 1, 2, 3
+PRUNES = {"mass": SINDI_PRUNE_MASS, "vector_number": SINDI_PRUNE_VECTOR_NUMBER, "list": SINDI_PRUNE_LIST,
+          "mass_list": SINDI_PRUNE_MASS_LIST}
 STATUS_NAMES = {0: "SINDI_OK", 1: "SINDI_ERR_INVALID_ARG", 2: "SINDI_ERR_INVALID_DATA", 3: "SINDI_ERR_OOM",
                 4: "SINDI_ERR_CUDA", 5: "SINDI_ERR_TIMEOUT", 6: "SINDI_ERR_UNSUPPORTED"}
 
@@ -34,7 +37,8 @@ class SindiError(RuntimeError):
 
 
 class sindi_build_params(ctypes.Structure):
-    _fields_ = [("window", ctypes.c_uint32), ("value_dtype", ctypes.c_int32), ("alpha", ctypes.c_double)]
+    _fields_ = [("window", ctypes.c_uint32), ("value_dtype", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("prune", ctypes.c_int32), ("prune_n", ctypes.c_uint32)]
 
 
 class sindi_search_params(ctypes.Structure):
@@ -46,7 +50,7 @@ class sindi_index_info_t(ctypes.Structure):
     _fields_ = [("n_docs", ctypes.c_int64), ("dim", ctypes.c_int32), ("value_dtype", ctypes.c_int32),
                 ("window", ctypes.c_uint32), ("n_windows", ctypes.c_uint32), ("postings", ctypes.c_int64),
                 ("doc_nnz", ctypes.c_int64), ("index_bytes", ctypes.c_int64), ("doc_bytes", ctypes.c_int64),
-                ("alpha", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("prune", ctypes.c_int32), ("prune_n", ctypes.c_uint32)]
 
 
 class sindi_stats_t(ctypes.Structure):
@@ -157,10 +161,11 @@ def _stream(stream, *tensors):
 
 # ---- the C entry points, same names -------------------------------------------------
 def sindi_build(indptr, indices, values, n_docs: int, dim: int, window: int = 0, alpha: float = 1.0,
-                value_dtype: str = "f32", stream=None) -> int:
+                value_dtype: str = "f32", stream=None, prune: str = "mass", prune_n: int = 0) -> int:
     """Algorithm 3 on the device; returns the opaque index handle (int)."""
     lib = load()
-    prm = sindi_build_params(window=int(window), value_dtype=DTYPES[value_dtype], alpha=float(alpha))
+    prm = sindi_build_params(window=int(window), value_dtype=DTYPES[value_dtype], alpha=float(alpha),
+                             prune=PRUNES[prune], prune_n=int(prune_n))
     out = ctypes.c_void_p()
     st = lib.sindi_build(_ptr(indptr, np.int64), _ptr(indices, np.int32), _ptr(values, np.float32), int(n_docs),
                          int(dim), ctypes.byref(prm), _stream(stream, indptr), ctypes.byref(out))
@@ -248,9 +253,10 @@ class Index:
     """A device-resident SINDI index (owns the C handle)."""
 
     def __init__(self, indptr, indices, values, dim: int, window: int = 0, alpha: float = 1.0,
-                 value_dtype: str = "f32", stream=None):
+                 value_dtype: str = "f32", stream=None, prune: str = "mass", prune_n: int = 0):
         n_docs = (indptr.shape[0] if hasattr(indptr, "shape") else len(indptr)) - 1
-        self.handle = sindi_build(indptr, indices, values, n_docs, dim, window, alpha, value_dtype, stream)
+        self.handle = sindi_build(indptr, indices, values, n_docs, dim, window, alpha, value_dtype, stream, prune,
+                                  prune_n)
         self.info = sindi_index_info(self.handle)
 
     def search(self, q_indptr, q_indices, q_values, k: int, gamma: int = 0, beta: float = 1.0,

@@ -91,6 +91,58 @@ def test_device_index_equals_oracle_lists(window, alpha, dtype):
     np.testing.assert_array_equal(got, pval)
 
 
+@pytest.mark.parametrize("prune,prune_n,alpha,dtype", [("vector_number", 5, 1.0, "f32"), ("list", 40, 1.0, "f32"),
+                                                       ("list", 3, 1.0, "f8"), ("mass_list", 25, 0.5, "f16")])
+def test_device_index_other_pruning_methods_equal_oracle_lists(prune, prune_n, alpha, dtype):
+    """Vector Number, List and Mass+List pruning (Sec. 4.1) on the device give the oracle's lists bit for bit,
+    including ties in |x| (coarse values) and, for FP8, the per-list scales of the pruned lists."""
+    ip, ix, v = datagen.random_csr(3000, 97, 14.0, seed=60, zipf_s=1.05, val_sigma=1.2)
+    v = (np.round(v * 8) / 8 + 0.125).astype(np.float32)
+    rng = np.random.default_rng(9)
+    for i in range(0, 3000, 11):
+        a, b = ip[i], ip[i + 1]
+        p = rng.permutation(b - a)
+        ix[a:b], v[a:b] = ix[a:b][p], v[a:b][p]
+    D = oracle.Dataset(ip, ix, v, 97)
+    I = oracle.Index(D, window=256, alpha=alpha, dtype=dtype, prune=prune, prune_n=prune_n)
+    seg, pid, pval, scale, kept = I.export()
+    with sindi.Index(dev(ip), dev(ix), dev(v), 97, window=256, alpha=alpha, value_dtype=dtype, prune=prune,
+                     prune_n=prune_n) as idx:
+        ex = idx.export()
+        assert idx.info["prune"] == sindi.PRUNES[prune] and idx.info["prune_n"] == prune_n
+    assert ex["info"]["postings"] == I.postings
+    np.testing.assert_array_equal(ex["seg"].astype(np.int64), seg)
+    np.testing.assert_array_equal(ex["kept"].astype(np.int64), kept)
+    np.testing.assert_array_equal(ex["ids"].astype(np.int64), pid % 256)
+    if dtype == "f8":
+        np.testing.assert_array_equal(ex["scale"], scale)
+    np.testing.assert_array_equal(_dequant(ex["vals"], dtype, ex["scale"], ex["seg"], I.sigma, 97), pval)
+
+
+@pytest.mark.parametrize("prune,prune_n,alpha", [("vector_number", 12, 1.0), ("list", 2000, 1.0),
+                                                 ("mass_list", 1500, 0.5)])
+def test_other_pruning_methods_search_parity(pruned_small, prune, prune_n, alpha):
+    """Coarse top-k and the reordered answer over a VNP / LP / MRP+LP index against the oracle's."""
+    w, (ip, ix, v), (qp, qx, qv), D, Q = pruned_small
+    I = oracle.Index(D, window=4096, alpha=alpha, prune=prune, prune_n=prune_n)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=4096, alpha=alpha, prune=prune,
+                     prune_n=prune_n) as idx:
+        assert idx.info["postings"] == I.postings
+        ids, sc = run_search(idx, qp, qx, qv, k=50, gamma=0, mode="plain")
+        rids, rsc = run_search(idx, qp, qx, qv, k=20, gamma=300, mode="batched")
+    for r in range(Q.n):
+        oi, os_ = I.search(Q, r, k=114, gamma=0)
+        check_ranked(ids[r], sc[r], oi, os_, 50, D.n, what=f"{prune} coarse query {r}")
+        check_reranked(rids[r], rsc[r], D, Q, r, I, 20, 300, what=f"{prune} rerank query {r}")
+
+
+def test_invalid_pruning_parameters():
+    ip, ix, v = datagen.random_csr(50, 16, 4.0, seed=3)
+    for prune, n in (("vector_number", 0), ("list", 0), ("mass_list", 0)):
+        with pytest.raises(sindi.SindiError, match="INVALID_ARG"):
+            sindi.Index(dev(ip), dev(ix), dev(v), 16, window=64, prune=prune, prune_n=n)
+
+
 def test_device_index_host_and_device_inputs_agree():
     ip, ix, v = datagen.random_csr(500, 64, 10.0, seed=77)
     with sindi.Index(ip, ix, v, 64, window=100, alpha=0.5) as a, \
