@@ -124,12 +124,13 @@ WORKLOADS: dict[str, Workload] = {
         queries=RowDist(100, NNZ_POISSON, 8.0, nnz_min=1, val_sigma=1.0),
         k=10, gamma=0, alpha=1.0, window=4096, doc_seed=1001, query_seed=2001,
     ),
-    # 1M docs x 30,522 dims; mass-ratio pruning alpha = 0.5, rerank 500, top-50
+    # 1M docs x 30,522 dims; mass-ratio pruning alpha = 0.5, rerank 500, top-50; window 16,384 (measured
+    # best for both schedules on this size)
     "pruned-1m": Workload(
         name="pruned-1m", dim=30522, zipf_s=1.05,
         docs=RowDist(1_000_000, NNZ_LOGNORMAL, 120.0, 0.5, 10, 400, val_sigma=0.8),
         queries=RowDist(1_000, NNZ_LOGNORMAL, 45.0, 0.5, 5, 150, val_sigma=0.8),
-        k=50, gamma=500, alpha=0.5, window=8192, doc_seed=1002, query_seed=2002,
+        k=50, gamma=500, alpha=0.5, window=16384, doc_seed=1002, query_seed=2002,
     ),
     # 8.8M docs, 10k queries of uneven nnz U[5, 200]
     "batched-8.8m": Workload(

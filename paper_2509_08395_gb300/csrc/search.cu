@@ -40,7 +40,9 @@ namespace sindi {
 
 constexpr int kScanThreadsPlain = 512;     // two blocks per SM: the windows of concurrent queries interleave
 constexpr int kScanThreadsBatched = 512;   // many windows: two blocks per SM overlap their phases
-constexpr int kPlainLanes = 8;             // plain schedule: query chains in flight at once
+constexpr int kPlainLanes = 16;            // plain schedule: query chains in flight at once
+constexpr uint32_t kSplitMinWindows = 8;   // plain schedule: a query of this many windows or more scans
+constexpr uint32_t kSplitFraction = 8;     // its first 1/kSplitFraction windows first
 constexpr int kMaxScanWarps = 1024 / 32;   // largest scan block
 constexpr int kChunkTable = 2048;          // chunks mapped to their list by a table (then a search)
 constexpr int kChunkU = 8;                 // postings per lane in one warp chunk
@@ -286,7 +288,11 @@ struct ScanArgs {
     int64_t q_first;
     uint32_t g;             // candidates per query: min(gamma or k, N)
     uint32_t win_cap;       // most candidates one window may emit without an exact select
-    int use_partial;        // read the per-query histogram before emitting
+    int use_partial;        // read the per-query histogram before emitting: 0 no; 1 copied at the
+                            // block's start (batched: earlier windows of the query are done); 2 read
+                            // after the accumulation, once the previous launch (the query's first
+                            // windows) is complete
+    uint32_t w0;            // first window of this launch
     Workspace ws;
 };
 
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     uint64_t* stage = reinterpret_cast<uint64_t*>(region);
 
     const DevIndex& ix = a.ix;
-    const uint32_t w = QUERY_MAJOR ? blockIdx.y : blockIdx.x;
+    const uint32_t w = a.w0 + (QUERY_MAJOR ? blockIdx.y : blockIdx.x);
     const uint32_t y = QUERY_MAJOR ? blockIdx.x : blockIdx.y;
     const int64_t r = a.q_first + y;
     const uint32_t lambda = ix.lambda;
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
 
     allow_next_kernel();
     uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
-    if (a.use_partial) {
+    if (a.use_partial == 1) {
         // the query's histogram of what its earlier windows emitted, copied
         // while the window accumulates (a snapshot: H only grows during the
         // launch, so any snapshot bounds the answer)
@@ -397,10 +403,16 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
     uint32_t pbin = 0;  // bin of the g-th emitted candidate, when g have been emitted
     bool bounded = false;
-    if (a.use_partial) {
+    if (a.use_partial == 1) {
         cp_async_wait_all();
         __syncthreads();
         block_find_bin<kHistBins, kScanThreads>([&](int b) { return hist[b]; }, a.g, red, st);
+        bounded = st[3] >= a.g;
+        pbin = st[0];
+        __syncthreads();
+    } else if (a.use_partial == 2) {
+        wait_previous_kernels();  // the first windows' candidates are all in H
+        block_find_bin<kHistBins, kScanThreads>([&](int b) { return __ldcg(H + b); }, a.g, red, st);
         bounded = st[3] >= a.g;
         pbin = st[0];
         __syncthreads();
@@ -1095,12 +1107,27 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
     // the coarse scan reads the beta-pruned queries when there are any (Alg. 4, the query-pruning step);
     // merge and rerank check and reorder with the full queries
     ScanArgs sa{dix, scan_q ? scan_q->indptr : q_indptr, scan_q ? scan_q->indices : q_indices,
-                scan_q ? scan_q->values : q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, ws};
+                scan_q ? scan_q->values : q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, 0u, ws};
     if (ev0) SINDI_CUDA(cudaEventRecord(ev0, stream));
-    // query-major grids put the queries of one window next to each other
-    // (shared lists stay in L2); gridDim.y limits sigma to 65535 there
-    launch_scan_pdl(ix.dtype, pl.block, batched, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem,
-                    stream, *chained && !ev0);
+    if (!batched && ix.sigma >= kSplitMinWindows) {
+        // One query: its first windows run alone and fill the query's
+        // histogram of candidates; the other windows then emit only what can
+        // still enter the answer (the running bound of Alg. 2's heap, taken
+        // from a block of windows instead of one window at a time).
+        const uint32_t first = std::max<uint32_t>(2u, (ix.sigma + kSplitFraction - 1) / kSplitFraction);
+        launch_scan_pdl(ix.dtype, pl.block, false, false, sa, first, nq, scan_smem, stream, *chained && !ev0);
+        ScanArgs sb = sa;
+        sb.use_partial = 2;
+        sb.w0 = first;
+        launch_scan_pdl(ix.dtype, pl.block, false, false, sb, ix.sigma - first, nq, scan_smem, stream, true);
+        ix.launches += 1;
+        ix.scan_launches += 1;
+    } else {
+        // query-major grids put the queries of one window next to each other
+        // (shared lists stay in L2); gridDim.y limits sigma to 65535 there
+        launch_scan_pdl(ix.dtype, pl.block, batched, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem,
+                        stream, *chained && !ev0);
+    }
     if (ev1) SINDI_CUDA(cudaEventRecord(ev1, stream));
     MergeArgs ma{dix, q_indptr, q_indices, q_values, q0, pl.g, pl.final_stage ? 1 : 0, k, out_ids, out_scores, ws};
     launch_kernel(merge_kernel, dim3(pl.merge_blocks, nq), dim3(kMergeThreads), (size_t)pl.fcap * 8, stream,
