@@ -513,6 +513,9 @@ def main():
                              float((nterms[g0:g0 + group] * (sigma * 8 + 8)).sum()))
         alg_bytes_per_launch = float(np.mean(per_group))
     achieved_gbs = alg_bytes_per_launch / (scan_ms_per_launch / 1000.0) / 1e9
+    # the same bytes for every scan of the timed region over the region's time (the plain schedule runs
+    # many queries' scans at once; merge and rerank share the region, so this is a lower bound)
+    achieved_step_gbs = alg_bytes_per_launch * scan_launches_per_step * args.steps / (dev_ms_max / 1000.0) / 1e9
     # scatter-adds (one FP32 shared-memory atomicAdd per posting and query): the scan kernel's own rate
     # (timed pass), the whole step's rate, and the probe's measured rate of that operation on this GPU
     adds_per_s = float(touched.sum()) * args.steps / (st2["scan_ms"] / 1000.0)
@@ -698,6 +701,9 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                      "frac": achieved_gbs / peak, "peak_kind": peak_kind,
                      "frac_of_nominal_8tbs": achieved_gbs / NOMINAL_HBM_GBS,
+                     "achieved_basis": "one scan stage alone (timed pass, one query chain at a time): "
+                                       "algorithmic bytes per launch / its CUDA-event duration",
+                     "achieved_in_step": achieved_step_gbs, "frac_in_step": achieved_step_gbs / peak,
                      "traffic": profile_traffic(sha), "kernel": "scan_window_kernel",
                      "alg_bytes_per_launch": alg_bytes_per_launch, "ms_per_launch": scan_ms_per_launch,
                      "postings_per_query": float(touched.mean()),

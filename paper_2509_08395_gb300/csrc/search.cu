@@ -55,8 +55,10 @@ constexpr int kSubBits = 8;                // second-level bins inside the cut b
 constexpr int kSubBins = 1 << kSubBits;
 constexpr int kRelBins = 256;              // window histogram bins below the window's top bin
 constexpr int kMergeThreads = 512;
+constexpr uint32_t kMergeOneBlock = 16384;  // candidates one merge block gathers alone
 constexpr int kRerankThreads = 256;
 constexpr int kRerankWarps = kRerankThreads / 32;
+constexpr int kRerankU = 16;               // row entries per lane loaded at once
 constexpr int kHashSlots = 4096;           // query hash (load <= 1/2 at the term limit)
 constexpr int kQueryTermLimit = kHashSlots / 2;
 
@@ -330,7 +332,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     const uint32_t lambda = ix.lambda;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    allow_next_kernel();
     uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
     if (a.use_partial == 1) {
         // the query's histogram of what its earlier windows emitted, copied
@@ -393,6 +394,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
         }
     }
     __syncthreads();
+
+    // the next kernel may start its blocks now (they wait for this one where they
+    // must); later than the block's start, so they do not sit idle through the
+    // accumulation
+    allow_next_kernel();
 
     // ---- window selection (ids >= N are not candidates)
     const int64_t gbase = (int64_t)w * lambda;
@@ -741,19 +747,72 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
     const Workspace& ws = a.ws;
     const uint32_t y = blockIdx.y;
     const int64_t r = a.q_first + y;
+    if (blockIdx.x == 0) {
+        // check the query (dims, values, repeats) while the scan still runs: the
+        // query is an input of the call, no kernel of the search writes it
+        const int64_t qb = a.q_indptr[r];
+        const int nt = (int)(a.q_indptr[r + 1] - qb);
+        build_query_hash<kMergeThreads>(a.q_indices + qb, a.q_values + qb, nt, a.ix.dim,
+                                        reinterpret_cast<int32_t*>(sbuf), nullptr, a.ix.err, true);
+    }
     wait_previous_kernels();
-    allow_next_kernel();
     const uint32_t C = min(ws.cand_count[y], ws.cand_cap);
     const uint32_t g = a.g < C ? a.g : C;
     const uint64_t* cand = ws.cand + (size_t)y * ws.cand_cap;
     uint32_t* H = ws.hist + (size_t)y * kHistBins;
 
     // bin of the g-th best candidate; every candidate below it is out
-    block_find_bin<kHistBins, kMergeThreads>([&](int b) { return H[b]; }, g, red, st);
+    block_find_bin<kHistBins, kMergeThreads>([&](int b) { return __ldcg(H + b); }, g, red, st);
     const uint32_t bstar = st[0];
     const uint32_t S = st[1] + st[2];  // candidates in bins >= bstar
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
+    uint64_t* dst = a.final_stage ? sel : ws.top + (size_t)y * ws.top_cap;
+    const uint32_t dcap = a.final_stage ? (uint32_t)kMaxK : ws.top_cap;
+    if (C <= kMergeOneBlock && S <= ws.fcap) {
+        // few candidates: block 0 alone gathers the survivors into shared
+        // memory and selects; no filter buffer, fence or ticket
+        if (blockIdx.x != 0) return;
+        for (uint32_t base = 0; base < C; base += kMergeThreads * 4) {
+            uint64_t kk[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint32_t i = base + (uint32_t)(u * kMergeThreads) + threadIdx.x;
+                kk[u] = i < C ? __ldcg(cand + i) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint32_t i = base + (uint32_t)(u * kMergeThreads) + threadIdx.x;
+                if (i < C && (uint32_t)(kk[u] >> kKeyBinShift) >= bstar) {
+                    const uint32_t pos = atomicAdd(&s_n, 1u);
+                    if (pos < ws.fcap) sbuf[pos] = kk[u];
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t nf = min(s_n, ws.fcap);
+        __syncthreads();
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        allow_next_kernel();  // the other blocks have exited: the rerank may start
+        auto key_of = [&](int i) -> uint64_t { return sbuf[i]; };
+        const uint64_t T = nf > g ? block_select_threshold<kMergeThreads>(key_of, (int)nf, (int)g, hist256, st) : 0ull;
+        gather_at_least<kMergeThreads>(key_of, nf, T, dst, dcap, &s_n);
+        if (a.final_stage) {
+            write_sorted_results<kMergeThreads>(sel, (int)min(s_n, (uint32_t)kMaxK), a.k, a.out_ids, a.out_scores,
+                                                r);
+        } else if (threadIdx.x == 0) {
+            ws.top_count[y] = min(s_n, ws.top_cap);
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < kHistBins; b += kMergeThreads) H[b] = 0;
+        if (threadIdx.x == 0) {
+            ws.cand_count[y] = 0;
+            ws.fcount[y] = 0;
+            ws.mticket[y] = 0;
+        }
+        return;
+    }
     {
         // this block's slice: survivors gathered in shared memory, then one
         // reservation in the query's filter buffer
@@ -791,18 +850,11 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
     if (!s_last) return;
     __threadfence();
 
-    // ---- last block of the query: check the query, exact best g
-    {
-        const int64_t qb = a.q_indptr[r];
-        const int nt = (int)(a.q_indptr[r + 1] - qb);
-        build_query_hash<kMergeThreads>(a.q_indices + qb, a.q_values + qb, nt, a.ix.dim,
-                                        reinterpret_cast<int32_t*>(sbuf), nullptr, a.ix.err, true);
-    }
+    // ---- last block of the query: exact best g
+    allow_next_kernel();
     const uint32_t nf = min(__ldcg(ws.fcount + y), ws.fcap);
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
-    uint64_t* dst = a.final_stage ? sel : ws.top + (size_t)y * ws.top_cap;
-    const uint32_t dcap = a.final_stage ? (uint32_t)kMaxK : ws.top_cap;
     if (S <= ws.fcap) {
         const uint64_t* fb = ws.fbuf + (size_t)y * ws.fcap;
         for (uint32_t i = threadIdx.x; i < nf; i += kMergeThreads) sbuf[i] = __ldcg(fb + i);
@@ -844,6 +896,7 @@ struct RerankArgs {
 };
 
 __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
+    extern __shared__ uint64_t rk[];  // [top_cap]: the exact keys, in the query's last block
     __shared__ int32_t hk[kHashSlots];
     __shared__ float hv[kHashSlots];
     __shared__ uint64_t s[kMaxK];
@@ -864,18 +917,22 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
     wait_previous_kernels();
     const uint32_t g = min(ws.top_count[y], ws.top_cap);
     uint64_t* rr = ws.rr + (size_t)y * ws.top_cap;
-    const uint32_t idx = blockIdx.x * kRerankWarps + warp;
+    // one half-warp per candidate: lanes 0-15 and 16-31 score two documents
+    const int half = lane >> 4, hl = lane & 15;
+    const unsigned hmask = half ? 0xFFFF0000u : 0x0000FFFFu;
+    const uint32_t idx = (blockIdx.x * kRerankWarps + warp) * 2 + half;
     if (idx < g) {
         const uint64_t key = ws.top[(size_t)y * ws.top_cap + idx];
         const uint32_t id = key_id(key);
         const int64_t b = a.ix.indptr[id], e = a.ix.indptr[id + 1];
         float acc = 0.0f;
-        for (int64_t p0 = b; p0 < e; p0 += 128) {
-            int32_t jj[4];
-            float xx[4];
+        // the row's entries, up to 16 * kRerankU at a time, all loads issued before the first is used
+        for (int64_t p0 = b; p0 < e; p0 += 16 * kRerankU) {
+            int32_t jj[kRerankU];
+            float xx[kRerankU];
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int64_t p = p0 + u * 32 + lane;
+            for (int u = 0; u < kRerankU; u++) {
+                const int64_t p = p0 + u * 16 + hl;
                 jj[u] = -1;
                 xx[u] = 0.0f;
                 if (p < e) {
@@ -884,12 +941,12 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; u++)
+            for (int u = 0; u < kRerankU; u++)
                 if (jj[u] >= 0) acc = fmaf(xx[u], query_weight(hk, hv, jj[u]), acc);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (lane == 0) rr[idx] = result_key(acc, id);
+        for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(hmask, acc, o);
+        if (hl == 0) rr[idx] = result_key(acc, id);
     }
     __threadfence();
     __syncthreads();
@@ -900,9 +957,11 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
     {
-        // the best k of the g exact scores, then sort only those
+        // the best k of the g exact scores (copied to shared memory once), then sort only those
+        for (uint32_t i = threadIdx.x; i < g; i += kRerankThreads) rk[i] = __ldcg(rr + i);
+        __syncthreads();
         const uint32_t kk = a.k < g ? a.k : g;
-        auto key_of = [&](int i) -> uint64_t { return __ldcg(rr + i); };
+        auto key_of = [&](int i) -> uint64_t { return rk[i]; };
         const uint64_t T = g > kk ? block_select_threshold<kRerankThreads>(key_of, (int)g, (int)kk, hist256, st) : 0ull;
         gather_at_least<kRerankThreads>(key_of, g, T, s, kMaxK, &s_n);
     }
@@ -1053,6 +1112,7 @@ void configure_search_kernels(int device) {
     allow_window_smem_dt<SINDI_F16>();
     allow_window_smem_dt<SINDI_F8E4M3>();
     SINDI_CUDA(cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8));
+    SINDI_CUDA(cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxGamma * 8));
     done.push_back(device);
 }
 
@@ -1136,8 +1196,8 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
     ix.scan_launches += 1;
     if (!pl.final_stage) {
         RerankArgs ra{dix, q_indptr, q_indices, q_values, q0, k, out_ids, out_scores, ws};
-        launch_kernel(rerank_kernel, dim3(ceil_div_u32(pl.g, kRerankWarps), nq), dim3(kRerankThreads), 0, stream,
-                      true, ra);
+        launch_kernel(rerank_kernel, dim3(ceil_div_u32(pl.g, 2 * kRerankWarps), nq), dim3(kRerankThreads),
+                      (size_t)pl.top_cap * 8, stream, true, ra);
         ix.launches += 1;
     }
     *chained = true;

@@ -204,6 +204,36 @@ def test_pruned_rerank_parity(pruned_small, window, gamma, k, mode):
     assert touched <= 2
 
 
+@pytest.mark.parametrize("window,gamma,k,mode", [(8192, 8192, 100, "plain"), (512, 3000, 50, "plain"),
+                                                 (2048, 8192, 20, "batched")])
+def test_large_candidate_pools(pruned_small, window, gamma, k, mode):
+    """Candidate pools past what one merge block gathers alone (tens of thousands of window candidates,
+    gamma up to the 8,192 limit): the multi-block merge, its filter buffer and the rerank's largest pool."""
+    w, (ip, ix, v), (qp, qx, qv), D, Q = pruned_small
+    I = oracle.Index(D, window=window, alpha=0.5)
+    nq = 12
+    qp, qx, qv = qp[: nq + 1], qx[: qp[nq]], qv[: qp[nq]]
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=window, alpha=0.5) as idx:
+        ids, sc = run_search(idx, qp, qx, qv, k=k, gamma=gamma, mode=mode)
+    for r in range(nq):
+        check_reranked(ids[r], sc[r], D, Q, r, I, k, gamma, what=f"query {r}")
+
+
+def test_rerank_of_long_documents():
+    """Documents of 500 to 3,000 entries (the long-row prune path, and rows the rerank reads in several
+    passes of 512 entries): reordered answers against the oracle."""
+    ip, ix, v = datagen.generate(datagen.RowDist(400, datagen.NNZ_UNIFORM, 500, 3000, 500, 3000), 4096, 0.6, 71)
+    qp, qx, qv = datagen.random_csr(10, 4096, 60.0, seed=72, zipf_s=0.6, nnz_min=5)
+    D, Q = oracle.Dataset(ip, ix, v, 4096), oracle.Dataset(qp, qx, qv, 4096)
+    I = oracle.Index(D, window=128, alpha=0.4)
+    with sindi.Index(dev(ip), dev(ix), dev(v), 4096, window=128, alpha=0.4) as idx:
+        assert idx.info["postings"] == I.postings
+        for mode in ("plain", "batched"):
+            ids, sc = run_search(idx, qp, qx, qv, k=10, gamma=60, mode=mode)
+            for r in range(Q.n):
+                check_reranked(ids[r], sc[r], D, Q, r, I, 10, 60, what=f"{mode} query {r}")
+
+
 @pytest.mark.parametrize("beta,mode", [(0.3, "plain"), (0.6, "batched")])
 def test_beta_query_pruning_parity(pruned_small, beta, mode):
     """Alg. 4 with beta < 1: the coarse scan uses beta-mass(q), the reorder the full q."""
