@@ -109,6 +109,9 @@ typedef struct {
                               ignored by MASS                                     */
 } sindi_build_params;
 
+/* sindi_search_params.block_threads value of the pipelined window scan. */
+#define SINDI_SCAN_PIPELINED 1u
+
 /* Parameters of Algorithm 4. */
 typedef struct {
     uint32_t k;            /* results per query, 1..1024                            */
@@ -120,8 +123,13 @@ typedef struct {
                               plans, servers and sindi_search_noalloc return
                               SINDI_ERR_UNSUPPORTED for beta < 1                    */
     uint32_t mode;         /* sindi_mode                                           */
-    uint32_t block_threads;/* threads per window-scan block: 256, 512 or 1024;
-                              0 = the schedule's default (512)                  */
+    uint32_t block_threads;/* window-scan shape: 0 = the default (one block of 512
+                              threads per window); 256, 512 or 1024 = one block
+                              of that many threads per window;
+                              SINDI_SCAN_PIPELINED = one resident block per SM
+                              that overlaps the scatter-add of one window with
+                              the cut of the previous (lambda <= 16384; larger
+                              windows take the default)                         */
 } sindi_search_params;
 
 typedef struct {

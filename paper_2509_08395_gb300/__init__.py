@@ -7,6 +7,7 @@ from .sindi import (  # noqa: F401
     DTYPES,
     MODES,
     PRUNES,
+    SINDI_SCAN_PIPELINED,
     Index,
     Plan,
     Server,

@@ -65,7 +65,7 @@ def default_windows(n_docs: int, sm_count: int):
 
 def autotune(indptr, indices, values, dim: int, q_indptr, q_indices, q_values, k: int, alpha: float,
              recall_target: float = 0.99, windows=None, gammas=(100, 200, 300, 500, 750, 1000, 1500, 2000, 4000),
-             blocks=(256, 512, 1024), modes=("plain", "batched"), value_dtype: str = "f32", repeats: int = 3,
+             blocks=(0, 1, 256, 512, 1024), modes=("plain", "batched"), value_dtype: str = "f32", repeats: int = 3,
              cache: str | None = None, alphas=None) -> dict:
     """Tune (window, gamma, schedule, block) on device tensors of documents and sample queries; with
     `alphas`, the pruning ratio too (each alpha is tried at every window).

@@ -118,4 +118,9 @@ struct CudaError {
 
 inline uint32_t ceil_div_u32(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
 
+// sindi_search_params.block_threads: 0 (default), SINDI_SCAN_PIPELINED, 256, 512 or 1024.
+inline bool valid_block_threads(uint32_t b) {
+    return b == 0 || b == SINDI_SCAN_PIPELINED || b == 256 || b == 512 || b == 1024;
+}
+
 }  // namespace sindi

@@ -42,12 +42,31 @@ constexpr int kScanBlock = 256;
 constexpr int kScanItems = 16;
 constexpr int64_t kScanTile = (int64_t)kScanBlock * kScanItems;
 
-// Block-wide exclusive sum of one value per thread; *total gets the block sum.
-// smem: [BLOCK / 32 + 1] elements. BLOCK <= 1024.
-template <typename T, int BLOCK = kScanBlock>
-__device__ __forceinline__ T block_exclusive_sum(T v, T* total, T* smem) {
-    constexpr int W = BLOCK / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Who cooperates in a collective below, and how they synchronise: the whole
+// block (__syncthreads), or a warp-aligned group of NT threads starting at
+// thread FIRST that meets at hardware barrier BAR (bar.sync; barrier 0 is the
+// block's own). tid() is the thread's index inside the group.
+template <int NT>
+struct SyncBlock {
+    static constexpr int kThreads = NT;
+    __device__ static __forceinline__ void sync() { __syncthreads(); }
+    __device__ static __forceinline__ int tid() { return (int)threadIdx.x; }
+};
+
+template <int BAR, int NT, int FIRST>
+struct SyncGroup {
+    static constexpr int kThreads = NT;
+    static_assert(NT % 32 == 0 && FIRST % 32 == 0 && BAR > 0 && BAR < 16, "warp-aligned group, barriers 1..15");
+    __device__ static __forceinline__ void sync() { asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory"); }
+    __device__ static __forceinline__ int tid() { return (int)threadIdx.x - FIRST; }
+};
+
+// Group-wide exclusive sum of one value per thread; *total gets the group sum.
+// smem: [S::kThreads / 32 + 1] elements. Group size <= 1024.
+template <typename T, typename S>
+__device__ __forceinline__ T group_exclusive_sum(T v, T* total, T* smem) {
+    constexpr int W = S::kThreads / 32;
+    const int lane = S::tid() & 31, warp = S::tid() >> 5;
     T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -55,7 +74,7 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* total, T* smem) {
         if (lane >= o) x += y;
     }
     if (lane == 31) smem[warp] = x;
-    __syncthreads();
+    S::sync();
     if (warp == 0) {
         T w = lane < W ? smem[lane] : T(0);
 #pragma unroll
@@ -66,12 +85,18 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* total, T* smem) {
         if (lane < W) smem[lane] = w;  // inclusive warp totals
         if (lane == W - 1) smem[W] = w;
     }
-    __syncthreads();
+    S::sync();
     T warp_excl = warp > 0 ? smem[warp - 1] : T(0);
     *total = smem[W];
     T r = warp_excl + x - v;
-    __syncthreads();
+    S::sync();
     return r;
+}
+
+// The same over the whole block of BLOCK threads.
+template <typename T, int BLOCK = kScanBlock>
+__device__ __forceinline__ T block_exclusive_sum(T v, T* total, T* smem) {
+    return group_exclusive_sum<T, SyncBlock<BLOCK>>(v, total, smem);
 }
 
 template <typename TI, typename TO>
@@ -253,16 +278,18 @@ inline void radix_sort_triples(uint32_t* key_a, uint32_t* doc_a, uint32_t* val_a
 // digits then go from the highest differing bit down, and a digit bucket that
 // holds exactly the remainder ends the search early.
 //   hist: shared uint32[256]; st: shared uint32[4].
-// Every thread of the block must call it (it synchronises).
+// Every thread of the group must call it (it synchronises).
 // ---------------------------------------------------------------------------
-template <int BLOCK, typename KeyOf>
-__device__ uint64_t block_select_threshold(const KeyOf& key_of, int n, int g, uint32_t* hist, uint32_t* st) {
+template <typename S, typename KeyOf>
+__device__ uint64_t group_select_threshold(const KeyOf& key_of, int n, int g, uint32_t* hist, uint32_t* st) {
+    constexpr int BLOCK = S::kThreads;
     constexpr int W = BLOCK / 32;
     static_assert(2 * W * 2 <= 256, "scratch for the reduction lives in hist");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = S::tid();
+    const int lane = tid & 31, warp = tid >> 5;
     // shared prefix: highest bit where the largest and smallest key differ
     uint64_t mx = 0, mn = ~0ull;
-    for (int i = threadIdx.x; i < n; i += BLOCK) {
+    for (int i = tid; i < n; i += BLOCK) {
         const uint64_t k = key_of(i);
         mx = k > mx ? k : mx;
         mn = k < mn ? k : mn;
@@ -274,13 +301,13 @@ __device__ uint64_t block_select_threshold(const KeyOf& key_of, int n, int g, ui
         mn = b < mn ? b : mn;
     }
     uint64_t* red64 = reinterpret_cast<uint64_t*>(hist);
-    __syncthreads();  // hist may still be read by the caller's previous use
+    S::sync();  // hist may still be read by the caller's previous use
     if (lane == 0) {
         red64[warp] = mx;
         red64[W + warp] = mn;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    S::sync();
+    if (tid == 0) {
         uint64_t a = 0, b = ~0ull;
         for (int i = 0; i < W; i++) {
             a = red64[i] > a ? red64[i] : a;
@@ -289,19 +316,19 @@ __device__ uint64_t block_select_threshold(const KeyOf& key_of, int n, int g, ui
         red64[0] = a;
         red64[1] = b;
     }
-    __syncthreads();
+    S::sync();
     const uint64_t kmax = red64[0], diff = kmax ^ red64[1];
-    __syncthreads();
+    S::sync();
     if (diff == 0) return kmax;  // a single key
     const int hb = 63 - __clzll((long long)diff);
     uint64_t mask = hb >= 63 ? 0ull : ~((2ull << hb) - 1ull);  // bits every key shares
     uint64_t prefix = kmax & mask;
     uint32_t remaining = (uint32_t)g;
     for (int shift = hb - 7 > 0 ? hb - 7 : 0;; shift = shift - 8 > 0 ? shift - 8 : 0) {
-        for (int b = threadIdx.x; b < 256; b += BLOCK) hist[b] = 0;
-        __syncthreads();
+        for (int b = tid; b < 256; b += BLOCK) hist[b] = 0;
+        S::sync();
         for (int base = 0; base < n; base += BLOCK) {
-            int i = base + threadIdx.x;
+            int i = base + tid;
             int dig = -1;
             if (i < n) {
                 uint64_t k = key_of(i);
@@ -310,7 +337,7 @@ __device__ uint64_t block_select_threshold(const KeyOf& key_of, int n, int g, ui
             unsigned peers = __match_any_sync(kFull, dig);
             if (dig >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[dig], (uint32_t)__popc(peers));
         }
-        __syncthreads();
+        S::sync();
         if (warp == 0) {
             // lane l owns bins 255-8l .. 248-8l (from the top)
             uint32_t c[8];
@@ -342,9 +369,9 @@ __device__ uint64_t block_select_threshold(const KeyOf& key_of, int n, int g, ui
                 }
             }
         }
-        __syncthreads();
+        S::sync();
         const uint32_t bin = st[0], above = st[1], cnt = st[2];
-        __syncthreads();
+        S::sync();
         remaining -= above;
         prefix = (prefix & ~((uint64_t)0xFF << shift)) | ((uint64_t)bin << shift);
         mask |= (uint64_t)0xFF << shift;
@@ -352,6 +379,11 @@ __device__ uint64_t block_select_threshold(const KeyOf& key_of, int n, int g, ui
         if (cnt == remaining) return prefix;
         if (shift == 0) return prefix;
     }
+}
+
+template <int BLOCK, typename KeyOf>
+__device__ uint64_t block_select_threshold(const KeyOf& key_of, int n, int g, uint32_t* hist, uint32_t* st) {
+    return group_select_threshold<SyncBlock<BLOCK>>(key_of, n, g, hist, st);
 }
 
 // Bitonic sort of n (power of two) 64-bit keys in shared memory, descending.

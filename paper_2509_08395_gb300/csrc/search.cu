@@ -41,6 +41,7 @@ namespace sindi {
 constexpr int kScanThreadsPlain = 512;     // two blocks per SM: the windows of concurrent queries interleave
 constexpr int kScanThreadsBatched = 512;   // many windows: two blocks per SM overlap their phases
 constexpr int kPlainLanes = 16;            // plain schedule: query chains in flight at once
+constexpr uint32_t kPlainPipeItems = 6;    // plain schedule, pipelined scan: windows per block
 constexpr uint32_t kSplitMinWindows = 8;   // plain schedule: a query of this many windows or more scans
 constexpr uint32_t kSplitFraction = 8;     // its first 1/kSplitFraction windows first
 constexpr int kMaxScanWarps = 1024 / 32;   // largest scan block
@@ -238,39 +239,46 @@ __device__ __forceinline__ void add_chunk(float* A, const Chunk& k) {
 // histogram read through `get`, counting from the top bin. Leaves the bin in
 // st[0] (0 when the total is below g), the count strictly above it in st[1],
 // its own count in st[2] and the histogram total in st[3]. red: [BLOCK/32 + 1].
-template <int BINS, int BLOCK, typename Get>
-__device__ void block_find_bin(const Get& get, uint32_t g, uint32_t* red, uint32_t* st) {
+template <int BINS, typename S, typename Get>
+__device__ void group_find_bin(const Get& get, uint32_t g, uint32_t* red, uint32_t* st) {
+    constexpr int BLOCK = S::kThreads;
     constexpr int BPT = (BINS + BLOCK - 1) / BLOCK;  // bins per thread, from the top
+    const int tid = S::tid();
     uint32_t c[BPT];
     uint32_t s = 0;
 #pragma unroll
     for (int j = 0; j < BPT; j++) {
-        const int b = BINS - 1 - BPT * (int)threadIdx.x - j;
+        const int b = BINS - 1 - BPT * (int)tid - j;
         c[j] = b >= 0 ? get(b) : 0u;
         s += c[j];
     }
     uint32_t tot;
-    const uint32_t ex = block_exclusive_sum<uint32_t, BLOCK>(s, &tot, red);
-    if (threadIdx.x == 0) {
+    const uint32_t ex = group_exclusive_sum<uint32_t, S>(s, &tot, red);
+    if (tid == 0) {
         st[0] = 0;
         st[1] = tot;
         st[2] = 0;
         st[3] = tot;
     }
-    __syncthreads();
+    S::sync();
     if (ex < g && g <= ex + s) {
         uint32_t above = ex;
 #pragma unroll
         for (int j = 0; j < BPT; j++) {
             if (above < g && g <= above + c[j]) {
-                st[0] = (uint32_t)(BINS - 1 - BPT * (int)threadIdx.x - j);
+                st[0] = (uint32_t)(BINS - 1 - BPT * (int)tid - j);
                 st[1] = above;
                 st[2] = c[j];
             }
             above += c[j];
         }
     }
-    __syncthreads();
+    S::sync();
+}
+
+template <int BINS, int BLOCK, typename Get>
+__device__ void block_find_bin(const Get& get, uint32_t g, uint32_t* red, uint32_t* st) {
+    group_find_bin<BINS, SyncBlock<BLOCK>>(get, g, red, st);
 }
 
 // 16-byte asynchronous copy global -> shared (through L2), and its completion.
@@ -295,21 +303,324 @@ struct ScanArgs {
                             // after the accumulation, once the previous launch (the query's first
                             // windows) is complete
     uint32_t w0;            // first window of this launch
+    uint32_t nq;            // pipelined scan: query rows and windows of the launch's items
+    uint32_t nwin;
     Workspace ws;
 };
 
+// Shared-memory scratch of one window cut, owned by the threads that select.
+struct CutScratch {
+    uint32_t* hist;         // [kHistBins]
+    uint32_t* hist2;        // [kSubBins]
+    unsigned char* region;  // per-warp private histograms, then staged keys (16-byte aligned)
+    uint32_t region_bytes;
+    uint32_t* warp_off;     // [warps of the group]
+    uint32_t* red;          // [warps of the group + 1]
+    uint32_t* st;           // [4]
+    uint32_t* s_staged;     // [1]
+};
+
+// The term table of one query over one window, for terms c0 .. c0 + nc - 1
+// of the query (nc <= the group's thread count): every term's posting range
+// and weight, and the map from warp chunks to terms. Returns the number of
+// chunks. Every thread of the group S calls it.
+template <int DT, typename S>
+__device__ uint32_t build_term_table(const ScanArgs& a, uint32_t w, int64_t qb, int c0, int nc, uint32_t* t_start,
+                                     uint32_t* t_end, float* t_w, uint32_t* c_pre, uint16_t* c_term, uint32_t* red) {
+    const DevIndex& ix = a.ix;
+    const int tid = S::tid();
+    uint32_t nch = 0;
+    if (tid < nc) {
+        const int32_t j = a.q_indices[qb + c0 + tid];
+        const float qv = a.q_values[qb + c0 + tid];
+        uint32_t start = 0, len = 0;
+        float wq = 0.0f;
+        if (j >= 0 && j < ix.dim && isfinite(qv)) {
+            const uint64_t sg = (uint64_t)j * ix.sigma + w;
+            start = ix.seg[sg];
+            len = ix.seg[sg + 1] - start;
+            wq = (DT == SINDI_F8E4M3) ? qv * ix.scale[j] : qv;
+        } else if (w == 0) {
+            atomicOr(ix.err, (j < 0 || j >= ix.dim) ? kErrQueryDim : kErrQueryValue);
+        }
+        t_start[tid] = start;
+        t_end[tid] = start + len;
+        t_w[tid] = wq;
+        // chunks of a long list tile its 8-aligned groups of postings
+        nch = len >= kVecMin ? (((start + len + 7u) & ~7u) - (start & ~7u) + kChunkLen - 1) / kChunkLen
+                             : (len ? 1u : 0u);
+    }
+    uint32_t total;
+    const uint32_t excl = group_exclusive_sum<uint32_t, S>(nch, &total, red);
+    if (tid < nc) {
+        c_pre[tid] = excl;
+        for (uint32_t c = excl; c < excl + nch && c < (uint32_t)kChunkTable; c++) c_term[c] = (uint16_t)tid;
+    }
+    S::sync();
+    return total;
+}
+
+// Scatter-add of one term table into the window A (Alg. 2's product and
+// accumulation loops): warp `warp` of NW takes chunks warp, warp + NW, ...;
+// the next chunk's loads are issued before this chunk's adds.
+template <int DT, int NW>
+__device__ __forceinline__ void accumulate_table(const DevIndex& ix, const uint32_t* t_start, const uint32_t* t_end,
+                                                 const float* t_w, const uint32_t* c_pre, const uint16_t* c_term,
+                                                 int nc, uint32_t total, int warp, int lane, float* A) {
+    uint32_t c = (uint32_t)warp;
+    Chunk cur;
+    if (c < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, c, lane, cur);
+    while (c < total) {
+        const uint32_t cn = c + NW;
+        Chunk nxt;
+        if (cn < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, cn, lane, nxt);
+        add_chunk(A, cur);
+        cur = nxt;
+        c = cn;
+    }
+}
+
+// The cut of one accumulated window w of query row y: emits into the query's
+// candidate list every slot that can still be among its best g, and adds what
+// it emitted to the query's histogram H (ids >= N are not candidates).
+// `bounded`: g candidates of the query already exist at or above bin pbin.
+// Every thread of the group S (NW warps) calls it; the workspace must be free.
+template <typename S, int NW>
+__device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uint32_t y, bool bounded, uint32_t pbin,
+                              const CutScratch& cs) {
+    constexpr int NT = S::kThreads;
+    const DevIndex& ix = a.ix;
+    const int tid = S::tid();
+    const int lane = tid & 31, warp = tid >> 5;
+    uint32_t* hist = cs.hist;
+    uint32_t* hist2 = cs.hist2;
+    uint32_t* warp_off = cs.warp_off;
+    uint32_t* red = cs.red;
+    uint32_t* st = cs.st;
+    uint64_t* stage = reinterpret_cast<uint64_t*>(cs.region);
+    const uint32_t stage_cap = cs.region_bytes / 8;
+    uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
+    const uint32_t lambda = ix.lambda;
+    const int64_t gbase = (int64_t)w * lambda;
+    const int64_t rest = ix.n_docs - gbase;
+    const int n_eff = (int)(rest < (int64_t)lambda ? rest : (int64_t)lambda);
+    const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
+    auto key_of = [&](int i) -> uint64_t { return result_key(A[i], (uint32_t)(gbase + i)); };
+    uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
+    if (bounded) {
+        // g candidates at or above bin pbin already exist, so only slots in
+        // bins >= pbin can be in the answer. When they fit the window's
+        // budget, emit all of them: no window histogram, no cut.
+        const unsigned lt = (1u << lane) - 1u;
+        uint32_t cnt = 0;
+        for (int base = warp * 32; base < n_eff; base += NT) {
+            const int i = base + lane;
+            const bool ok = i < n_eff && (float_order_bits(A[i]) >> (32 - kHistBits)) >= pbin;
+            cnt += (uint32_t)__popc(__ballot_sync(kFull, ok));
+        }
+        if (lane == 0) warp_off[warp] = cnt;
+        S::sync();
+        if (tid == 0) {
+            uint32_t acc = 0;
+            for (int k = 0; k < NW; k++) {
+                const uint32_t c = warp_off[k];
+                warp_off[k] = acc;
+                acc += c;
+            }
+            cs.s_staged[0] = acc;
+            st[0] = acc && acc <= a.win_cap ? atomicAdd(a.ws.cand_count + y, acc) : 0u;
+        }
+        S::sync();
+        const uint32_t n_hi = cs.s_staged[0];
+        if (n_hi <= a.win_cap) {
+            uint32_t at = st[0] + warp_off[warp];
+            for (int base = warp * 32; base < n_eff && n_hi; base += NT) {
+                const int i = base + lane;
+                const uint32_t bin = i < n_eff ? float_order_bits(A[i]) >> (32 - kHistBits) : 0u;
+                const bool ok = i < n_eff && bin >= pbin;
+                const unsigned bal = __ballot_sync(kFull, ok);
+                if (ok) {
+                    const uint32_t pos = at + (uint32_t)__popc(bal & lt);
+                    if (pos < a.ws.cand_cap) cand[pos] = key_of(i);
+                    else atomicOr(ix.err, kErrCandOverflow);
+                    atomicAdd(H + bin, 1u);
+                }
+                at += (uint32_t)__popc(bal);
+            }
+            S::sync();  // warp_off and st are reused by the caller's next cut
+            return;
+        }
+        // too many: the cut below decides (group-uniform)
+    }
+    // level 1: 12-bit bins of the score key. Each warp counts its slots in a
+    // private histogram of the 256 bins below the window's top bin (no
+    // contention between warps); the window histogram is their sum. When the
+    // cut falls below that range, a full 4096-bin histogram is used instead.
+    uint32_t* priv = reinterpret_cast<uint32_t*>(cs.region) + warp * kRelBins;
+    uint32_t top_key = 0;
+    for (int i = tid; i < n_eff; i += NT) top_key = max(top_key, float_order_bits(A[i]));
+    top_key = __reduce_max_sync(kFull, top_key);
+    if (lane == 0) red[warp] = top_key;
+    for (int b = tid; b < kSubBins; b += NT) hist2[b] = 0;
+    S::sync();
+    if (tid == 0) {
+        uint32_t m = 0;
+        for (int i = 0; i < NW; i++) m = max(m, red[i]);
+        st[0] = m;
+    }
+    for (int b = lane; b < kRelBins; b += 32) priv[b] = 0;
+    S::sync();
+    const uint32_t top_bin = st[0] >> (32 - kHistBits);
+    for (int i = tid; i < n_eff; i += NT) {
+        const uint32_t rel = top_bin - (float_order_bits(A[i]) >> (32 - kHistBits));
+        atomicAdd(&priv[rel < (uint32_t)kRelBins ? rel : kRelBins - 1], 1u);
+    }
+    S::sync();
+    for (int b = tid; b < kRelBins; b += NT) {
+        uint32_t c = 0;
+        for (int k = 0; k < NW; k++) c += reinterpret_cast<uint32_t*>(cs.region)[k * kRelBins + b];
+        hist[b] = c;  // hist[rel] = slots in bin top_bin - rel (rel 255: that bin and all below)
+    }
+    S::sync();
+    group_find_bin<kRelBins, S>([&](int b) { return hist[kRelBins - 1 - b]; }, g_w, red, st);
+    const uint32_t rel_cut = kRelBins - 1 - st[0];
+    uint32_t bw = top_bin - rel_cut;
+    uint32_t above_bw = st[1];
+    uint32_t c_bw = st[1] + st[2];  // slots in bins >= bw
+    S::sync();
+    const bool relative = rel_cut < (uint32_t)kRelBins - 1;
+    if (!relative) {
+        for (int b = tid; b < kHistBins; b += NT) hist[b] = 0;
+        S::sync();
+        for (int base = 0; base < n_eff; base += NT) {
+            const int i = base + tid;
+            const int bin = i < n_eff ? (int)(float_order_bits(A[i]) >> (32 - kHistBits)) : -1;
+            const unsigned peers = __match_any_sync(kFull, bin);
+            if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+        }
+        S::sync();
+        group_find_bin<kHistBins, S>([&](int b) { return hist[b]; }, g_w, red, st);
+        bw = st[0];
+        above_bw = st[1];
+        c_bw = st[1] + st[2];
+        S::sync();
+    }
+    // slots of the window in 12-bit bin b (b within the histogram kept above)
+    auto bin_count = [&](uint32_t b) -> uint32_t {
+        if (!relative) return hist[b];
+        const uint32_t rel = top_bin - b;
+        return rel < (uint32_t)kRelBins - 1 ? hist[rel] : 0u;
+    };
+    wait_previous_kernels();  // the workspace is free from here on
+    uint32_t lo = bw;
+    // g slots already emitted at or above a bin prove the answer lies there
+    if (bounded && pbin > lo) lo = pbin;
+    const bool staged = relative && c_bw <= stage_cap;  // slots >= bin lo fit in the staging area
+    uint32_t n_src = (uint32_t)n_eff;
+    if (staged) {
+        // per-warp counts of slots at or above bin lo (from the private
+        // histograms) give every warp its staging range: no atomics below
+        uint32_t mine_w = 0;
+        for (int b = lane; b < kRelBins - 1; b += 32)
+            if (top_bin - (uint32_t)b >= lo) mine_w += priv[b];
+        mine_w = __reduce_add_sync(kFull, mine_w);
+        if (lane == 0) warp_off[warp] = mine_w;
+        S::sync();
+        if (tid == 0) {
+            uint32_t acc = 0;
+            for (int k = 0; k < NW; k++) {
+                const uint32_t c = warp_off[k];
+                warp_off[k] = acc;
+                acc += c;
+            }
+            cs.s_staged[0] = acc;
+        }
+        S::sync();  // the private histograms are dead from here on
+        uint32_t at = warp_off[warp];
+        const unsigned lt = (1u << lane) - 1u;
+        for (int base = warp * 32; base < n_eff; base += NT) {
+            const int i = base + lane;
+            const bool ok = i < n_eff && (float_order_bits(A[i]) >> (32 - kHistBits)) >= lo;
+            const unsigned bal = __ballot_sync(kFull, ok);
+            if (ok) stage[at + __popc(bal & lt)] = key_of(i);
+            at += __popc(bal);
+        }
+        S::sync();
+        n_src = cs.s_staged[0];
+    }
+    // candidates: the staged keys, or the whole window
+    auto src_key = [&](int i) -> uint64_t { return staged ? stage[i] : key_of(i); };
+    uint64_t thr = (uint64_t)lo << kKeyBinShift;
+    bool exact = false;
+    if (lo == bw) {
+        // level 2: the next 8 bits, inside bin bw only
+        for (int i = tid; i < (int)n_src; i += NT) {
+            const uint64_t k = src_key(i);
+            if ((uint32_t)(k >> kKeyBinShift) == bw)
+                atomicAdd(&hist2[(uint32_t)(k >> (kKeyBinShift - kSubBits)) & (kSubBins - 1)], 1u);
+        }
+        S::sync();
+        group_find_bin<kSubBins, S>([&](int b) { return hist2[b]; }, g_w - above_bw, red, st);
+        const uint32_t bw2 = st[0];
+        const uint32_t c_cut = above_bw + st[1] + st[2];   // slots at or above the 20-bit cut
+        S::sync();
+        thr = ((uint64_t)((bw << kSubBits) | bw2)) << (kKeyBinShift - kSubBits);
+        exact = c_cut > a.win_cap;
+    }
+    if (exact) {
+        // ties crowd the cut: exact best g_w of the window
+        thr = group_select_threshold<S>(src_key, (int)n_src, (int)g_w, hist2, st);
+    }
+    // emit keys >= thr: count, reserve the group's range with one atomic, write
+    uint32_t mine = 0;
+    for (int i = tid; i < (int)n_src; i += NT)
+        if (src_key(i) >= thr) mine++;
+    uint32_t total;
+    uint32_t pos = group_exclusive_sum<uint32_t, S>(mine, &total, red);
+    if (tid == 0) st[0] = total ? atomicAdd(a.ws.cand_count + y, total) : 0u;
+    S::sync();
+    pos += st[0];
+    for (int i = tid; i < (int)n_src && mine; i += NT) {
+        const uint64_t key = src_key(i);
+        if (key >= thr) {
+            if (pos < a.ws.cand_cap) cand[pos] = key;
+            else atomicOr(ix.err, kErrCandOverflow);
+            pos++;
+            mine--;
+        }
+    }
+    // what was emitted, per 12-bit bin, into the query's histogram: every
+    // bin above the cut bin in full, the rest of the emitted slots in it
+    const uint32_t tb = (uint32_t)(thr >> kKeyBinShift);
+    uint32_t above_mine = 0;
+    for (int b = tid; b < kHistBins; b += NT) {
+        const uint32_t c = (uint32_t)b > tb ? bin_count((uint32_t)b) : 0u;
+        if (c) {
+            above_mine += c;
+            atomicAdd(H + b, c);
+        }
+    }
+    uint32_t above;
+    (void)group_exclusive_sum<uint32_t, S>(above_mine, &above, red);
+    if (tid == 0 && total > above) atomicAdd(H + tb, total - above);
+    S::sync();  // hist, region and st are reused by the caller's next cut
+}
+
+// One block per (window, query): the term tables are staged in shared memory,
+// the block's warps scatter-add every term's postings of the window into A,
+// then the block cuts the window.
 template <int DT, bool QUERY_MAJOR, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanArgs a) {
     constexpr int kScanThreads = BLOCK;
     constexpr int kScanWarps = BLOCK / 32;
     constexpr int kTermChunk = BLOCK;   // query terms staged per pass (one per thread)
+    using S = SyncBlock<BLOCK>;
     // Shared memory: the window's scores, two histograms, and one region that
     // holds the term tables while postings are added and the staged
     // candidates of the window afterwards.
     constexpr int kTableBytes = ((4 * kTermChunk + 1) * 4 + kChunkTable * 2 + 15) & ~15;
     constexpr int kPrivBytes = kScanWarps * kRelBins * 4;
     constexpr int kRegionBytes = kTableBytes > kPrivBytes ? kTableBytes : kPrivBytes;
-    constexpr int kStageCap = kRegionBytes / 8;
     extern __shared__ float A[];                    // [lambda]
     __shared__ uint32_t hist[kHistBins];
     __shared__ uint32_t hist2[kSubBins];
@@ -323,7 +634,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     uint32_t* c_pre = t_end + kTermChunk;
     float* t_w = reinterpret_cast<float*>(c_pre + kTermChunk + 1);
     uint16_t* c_term = reinterpret_cast<uint16_t*>(t_w + kTermChunk);
-    uint64_t* stage = reinterpret_cast<uint64_t*>(region);
 
     const DevIndex& ix = a.ix;
     const uint32_t w = a.w0 + (QUERY_MAJOR ? blockIdx.y : blockIdx.x);
@@ -345,53 +655,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     const int nt = (int)(a.q_indptr[r + 1] - qb);
 
     for (uint32_t m = threadIdx.x; m < lambda; m += kScanThreads) A[m] = 0.0f;
-    if (threadIdx.x < kSubBins) hist2[threadIdx.x] = 0;
 
     for (int c0 = 0; c0 < nt; c0 += kTermChunk) {
         const int nc = min(kTermChunk, nt - c0);
         __syncthreads();  // previous chunk fully consumed
-        uint32_t nch = 0;
-        if ((int)threadIdx.x < nc) {
-            const int32_t j = a.q_indices[qb + c0 + threadIdx.x];
-            const float qv = a.q_values[qb + c0 + threadIdx.x];
-            uint32_t start = 0, len = 0;
-            float wq = 0.0f;
-            if (j >= 0 && j < ix.dim && isfinite(qv)) {
-                const uint64_t s = (uint64_t)j * ix.sigma + w;
-                start = ix.seg[s];
-                len = ix.seg[s + 1] - start;
-                wq = (DT == SINDI_F8E4M3) ? qv * ix.scale[j] : qv;
-            } else if (w == 0) {
-                atomicOr(ix.err, (j < 0 || j >= ix.dim) ? kErrQueryDim : kErrQueryValue);
-            }
-            t_start[threadIdx.x] = start;
-            t_end[threadIdx.x] = start + len;
-            t_w[threadIdx.x] = wq;
-            // chunks of a long list tile its 8-aligned groups of postings
-            nch = len >= kVecMin ? (((start + len + 7u) & ~7u) - (start & ~7u) + kChunkLen - 1) / kChunkLen
-                                 : (len ? 1u : 0u);
-        }
-        uint32_t total;
-        const uint32_t excl = block_exclusive_sum<uint32_t, kScanThreads>(nch, &total, red);
-        if ((int)threadIdx.x < nc) {
-            c_pre[threadIdx.x] = excl;
-            for (uint32_t c = excl; c < excl + nch && c < (uint32_t)kChunkTable; c++) c_term[c] = (uint16_t)threadIdx.x;
-        }
-        __syncthreads();
-
-        // scatter-add: a warp takes chunks of one list; the next chunk's loads are
-        // issued before this chunk's adds
-        uint32_t c = (uint32_t)warp;
-        Chunk cur;
-        if (c < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, c, lane, cur);
-        while (c < total) {
-            const uint32_t cn = c + kScanWarps;
-            Chunk nxt;
-            if (cn < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, cn, lane, nxt);
-            add_chunk(A, cur);
-            cur = nxt;
-            c = cn;
-        }
+        const uint32_t total = build_term_table<DT, S>(a, w, qb, c0, nc, t_start, t_end, t_w, c_pre, c_term, red);
+        accumulate_table<DT, kScanWarps>(ix, t_start, t_end, t_w, c_pre, c_term, nc, total, warp, lane, A);
     }
     __syncthreads();
 
@@ -400,13 +669,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     // accumulation
     allow_next_kernel();
 
-    // ---- window selection (ids >= N are not candidates)
-    const int64_t gbase = (int64_t)w * lambda;
-    const int64_t rest = ix.n_docs - gbase;
-    const int n_eff = (int)(rest < (int64_t)lambda ? rest : (int64_t)lambda);
-    const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
-    auto key_of = [&](int i) -> uint64_t { return result_key(A[i], (uint32_t)(gbase + i)); };
-    uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
     uint32_t pbin = 0;  // bin of the g-th emitted candidate, when g have been emitted
     bool bounded = false;
     if (a.use_partial == 1) {
@@ -423,200 +685,161 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
         pbin = st[0];
         __syncthreads();
     }
-    if (bounded) {
-        // g candidates at or above bin pbin already exist, so only slots in
-        // bins >= pbin can be in the answer. When they fit the window's
-        // budget, emit all of them: no window histogram, no cut.
-        const unsigned lt = (1u << lane) - 1u;
-        uint32_t cnt = 0;
-        for (int base = warp * 32; base < n_eff; base += kScanThreads) {
-            const int i = base + lane;
-            const bool ok = i < n_eff && (float_order_bits(A[i]) >> (32 - kHistBits)) >= pbin;
-            cnt += (uint32_t)__popc(__ballot_sync(kFull, ok));
-        }
-        if (lane == 0) warp_off[warp] = cnt;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t acc = 0;
-            for (int k = 0; k < kScanWarps; k++) {
-                const uint32_t c = warp_off[k];
-                warp_off[k] = acc;
-                acc += c;
-            }
-            s_staged = acc;
-            st[0] = acc && acc <= a.win_cap ? atomicAdd(a.ws.cand_count + y, acc) : 0u;
-        }
-        __syncthreads();
-        const uint32_t n_hi = s_staged;
-        if (n_hi <= a.win_cap) {
-            uint32_t at = st[0] + warp_off[warp];
-            for (int base = warp * 32; base < n_eff && n_hi; base += kScanThreads) {
-                const int i = base + lane;
-                const uint32_t bin = i < n_eff ? float_order_bits(A[i]) >> (32 - kHistBits) : 0u;
-                const bool ok = i < n_eff && bin >= pbin;
-                const unsigned bal = __ballot_sync(kFull, ok);
-                if (ok) {
-                    const uint32_t pos = at + (uint32_t)__popc(bal & lt);
-                    if (pos < a.ws.cand_cap) cand[pos] = key_of(i);
-                    else atomicOr(ix.err, kErrCandOverflow);
-                    atomicAdd(H + bin, 1u);
-                }
-                at += (uint32_t)__popc(bal);
-            }
-            return;
-        }
-        // too many: the cut below decides (block-uniform)
-    }
-    // level 1: 12-bit bins of the score key. Each warp counts its slots in a
-    // private histogram of the 256 bins below the window's top bin (no
-    // contention between warps); the window histogram is their sum. When the
-    // cut falls below that range, a full 4096-bin histogram is used instead.
-    uint32_t* priv = reinterpret_cast<uint32_t*>(region) + warp * kRelBins;
-    uint32_t top_key = 0;
-    for (int i = threadIdx.x; i < n_eff; i += kScanThreads) top_key = max(top_key, float_order_bits(A[i]));
-    top_key = __reduce_max_sync(kFull, top_key);
-    if (lane == 0) red[warp] = top_key;
-    __syncthreads();  // (also: the term tables are dead from here on)
-    if (threadIdx.x == 0) {
-        uint32_t m = 0;
-        for (int i = 0; i < kScanWarps; i++) m = max(m, red[i]);
-        st[0] = m;
-    }
-    for (int b = lane; b < kRelBins; b += 32) priv[b] = 0;
-    __syncthreads();
-    const uint32_t top_bin = st[0] >> (32 - kHistBits);
-    for (int i = threadIdx.x; i < n_eff; i += kScanThreads) {
-        const uint32_t rel = top_bin - (float_order_bits(A[i]) >> (32 - kHistBits));
-        atomicAdd(&priv[rel < (uint32_t)kRelBins ? rel : kRelBins - 1], 1u);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < kRelBins; b += kScanThreads) {
-        uint32_t c = 0;
-        for (int k = 0; k < kScanWarps; k++) c += reinterpret_cast<uint32_t*>(region)[k * kRelBins + b];
-        hist[b] = c;  // hist[rel] = slots in bin top_bin - rel (rel 255: that bin and all below)
-    }
-    __syncthreads();
-    block_find_bin<kRelBins, kScanThreads>([&](int b) { return hist[kRelBins - 1 - b]; }, g_w, red, st);
-    const uint32_t rel_cut = kRelBins - 1 - st[0];
-    uint32_t bw = top_bin - rel_cut;
-    uint32_t above_bw = st[1];
-    uint32_t c_bw = st[1] + st[2];  // slots in bins >= bw
-    __syncthreads();
-    const bool relative = rel_cut < (uint32_t)kRelBins - 1;
-    if (!relative) {
-        for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) hist[b] = 0;
-        __syncthreads();
-        for (int base = 0; base < n_eff; base += kScanThreads) {
-            const int i = base + threadIdx.x;
-            const int bin = i < n_eff ? (int)(float_order_bits(A[i]) >> (32 - kHistBits)) : -1;
-            const unsigned peers = __match_any_sync(kFull, bin);
-            if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-        }
-        __syncthreads();
-        block_find_bin<kHistBins, kScanThreads>([&](int b) { return hist[b]; }, g_w, red, st);
-        bw = st[0];
-        above_bw = st[1];
-        c_bw = st[1] + st[2];
-        __syncthreads();
-    }
-    // slots of the window in 12-bit bin b (b within the histogram kept above)
-    auto bin_count = [&](uint32_t b) -> uint32_t {
-        if (!relative) return hist[b];
-        const uint32_t rel = top_bin - b;
-        return rel < (uint32_t)kRelBins - 1 ? hist[rel] : 0u;
+    const CutScratch cs{hist, hist2, region, (uint32_t)kRegionBytes, warp_off, red, st, &s_staged};
+    select_window<S, kScanWarps>(a, A, w, y, bounded, pbin, cs);
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined window scan: one resident block per SM walks a list of (window,
+// query) items with two window arrays in shared memory. Warps 0..23 scatter-
+// add item i + 1 into one array while warps 24..31 cut item i in the other
+// and build the term tables ahead, so the shared-memory scatter-add (the
+// scan's bound) does not stop for the cut. Hardware named barriers hand the
+// arrays and tables between the two groups:
+//   ready[t]: table t holds the next stage's terms (cut group -> add group)
+//   free[t]:  the add group is done with table t (add -> cut)
+//   done[b]:  array b holds an item's complete scores (add -> cut)
+//   empty[b]: array b is cut and zeroed again (cut -> add)
+// An item with more terms than one table holds takes several stages.
+// ---------------------------------------------------------------------------
+constexpr int kPipeAddWarps = 24;
+constexpr int kPipeCutWarps = 8;
+constexpr int kPipeThreads = (kPipeAddWarps + kPipeCutWarps) * 32;
+constexpr int kPipeTerms = kPipeCutWarps * 32;  // query terms per table (one per cutting thread)
+constexpr int kPipeTableBytes = ((4 * kPipeTerms + 1) * 4 + kChunkTable * 2 + 15) & ~15;
+constexpr int kPipeRegionBytes = 16384;         // cut scratch: 8 KiB private histograms / 2,048 staged keys
+constexpr uint32_t kPipeMaxWindow = 16384;      // two window arrays of 64 KiB each
+constexpr int kBarReady = 1, kBarFree = 3, kBarDone = 5, kBarEmpty = 7, kBarCut = 9;
+
+__device__ __forceinline__ void named_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kPipeThreads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "n"(kPipeThreads) : "memory");
+}
+
+static size_t pipe_smem_bytes(uint32_t lambda) {
+    return (((size_t)8 * lambda + 15) & ~(size_t)15) + 2 * (size_t)kPipeTableBytes + kPipeRegionBytes;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kPipeThreads, 1) scan_pipe_kernel(ScanArgs a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ uint32_t hist[kHistBins];
+    __shared__ uint32_t hist2[kSubBins];
+    __shared__ uint32_t warp_off[kPipeCutWarps];
+    __shared__ uint32_t red[kPipeCutWarps + 1];
+    __shared__ uint32_t st[4];
+    __shared__ uint32_t s_staged;
+    __shared__ uint32_t t_total[2];
+    __shared__ int t_nc[2];
+    using S = SyncGroup<kBarCut, kPipeCutWarps * 32, kPipeAddWarps * 32>;
+    const DevIndex& ix = a.ix;
+    const uint32_t lambda = ix.lambda;
+    float* buf0 = reinterpret_cast<float*>(dsm);
+    unsigned char* tab = dsm + (((size_t)8 * lambda + 15) & ~(size_t)15);
+    unsigned char* region = tab + 2 * kPipeTableBytes;
+    auto t_start = [&](int t) { return reinterpret_cast<uint32_t*>(tab + t * kPipeTableBytes); };
+    auto t_end = [&](int t) { return t_start(t) + kPipeTerms; };
+    auto c_pre = [&](int t) { return t_start(t) + 2 * kPipeTerms; };
+    auto t_w = [&](int t) { return reinterpret_cast<float*>(t_start(t) + 3 * kPipeTerms + 1); };
+    auto c_term = [&](int t) { return reinterpret_cast<uint16_t*>(t_start(t) + 4 * kPipeTerms + 1); };
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // items: k = blockIdx.x + it * gridDim.x; window w0 + k / nq, query row k % nq
+    const uint32_t n_all = a.nq * a.nwin;
+    const uint32_t n_my = blockIdx.x < n_all ? (n_all - blockIdx.x + gridDim.x - 1) / gridDim.x : 0u;
+    auto item_y = [&](uint32_t it) { return (blockIdx.x + it * gridDim.x) % a.nq; };
+    auto item_w = [&](uint32_t it) { return a.w0 + (blockIdx.x + it * gridDim.x) / a.nq; };
+    auto passes = [&](uint32_t y) {
+        const int64_t r = a.q_first + y;
+        const int nt = (int)(a.q_indptr[r + 1] - a.q_indptr[r]);
+        return nt > 0 ? (nt + kPipeTerms - 1) / kPipeTerms : 1;
     };
-    wait_previous_kernels();  // the workspace is free from here on
-    uint32_t lo = bw;
-    // g slots already emitted at or above a bin prove the answer lies there
-    if (bounded && pbin > lo) lo = pbin;
-    const bool staged = relative && c_bw <= (uint32_t)kStageCap;  // slots >= bin lo fit in the staging area
-    uint32_t n_src = (uint32_t)n_eff;
-    if (staged) {
-        // per-warp counts of slots at or above bin lo (from the private
-        // histograms) give every warp its staging range: no atomics below
-        uint32_t mine_w = 0;
-        for (int b = lane; b < kRelBins - 1; b += 32)
-            if (top_bin - (uint32_t)b >= lo) mine_w += priv[b];
-        mine_w = __reduce_add_sync(kFull, mine_w);
-        if (lane == 0) warp_off[warp] = mine_w;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t acc = 0;
-            for (int k = 0; k < kScanWarps; k++) {
-                const uint32_t c = warp_off[k];
-                warp_off[k] = acc;
-                acc += c;
-            }
-            s_staged = acc;
-        }
-        __syncthreads();  // the private histograms are dead from here on
-        uint32_t at = warp_off[warp];
-        const unsigned lt = (1u << lane) - 1u;
-        for (int base = warp * 32; base < n_eff; base += kScanThreads) {
-            const int i = base + lane;
-            const bool ok = i < n_eff && (float_order_bits(A[i]) >> (32 - kHistBits)) >= lo;
-            const unsigned bal = __ballot_sync(kFull, ok);
-            if (ok) stage[at + __popc(bal & lt)] = key_of(i);
-            at += __popc(bal);
-        }
-        __syncthreads();
-        n_src = s_staged;
-    }
-    // candidates: the staged keys, or the whole window
-    auto src_key = [&](int i) -> uint64_t { return staged ? stage[i] : key_of(i); };
-    uint64_t thr = (uint64_t)lo << kKeyBinShift;
-    bool exact = false;
-    if (lo == bw) {
-        // level 2: the next 8 bits, inside bin bw only
-        for (int i = threadIdx.x; i < (int)n_src; i += kScanThreads) {
-            const uint64_t k = src_key(i);
-            if ((uint32_t)(k >> kKeyBinShift) == bw)
-                atomicAdd(&hist2[(uint32_t)(k >> (kKeyBinShift - kSubBits)) & (kSubBins - 1)], 1u);
-        }
-        __syncthreads();
-        block_find_bin<kSubBins, kScanThreads>([&](int b) { return hist2[b]; }, g_w - above_bw, red, st);
-        const uint32_t bw2 = st[0];
-        const uint32_t c_cut = above_bw + st[1] + st[2];   // slots at or above the 20-bit cut
-        __syncthreads();
-        thr = ((uint64_t)((bw << kSubBits) | bw2)) << (kKeyBinShift - kSubBits);
-        exact = c_cut > a.win_cap;
-    }
-    if (exact) {
-        // ties crowd the cut: exact best g_w of the window
-        thr = block_select_threshold<kScanThreads>(src_key, (int)n_src, (int)g_w, hist2, st);
-    }
-    // emit keys >= thr: count, reserve the block's range with one atomic, write
-    uint32_t mine = 0;
-    for (int i = threadIdx.x; i < (int)n_src; i += kScanThreads)
-        if (src_key(i) >= thr) mine++;
-    uint32_t total;
-    uint32_t pos = block_exclusive_sum<uint32_t, kScanThreads>(mine, &total, red);
-    if (threadIdx.x == 0) st[0] = total ? atomicAdd(a.ws.cand_count + y, total) : 0u;
+
+    for (uint32_t m = threadIdx.x; m < 2 * lambda; m += kPipeThreads) buf0[m] = 0.0f;
     __syncthreads();
-    pos += st[0];
-    for (int i = threadIdx.x; i < (int)n_src && mine; i += kScanThreads) {
-        const uint64_t key = src_key(i);
-        if (key >= thr) {
-            if (pos < a.ws.cand_cap) cand[pos] = key;
-            else atomicOr(ix.err, kErrCandOverflow);
-            pos++;
-            mine--;
+
+    if (warp < kPipeAddWarps) {
+        // ---- add group: scatter-add stage after stage
+        int s = 0;
+        for (uint32_t it = 0; it < n_my; it++) {
+            const int np = passes(item_y(it));
+            const int b = it & 1;
+            for (int p = 0; p < np; p++, s++) {
+                const int t = s & 1;
+                named_sync(kBarReady + t);
+                if (p == 0 && it >= 2) named_sync(kBarEmpty + b);
+                accumulate_table<DT, kPipeAddWarps>(ix, t_start(t), t_end(t), t_w(t), c_pre(t), c_term(t), t_nc[t],
+                                                    t_total[t], warp, lane, buf0 + (size_t)b * lambda);
+                named_arrive(kBarFree + t);
+                if (p == np - 1) named_arrive(kBarDone + b);
+            }
         }
+        allow_next_kernel();
+        return;
     }
-    // what was emitted, per 12-bit bin, into the query's histogram: every
-    // bin above the cut bin in full, the rest of the emitted slots in it
-    const uint32_t tb = (uint32_t)(thr >> kKeyBinShift);
-    uint32_t above_mine = 0;
-    for (int b = threadIdx.x; b < kHistBins; b += kScanThreads) {
-        const uint32_t c = (uint32_t)b > tb ? bin_count((uint32_t)b) : 0u;
-        if (c) {
-            above_mine += c;
-            atomicAdd(H + b, c);
+
+    // ---- cut group: tables ahead, then the cut of every accumulated item
+    const CutScratch cs{hist, hist2, region, (uint32_t)kPipeRegionBytes, warp_off, red, st, &s_staged};
+    uint32_t bi = 0;  // next stage to build: item bi, pass bp
+    int bp = 0;
+    auto build_next = [&](int t) {
+        const uint32_t y = item_y(bi), w = item_w(bi);
+        const int64_t r = a.q_first + y;
+        const int64_t qb = a.q_indptr[r];
+        const int nt = (int)(a.q_indptr[r + 1] - qb);
+        const int c0 = bp * kPipeTerms;
+        const int nc = nt - c0 < kPipeTerms ? (nt - c0 > 0 ? nt - c0 : 0) : kPipeTerms;
+        const uint32_t total = build_term_table<DT, S>(a, w, qb, c0, nc, t_start(t), t_end(t), t_w(t), c_pre(t),
+                                                       c_term(t), red);
+        if (S::tid() == 0) {
+            t_total[t] = total;
+            t_nc[t] = nc;
         }
+        const int np = nt > 0 ? (nt + kPipeTerms - 1) / kPipeTerms : 1;
+        if (++bp == np) {
+            bp = 0;
+            bi++;
+        }
+    };
+    if (bi < n_my) {
+        build_next(0);
+        named_arrive(kBarReady + 0);
     }
-    uint32_t above;
-    (void)block_exclusive_sum<uint32_t, kScanThreads>(above_mine, &above, red);
-    if (threadIdx.x == 0 && total > above) atomicAdd(H + tb, total - above);
+    if (bi < n_my) {
+        build_next(1);
+        named_arrive(kBarReady + 1);
+    }
+    int s = 0;
+    for (uint32_t it = 0; it < n_my; it++) {
+        const uint32_t y = item_y(it), w = item_w(it);
+        const int np = passes(y);
+        const int b = it & 1;
+        for (int p = 0; p < np; p++, s++) {
+            const int t = s & 1;
+            named_sync(kBarFree + t);
+            if (bi < n_my) {
+                build_next(t);
+                named_arrive(kBarReady + t);
+            }
+        }
+        named_sync(kBarDone + b);
+        // the workspace (and, for a query's later windows, H) is final from here on;
+        // tables read only the index and the queries, so they were built before
+        if (it == 0) wait_previous_kernels();
+        if (it + 1 == n_my) allow_next_kernel();
+        // the query's running bound: g candidates emitted at or above a bin
+        const uint32_t* H = a.ws.hist + (size_t)y * kHistBins;
+        group_find_bin<kHistBins, S>([&](int bb) { return __ldcg(H + bb); }, a.g, red, st);
+        const bool bounded = st[3] >= a.g;
+        const uint32_t pbin = st[0];
+        S::sync();
+        float* A = buf0 + (size_t)b * lambda;
+        select_window<S, kPipeCutWarps>(a, A, w, y, bounded, pbin, cs);
+        for (uint32_t m = (uint32_t)S::tid(); m < lambda; m += S::kThreads) A[m] = 0.0f;
+        if (it + 2 < n_my) named_arrive(kBarEmpty + b);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1093,12 +1316,38 @@ static void allow_window_smem() {
 
 template <int DT>
 static void allow_window_smem_dt() {
+    SINDI_CUDA(cudaFuncSetAttribute(scan_pipe_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)pipe_smem_bytes(kPipeMaxWindow)));
     allow_window_smem<DT, false, 256>();
     allow_window_smem<DT, false, 512>();
     allow_window_smem<DT, false, 1024>();
     allow_window_smem<DT, true, 256>();
     allow_window_smem<DT, true, 512>();
     allow_window_smem<DT, true, 1024>();
+}
+
+// SMs of the device (once per device).
+static int device_sms(int device) {
+    static std::mutex mu;
+    static std::map<int, int> sms;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = sms.find(device);
+    if (it != sms.end()) return it->second;
+    int n = 0;
+    SINDI_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device));
+    sms[device] = n;
+    return n;
+}
+
+template <int DT>
+static void launch_pipe_t(const ScanArgs& a, uint32_t blocks, size_t smem, cudaStream_t s, bool pdl) {
+    launch_kernel(scan_pipe_kernel<DT>, dim3(blocks), dim3(kPipeThreads), smem, s, pdl, a);
+}
+
+static void launch_pipe(int dt, const ScanArgs& a, uint32_t blocks, size_t smem, cudaStream_t s, bool pdl) {
+    if (dt == SINDI_F32) launch_pipe_t<SINDI_F32>(a, blocks, smem, s, pdl);
+    else if (dt == SINDI_F16) launch_pipe_t<SINDI_F16>(a, blocks, smem, s, pdl);
+    else launch_pipe_t<SINDI_F8E4M3>(a, blocks, smem, s, pdl);
 }
 
 // Shared-memory limits of every search kernel, set once per device before the
@@ -1167,25 +1416,43 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
     // the coarse scan reads the beta-pruned queries when there are any (Alg. 4, the query-pruning step);
     // merge and rerank check and reorder with the full queries
     ScanArgs sa{dix, scan_q ? scan_q->indptr : q_indptr, scan_q ? scan_q->indices : q_indices,
-                scan_q ? scan_q->values : q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, 0u, ws};
+                scan_q ? scan_q->values : q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, 0u, nq, ix.sigma, ws};
     if (ev0) SINDI_CUDA(cudaEventRecord(ev0, stream));
-    if (!batched && ix.sigma >= kSplitMinWindows) {
+    // the pipelined scan when asked for and its two window arrays fit; any
+    // other shape is one block per window (block 0 or 1: the default size)
+    const bool pipe = pl.block == SINDI_SCAN_PIPELINED && ix.lambda <= kPipeMaxWindow;
+    const uint32_t block = pl.block == SINDI_SCAN_PIPELINED ? 0u : pl.block;
+    const size_t pipe_smem = pipe_smem_bytes(ix.lambda);
+    if (pipe && batched) {
+        // one resident block per SM walks the (window, query) items in
+        // window-major order, so a query's windows come one after another
+        const uint64_t items = (uint64_t)nq * ix.sigma;
+        const uint32_t blocks = (uint32_t)std::min<uint64_t>(items, (uint64_t)device_sms(ix.device));
+        launch_pipe(ix.dtype, sa, blocks, pipe_smem, stream, *chained && !ev0);
+    } else if (!batched && ix.sigma >= kSplitMinWindows) {
         // One query: its first windows run alone and fill the query's
         // histogram of candidates; the other windows then emit only what can
         // still enter the answer (the running bound of Alg. 2's heap, taken
         // from a block of windows instead of one window at a time).
         const uint32_t first = std::max<uint32_t>(2u, (ix.sigma + kSplitFraction - 1) / kSplitFraction);
-        launch_scan_pdl(ix.dtype, pl.block, false, false, sa, first, nq, scan_smem, stream, *chained && !ev0);
+        launch_scan_pdl(ix.dtype, block, false, false, sa, first, nq, scan_smem, stream, *chained && !ev0);
         ScanArgs sb = sa;
         sb.use_partial = 2;
         sb.w0 = first;
-        launch_scan_pdl(ix.dtype, pl.block, false, false, sb, ix.sigma - first, nq, scan_smem, stream, true);
+        sb.nwin = ix.sigma - first;
+        if (pipe) {
+            // a few blocks per query, each walking several windows
+            const uint32_t blocks = (sb.nwin + kPlainPipeItems - 1) / kPlainPipeItems;
+            launch_pipe(ix.dtype, sb, blocks, pipe_smem, stream, true);
+        } else {
+            launch_scan_pdl(ix.dtype, block, false, false, sb, ix.sigma - first, nq, scan_smem, stream, true);
+        }
         ix.launches += 1;
         ix.scan_launches += 1;
     } else {
         // query-major grids put the queries of one window next to each other
         // (shared lists stay in L2); gridDim.y limits sigma to 65535 there
-        launch_scan_pdl(ix.dtype, pl.block, batched, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem,
+        launch_scan_pdl(ix.dtype, block, batched, batched && ix.sigma <= 65535u, sa, ix.sigma, nq, scan_smem,
                         stream, *chained && !ev0);
     }
     if (ev1) SINDI_CUDA(cudaEventRecord(ev1, stream));

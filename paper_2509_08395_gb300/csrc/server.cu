@@ -234,7 +234,7 @@ sindi_status sindi_server_create(const sindi_index* index, const sindi_server_pa
     const sindi_search_params& sp = p.search;
     if (p.max_batch > 4096 || p.max_slots > 64 || p.max_query_nnz > 2048 || sp.k < 1 || sp.k > kMaxK ||
         (sp.gamma != 0 && (sp.gamma < sp.k || sp.gamma > kMaxGamma)) || !(sp.beta > 0.0 && sp.beta <= 1.0) ||
-        (sp.block_threads != 0 && sp.block_threads != 256 && sp.block_threads != 512 && sp.block_threads != 1024)) {
+        !valid_block_threads(sp.block_threads)) {
         set_last_error("max_batch <= 4096, max_slots <= 64, max_query_nnz <= 2048; k in [1, 1024]; gamma 0 or in "
                        "[k, 8192]; beta in (0, 1]");
         return SINDI_ERR_INVALID_ARG;

@@ -24,6 +24,7 @@ SINDI_MODE_PLAIN, SINDI_MODE_BATCHED = 0, 1
 DTYPES = {"f32": SINDI_F32, "f16": SINDI_F16, "f8": SINDI_F8E4M3, "e4m3": SINDI_F8E4M3}
 MODES = {"plain": SINDI_MODE_PLAIN, "batched": SINDI_MODE_BATCHED}
 SINDI_PRUNE_MASS, SINDI_PRUNE_VECTOR_NUMBER, SINDI_PRUNE_LIST, SINDI_PRUNE_MASS_LIST = 0, 1, 2, 3
+SINDI_SCAN_PIPELINED = 1  # block_threads value of the pipelined window scan
 PRUNES = {"mass": SINDI_PRUNE_MASS, "vector_number": SINDI_PRUNE_VECTOR_NUMBER, "list": SINDI_PRUNE_LIST,
           "mass_list": SINDI_PRUNE_MASS_LIST}
 STATUS_NAMES = {0: "SINDI_OK", 1: "SINDI_ERR_INVALID_ARG", 2: "SINDI_ERR_INVALID_DATA", 3: "SINDI_ERR_OOM",

@@ -66,7 +66,7 @@ def test_block_shapes_give_the_same_results(setup, mode):
     w, idx, _, (qp, qx, qv) = setup
     q = [_dev(qp), _dev(qx), _dev(qv)]
     ref = [t.cpu().numpy() for t in idx.search(*q, k=50, gamma=500, mode=mode)]
-    for block in (256, 512, 1024):
+    for block in (sindi.SINDI_SCAN_PIPELINED, 256, 512, 1024):
         got = [t.cpu().numpy() for t in idx.search(*q, k=50, gamma=500, mode=mode, block=block)]
         idx.check()
         _same(got[0], got[1], ref[0], ref[1], f"{mode} block {block}")

@@ -21,11 +21,11 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def run_search(idx, qp, qx, qv, k, gamma=0, mode="plain", host=False, beta=1.0):
+def run_search(idx, qp, qx, qv, k, gamma=0, mode="plain", host=False, beta=1.0, block=0):
     if host:
-        ids, sc = idx.search(qp, qx, qv, k=k, gamma=gamma, mode=mode, beta=beta)
+        ids, sc = idx.search(qp, qx, qv, k=k, gamma=gamma, mode=mode, beta=beta, block=block)
         return ids.astype(np.int64), sc
-    ids, sc = idx.search(dev(qp), dev(qx), dev(qv), k=k, gamma=gamma, mode=mode, beta=beta)
+    ids, sc = idx.search(dev(qp), dev(qx), dev(qv), k=k, gamma=gamma, mode=mode, beta=beta, block=block)
     idx.check()
     return ids.cpu().numpy().view(np.uint32).astype(np.int64), sc.cpu().numpy()
 
@@ -217,6 +217,25 @@ def test_large_candidate_pools(pruned_small, window, gamma, k, mode):
         ids, sc = run_search(idx, qp, qx, qv, k=k, gamma=gamma, mode=mode)
     for r in range(nq):
         check_reranked(ids[r], sc[r], D, Q, r, I, k, gamma, what=f"query {r}")
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_pipelined_scan_parity(pruned_small, mode):
+    """The pipelined window scan (one resident block per SM, scatter-add and cut overlapped), with queries of
+    300 to 700 terms so that a window takes several term tables: coarse and reordered answers vs the oracle."""
+    w, (ip, ix, v), _, D, _ = pruned_small
+    qp, qx, qv = datagen.generate(datagen.RowDist(10, datagen.NNZ_UNIFORM, 300, 700, 300, 700, val_sigma=0.8),
+                                  w.dim, w.zipf_s, 91)
+    Q = oracle.Dataset(qp, qx, qv, w.dim)
+    I = oracle.Index(D, window=2048, alpha=0.5)
+    pipe = sindi.SINDI_SCAN_PIPELINED
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=2048, alpha=0.5) as idx:
+        ids, sc = run_search(idx, qp, qx, qv, k=50, gamma=0, mode=mode, block=pipe)
+        rids, rsc = run_search(idx, qp, qx, qv, k=20, gamma=400, mode=mode, block=pipe)
+    for r in range(Q.n):
+        oi, os_ = I.search(Q, r, k=114, gamma=0)
+        check_ranked(ids[r], sc[r], oi, os_, 50, D.n, what=f"coarse query {r}")
+        check_reranked(rids[r], rsc[r], D, Q, r, I, 20, 400, what=f"rerank query {r}")
 
 
 def test_rerank_of_long_documents():
