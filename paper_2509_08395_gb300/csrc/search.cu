@@ -410,44 +410,65 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
     if (bounded) {
         // g candidates at or above bin pbin already exist, so only slots in
         // bins >= pbin can be in the answer. When they fit the window's
-        // budget, emit all of them: no window histogram, no cut.
+        // budget, emit all of them: no window histogram, no cut. One pass:
+        // every warp stages its slots in its own share of the staging area
+        // (in order, no atomics); then one reservation for the group.
         const unsigned lt = (1u << lane) - 1u;
+        const uint32_t share = stage_cap / NW;
+        uint64_t* mine_st = stage + (size_t)warp * share;
         uint32_t cnt = 0;
         for (int base = warp * 32; base < n_eff; base += NT) {
             const int i = base + lane;
             const bool ok = i < n_eff && (float_order_bits(A[i]) >> (32 - kHistBits)) >= pbin;
-            cnt += (uint32_t)__popc(__ballot_sync(kFull, ok));
+            const unsigned bal = __ballot_sync(kFull, ok);
+            const uint32_t at = cnt + (uint32_t)__popc(bal & lt);
+            if (ok && at < share) mine_st[at] = key_of(i);
+            cnt += (uint32_t)__popc(bal);
         }
         if (lane == 0) warp_off[warp] = cnt;
         S::sync();
         if (tid == 0) {
-            uint32_t acc = 0;
+            uint32_t acc = 0, over = 0;
             for (int k = 0; k < NW; k++) {
                 const uint32_t c = warp_off[k];
+                over |= c > share ? 1u : 0u;
                 warp_off[k] = acc;
                 acc += c;
             }
             cs.s_staged[0] = acc;
+            st[1] = over;
             st[0] = acc && acc <= a.win_cap ? atomicAdd(a.ws.cand_count + y, acc) : 0u;
         }
         S::sync();
         const uint32_t n_hi = cs.s_staged[0];
         if (n_hi <= a.win_cap) {
-            uint32_t at = st[0] + warp_off[warp];
-            for (int base = warp * 32; base < n_eff && n_hi; base += NT) {
-                const int i = base + lane;
-                const uint32_t bin = i < n_eff ? float_order_bits(A[i]) >> (32 - kHistBits) : 0u;
-                const bool ok = i < n_eff && bin >= pbin;
-                const unsigned bal = __ballot_sync(kFull, ok);
-                if (ok) {
-                    const uint32_t pos = at + (uint32_t)__popc(bal & lt);
-                    if (pos < a.ws.cand_cap) cand[pos] = key_of(i);
+            const uint32_t at0 = st[0] + warp_off[warp];
+            if (st[1] == 0) {
+                // the staged keys out, each counted in the query's histogram
+                for (uint32_t t = (uint32_t)lane; t < cnt; t += 32) {
+                    const uint64_t key = mine_st[t];
+                    if (at0 + t < a.ws.cand_cap) cand[at0 + t] = key;
                     else atomicOr(ix.err, kErrCandOverflow);
-                    atomicAdd(H + bin, 1u);
+                    atomicAdd(H + (uint32_t)(key >> kKeyBinShift), 1u);
                 }
-                at += (uint32_t)__popc(bal);
+            } else {
+                // a warp had more slots than its share: read the window again
+                uint32_t at = at0;
+                for (int base = warp * 32; base < n_eff; base += NT) {
+                    const int i = base + lane;
+                    const uint32_t bin = i < n_eff ? float_order_bits(A[i]) >> (32 - kHistBits) : 0u;
+                    const bool ok = i < n_eff && bin >= pbin;
+                    const unsigned bal = __ballot_sync(kFull, ok);
+                    if (ok) {
+                        const uint32_t pos = at + (uint32_t)__popc(bal & lt);
+                        if (pos < a.ws.cand_cap) cand[pos] = key_of(i);
+                        else atomicOr(ix.err, kErrCandOverflow);
+                        atomicAdd(H + bin, 1u);
+                    }
+                    at += (uint32_t)__popc(bal);
+                }
             }
-            S::sync();  // warp_off and st are reused by the caller's next cut
+            S::sync();  // warp_off, st and the staging area are reused by the caller's next cut
             return;
         }
         // too many: the cut below decides (group-uniform)
