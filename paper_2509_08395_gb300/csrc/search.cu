@@ -1392,9 +1392,9 @@ static void launch_scan_t(const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t
     launch_kernel(scan_window_kernel<DT, QM, BLOCK>, grid, dim3(BLOCK), smem, s, pdl, a);
 }
 
-// Plain schedules (one query) take window-major grids, by default of
-// 1024-thread blocks; batched schedules take query-major grids (window-major
-// when sigma exceeds the grid's y limit), by default of 512-thread blocks.
+// Plain schedules (one query) take window-major grids; batched schedules take
+// query-major grids (window-major when sigma exceeds the grid's y limit). Both
+// default to 512-thread blocks.
 template <int DT, bool QM>
 static void launch_scan_block(uint32_t block, const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem,
                               cudaStream_t s, bool pdl) {
