@@ -588,6 +588,10 @@ def main():
                 del dip, dix, dv
                 oi = torch.empty_like(out_ids)
                 os_ = torch.empty_like(out_sc)
+                # the other schedule too: reduced precision is a posting format, either schedule reads it
+                oth = "batched" if args.mode == "plain" else "plain"
+                forms[dt + "_" + oth] = {"qps": timed(lambda: lp.search(*q_dev, k=w.k, gamma=w.gamma, mode=oth,
+                                                                        out=(oi, os_)), args.steps)}
                 qps = timed(lambda: lp.search(*q_dev, k=w.k, gamma=w.gamma, mode=args.mode, out=(oi, os_)),
                             args.steps)
                 lp.check()
