@@ -301,6 +301,101 @@ __global__ void lp_compact_kernel(const uint32_t* keep, const uint32_t* off, int
     }
 }
 
+// Posting order inside every list segment I_{j,w}, for the window scan's
+// shared-memory scatter-add: the 32 postings one add instruction of a warp
+// takes should sit in 32 different shared-memory banks (window slot mod 32),
+// which makes the FP32 atomicAdd conflict-free. One warp per segment:
+//   1. every posting gets its bank b and a rank r among the segment's
+//      postings of bank b; ordering the postings by (r, b) visits the banks
+//      round robin, so any 32 consecutive ones hold 32 banks while every bank
+//      still has postings;
+//   2. that order is laid out over the positions of the segment in the order
+//      the scan's add instructions visit them (see kVecMin), so each
+//      instruction takes 32 consecutive ones.
+// Any order of a segment gives the same scores up to FP32 rounding; this one
+// only changes which bank each add of an instruction meets.
+// scratch: uint32[P]; (sdoc, sval) in, (odoc, oval) out.
+constexpr int kOrderWarps = 8;
+__global__ void __launch_bounds__(kOrderWarps * 32) bank_order_kernel(const uint32_t* seg, int64_t S,
+                                                                     const uint32_t* sdoc, const uint32_t* sval,
+                                                                     uint32_t lambda, uint32_t* scratch,
+                                                                     uint32_t* odoc, uint32_t* oval) {
+    __shared__ uint32_t cnt[kOrderWarps][32];
+    __shared__ uint32_t rnk[kOrderWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t warps = (int64_t)gridDim.x * kOrderWarps;
+    for (int64_t sg = (int64_t)blockIdx.x * kOrderWarps + warp; sg < S; sg += warps) {
+        const uint32_t s = seg[sg], e = seg[sg + 1], L = e - s;
+        if (L <= 32) {
+            // one add instruction takes the whole segment: nothing to gain
+            if (lane < (int)L) {
+                odoc[s + lane] = sdoc[s + lane];
+                oval[s + lane] = sval[s + lane];
+            }
+            continue;
+        }
+        cnt[warp][lane] = 0;
+        rnk[warp][lane] = 0;
+        __syncwarp();
+        for (uint32_t i = lane; i < L; i += 32) atomicAdd(&cnt[warp][(sdoc[s + i] % lambda) & 31u], 1u);
+        __syncwarp();
+        for (uint32_t i0 = 0; i0 < L; i0 += 32) {
+            // rank = earlier postings of the same bank, in segment order (deterministic)
+            const uint32_t i = i0 + (uint32_t)lane;
+            const bool ok = i < L;
+            const uint32_t b = ok ? (sdoc[s + i] % lambda) & 31u : 32u + (uint32_t)lane;
+            const unsigned peers = __match_any_sync(kFull, b);
+            const uint32_t r = ok ? rnk[warp][b] + (uint32_t)__popc(peers & lt) : 0u;
+            __syncwarp();
+            if (ok && (peers & lt) == 0) rnk[warp][b] += (uint32_t)__popc(peers);
+            __syncwarp();
+            if (ok) {
+                // position of (r, b) in the (rank, bank) order
+                uint32_t q = 0;
+                for (uint32_t bb = 0; bb < 32; bb++) {
+                    const uint32_t c = cnt[warp][bb];
+                    q += c < r ? c : r;
+                    q += (bb < b && c > r) ? 1u : 0u;
+                }
+                scratch[s + q] = s + i;
+            }
+        }
+        __syncwarp();
+        // the positions in the order the scan's add instructions take them
+        uint32_t run = 0;
+        if (L >= kVecMin) {
+            const uint32_t g0 = s & ~7u, e8 = (e + 7u) & ~7u;
+            for (uint32_t base = g0; base < e8; base += (uint32_t)kChunkLen) {
+                for (int u = 0; u < kChunkU; u++) {
+                    const uint32_t p = base + 8u * (uint32_t)lane + (uint32_t)u;
+                    const bool ok = p >= s && p < e;
+                    const unsigned bal = __ballot_sync(kFull, ok);
+                    if (ok) {
+                        const uint32_t src = scratch[s + run + (uint32_t)__popc(bal & lt)];
+                        odoc[p] = sdoc[src];
+                        oval[p] = sval[src];
+                    }
+                    run += (uint32_t)__popc(bal);
+                }
+            }
+        } else {
+            for (uint32_t u = 0; u * 32 < L; u++) {
+                const uint32_t p = s + 32u * u + (uint32_t)lane;
+                const bool ok = p < e;
+                const unsigned bal = __ballot_sync(kFull, ok);
+                if (ok) {
+                    const uint32_t src = scratch[s + run + (uint32_t)__popc(bal & lt)];
+                    odoc[p] = sdoc[src];
+                    oval[p] = sval[src];
+                }
+                run += (uint32_t)__popc(bal);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void fill_u32_kernel(float* p, int64_t n, float v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
@@ -499,6 +594,18 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
         SINDI_CUDA(cudaGetLastError());
     }
     if (Pn > 0) {
+        // bank-aware order inside every segment (the scan's scatter-add)
+        uint32_t* scratch = P.alloc<uint32_t>(Pn);
+        uint32_t* odoc = P.alloc<uint32_t>(Pn);
+        uint32_t* oval = P.alloc<uint32_t>(Pn);
+        bank_order_kernel<<<grid_for(S, kOrderWarps, 152 * 16), kOrderWarps * 32, 0, stream>>>(
+            ix.seg, S, sdoc, sval, lambda, scratch, odoc, oval);
+        SINDI_CUDA(cudaGetLastError());
+        P.free(scratch);
+        P.free(sdoc);
+        P.free(sval);
+        sdoc = odoc;
+        sval = oval;
         if (ix.dtype == SINDI_F32)
             pack_kernel<SINDI_F32><<<grid_for(Pn, 256), 256, 0, stream>>>(sdim, sdoc, sval, Pn, lambda, ix.scale,
                                                                           ix.pid, ix.pval);

@@ -118,6 +118,15 @@ struct CudaError {
 
 inline uint32_t ceil_div_u32(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
 
+// How the window scan reads a list segment I_{j,w}, which the build's posting
+// order follows: a warp chunk is 256 postings of one segment; a segment of at
+// least kVecMin postings is tiled on 8-aligned groups (lane l of a chunk owns
+// the l-th group of 8, one posting per add instruction u = 0..7); a shorter
+// segment is one chunk whose lane l owns postings s + l + 32u.
+constexpr int kChunkU = 8;                 // postings per lane in one warp chunk
+constexpr int kChunkLen = 32 * kChunkU;    // postings of one warp chunk (one list only)
+constexpr uint32_t kVecMin = 128;          // segments this long are read with vector loads
+
 // sindi_search_params.block_threads: 0 (default), SINDI_SCAN_PIPELINED, 256, 512 or 1024.
 inline bool valid_block_threads(uint32_t b) {
     return b == 0 || b == SINDI_SCAN_PIPELINED || b == 256 || b == 512 || b == 1024;

@@ -46,9 +46,6 @@ constexpr uint32_t kSplitMinWindows = 8;   // plain schedule: a query of this ma
 constexpr uint32_t kSplitFraction = 8;     // its first 1/kSplitFraction windows first
 constexpr int kMaxScanWarps = 1024 / 32;   // largest scan block
 constexpr int kChunkTable = 2048;          // chunks mapped to their list by a table (then a search)
-constexpr int kChunkU = 8;                 // postings per lane in one warp chunk
-constexpr int kChunkLen = 32 * kChunkU;    // postings of one warp chunk (one list only)
-constexpr uint32_t kVecMin = 128;          // lists this long are read with vector loads
 constexpr int kHistBits = 12;
 constexpr int kHistBins = 1 << kHistBits;  // bins on the top 12 bits of a score key
 constexpr int kKeyBinShift = 64 - kHistBits;

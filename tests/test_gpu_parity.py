@@ -50,6 +50,15 @@ def test_exact_10k_top10_equals_brute_force(exact10k, mode):
         check_ranked(ids[r], sc[r], oi, os_, w.k, D.n, what=f"query {r}")
 
 
+def _in_id_order(seg, ids, vals):
+    """The device orders each list segment I_{j,w} for its scatter-add (shared-memory banks); the oracle keeps
+    ascending document ids. Put every device segment in id order (ids are unique within a segment)."""
+    seg = np.asarray(seg, np.int64)
+    which = np.repeat(np.arange(len(seg) - 1), np.diff(seg))
+    order = np.lexsort((np.asarray(ids, np.int64), which))
+    return np.asarray(ids)[order], np.asarray(vals)[order]
+
+
 def _dequant(vals, dtype, scale, seg, sigma, dim):
     if dtype == "f32":
         return vals.astype(np.float64)
@@ -84,10 +93,11 @@ def test_device_index_equals_oracle_lists(window, alpha, dtype):
     assert ex["info"]["n_windows"] == I.sigma and ex["info"]["postings"] == I.postings
     np.testing.assert_array_equal(ex["seg"].astype(np.int64), seg)
     np.testing.assert_array_equal(ex["kept"].astype(np.int64), kept)
-    np.testing.assert_array_equal(ex["ids"].astype(np.int64), pid % window)
+    ids, vals = _in_id_order(ex["seg"], ex["ids"], ex["vals"])
+    np.testing.assert_array_equal(ids.astype(np.int64), pid % window)
     if dtype == "f8":
         np.testing.assert_array_equal(ex["scale"], scale)
-    got = _dequant(ex["vals"], dtype, ex["scale"], ex["seg"], I.sigma, 97)
+    got = _dequant(vals, dtype, ex["scale"], ex["seg"], I.sigma, 97)
     np.testing.assert_array_equal(got, pval)
 
 
@@ -113,10 +123,11 @@ def test_device_index_other_pruning_methods_equal_oracle_lists(prune, prune_n, a
     assert ex["info"]["postings"] == I.postings
     np.testing.assert_array_equal(ex["seg"].astype(np.int64), seg)
     np.testing.assert_array_equal(ex["kept"].astype(np.int64), kept)
-    np.testing.assert_array_equal(ex["ids"].astype(np.int64), pid % 256)
+    ids, vals = _in_id_order(ex["seg"], ex["ids"], ex["vals"])
+    np.testing.assert_array_equal(ids.astype(np.int64), pid % 256)
     if dtype == "f8":
         np.testing.assert_array_equal(ex["scale"], scale)
-    np.testing.assert_array_equal(_dequant(ex["vals"], dtype, ex["scale"], ex["seg"], I.sigma, 97), pval)
+    np.testing.assert_array_equal(_dequant(vals, dtype, ex["scale"], ex["seg"], I.sigma, 97), pval)
 
 
 @pytest.mark.parametrize("prune,prune_n,alpha", [("vector_number", 12, 1.0), ("list", 2000, 1.0),
@@ -141,6 +152,36 @@ def test_invalid_pruning_parameters():
     for prune, n in (("vector_number", 0), ("list", 0), ("mass_list", 0)):
         with pytest.raises(sindi.SindiError, match="INVALID_ARG"):
             sindi.Index(dev(ip), dev(ix), dev(v), 16, window=64, prune=prune, prune_n=n)
+
+
+def test_segment_order_spreads_banks():
+    """Each list segment is a permutation of its ids, laid out so that the 32 postings of one add instruction
+    of the scan mostly sit in different shared-memory banks (slot mod 32)."""
+    ip, ix, v = datagen.random_csr(60_000, 50, 30.0, seed=81, zipf_s=0.3)
+    D = oracle.Dataset(ip, ix, v, 50)
+    I = oracle.Index(D, window=8192, alpha=1.0)
+    seg, pid, pval, _, _ = I.export()
+    with sindi.Index(dev(ip), dev(ix), dev(v), 50, window=8192) as idx:
+        ex = idx.export()
+    ids, _ = _in_id_order(ex["seg"], ex["ids"], ex["vals"])
+    np.testing.assert_array_equal(ids.astype(np.int64), pid % 8192)
+
+    def worst_bank_load(order):
+        loads = []
+        for k in range(len(seg) - 1):
+            s_, e_ = int(seg[k]), int(seg[k + 1])
+            if e_ - s_ < 128:
+                continue
+            g0 = s_ & ~7
+            for base in range(g0, (e_ + 7) & ~7, 256):
+                for u in range(8):
+                    b = [int(order[p]) % 32 for p in range(base + u, base + u + 256, 8) if s_ <= p < e_]
+                    if len(b) == 32:
+                        loads.append(np.bincount(b, minlength=32).max())
+        return np.mean(loads)
+
+    before, after = worst_bank_load(pid % 8192), worst_bank_load(ex["ids"].astype(np.int64))
+    assert after < 0.6 * before, (before, after)
 
 
 def test_device_index_host_and_device_inputs_agree():
