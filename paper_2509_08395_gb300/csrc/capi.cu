@@ -94,9 +94,16 @@ static void free_index_memory(IndexImpl& ix, cudaStream_t s) {
     ix.scale = nullptr;
     ix.kept = nullptr;
     ix.err = nullptr;
-    std::lock_guard<std::mutex> lk(ix.lane_mu);
-    for (cudaStream_t l : ix.lanes) (void)cudaStreamDestroy(l);
-    ix.lanes.clear();
+    {
+        std::lock_guard<std::mutex> lk(ix.lane_mu);
+        for (cudaStream_t l : ix.lanes) (void)cudaStreamDestroy(l);
+        ix.lanes.clear();
+    }
+    std::lock_guard<std::mutex> lk(ix.graph_mu);
+    if (ix.graph_exec) (void)cudaGraphExecDestroy(ix.graph_exec);
+    if (ix.graph_ws) (void)cudaFree(ix.graph_ws);
+    ix.graph_exec = nullptr;
+    ix.graph_ws = nullptr;
 }
 
 static std::string query_error_text(uint32_t e) {

@@ -1488,6 +1488,106 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
     *chained = true;
 }
 
+// The plain schedule's launches: query i's chain on lane i mod lanes. Every
+// lane starts after the work already on `stream` (fork event) and `stream`
+// continues after every lane (join events). The events go to `evs`; the
+// caller destroys them once they are recorded (or once a capture ends).
+static void enqueue_plain_lanes(const IndexImpl& ix, const Plan& pl, const std::vector<Workspace>& wss,
+                                const int64_t* q_indptr, const int32_t* q_indices, const float* q_values,
+                                int64_t n_queries, uint32_t k, uint32_t* out_ids, float* out_scores,
+                                cudaStream_t stream, const std::vector<cudaStream_t>& ls, const QueryCsr* pruned,
+                                std::vector<cudaEvent_t>& evs) {
+    const int lanes = (int)ls.size();
+    cudaEvent_t fork = nullptr;
+    SINDI_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    evs.push_back(fork);
+    SINDI_CUDA(cudaEventRecord(fork, stream));
+    for (cudaStream_t l : ls) SINDI_CUDA(cudaStreamWaitEvent(l, fork, 0));
+    std::vector<char> lane_chained(lanes, 0);
+    for (int64_t q = 0; q < n_queries; q++) {
+        const int l = (int)(q % lanes);
+        bool c = lane_chained[l] != 0;
+        launch_group(ix, pl, wss[l], q_indptr, q_indices, q_values, q, 1, false, k, out_ids, out_scores, ls[l], &c,
+                     nullptr, nullptr, pruned);
+        lane_chained[l] = c ? 1 : 0;
+    }
+    for (cudaStream_t l : ls) {
+        cudaEvent_t join = nullptr;
+        SINDI_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        evs.push_back(join);
+        SINDI_CUDA(cudaEventRecord(join, l));
+        SINDI_CUDA(cudaStreamWaitEvent(stream, join, 0));
+    }
+}
+
+// Records the plain schedule of one call as a CUDA graph with workspaces of
+// its own, on streams of its own (so no other search's streams are ever in
+// capture). Replaces the index's previous graph. Caller holds ix.graph_mu.
+static void capture_plain_graph(const IndexImpl& ix, const Plan& pl, const IndexImpl::PlainCall& call, int lanes,
+                                const int64_t* q_indptr, const int32_t* q_indices, const float* q_values,
+                                int64_t n_queries, uint32_t k, uint32_t* out_ids, float* out_scores) {
+    configure_search_kernels(ix.device);  // attributes cannot be set during a capture
+    if (ix.graph_exec) {
+        SINDI_CUDA(cudaDeviceSynchronize());  // the old graph may still run
+        SINDI_CUDA(cudaGraphExecDestroy(ix.graph_exec));
+        ix.graph_exec = nullptr;
+    }
+    if (ix.graph_ws) {
+        SINDI_CUDA(cudaFree(ix.graph_ws));
+        ix.graph_ws = nullptr;
+    }
+    const size_t ws_one = workspace_bytes(1, pl.cand_cap, pl.fcap, pl.top_cap);
+    const size_t ws_stride = (ws_one + 255) & ~(size_t)255;
+    unsigned char* mem = nullptr;
+    SINDI_CUDA(cudaMalloc(&mem, ws_stride * lanes));
+    ix.graph_ws = mem;
+    std::vector<Workspace> wss;
+    for (int l = 0; l < lanes; l++) wss.push_back(carve_workspace(mem + ws_stride * l, 1, pl.cand_cap, pl.fcap, pl.top_cap));
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> ls(lanes, nullptr);
+    std::vector<cudaEvent_t> evs;
+    cudaGraph_t graph = nullptr;
+    const uint64_t l0 = ix.launches.load(), s0 = ix.scan_launches.load();
+    bool capturing = false;
+    try {
+        SINDI_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        for (auto& l : ls) SINDI_CUDA(cudaStreamCreateWithFlags(&l, cudaStreamNonBlocking));
+        SINDI_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
+        for (int l = 0; l < lanes; l++)
+            SINDI_CUDA(cudaMemsetAsync(mem + ws_stride * l, 0, workspace_counter_bytes(1), cap));
+        enqueue_plain_lanes(ix, pl, wss, q_indptr, q_indices, q_values, n_queries, k, out_ids, out_scores, cap, ls,
+                            nullptr, evs);
+        capturing = false;
+        SINDI_CUDA(cudaStreamEndCapture(cap, &graph));
+        SINDI_CUDA(cudaGraphInstantiate(&ix.graph_exec, graph, 0));
+    } catch (...) {
+        if (capturing) {
+            cudaGraph_t g = nullptr;
+            (void)cudaStreamEndCapture(cap, &g);
+            if (g) (void)cudaGraphDestroy(g);
+        }
+        if (graph) (void)cudaGraphDestroy(graph);
+        for (cudaEvent_t e : evs) (void)cudaEventDestroy(e);
+        for (cudaStream_t l : ls)
+            if (l) (void)cudaStreamDestroy(l);
+        if (cap) (void)cudaStreamDestroy(cap);
+        ix.launches = l0;
+        ix.scan_launches = s0;
+        throw;
+    }
+    SINDI_CUDA(cudaGraphDestroy(graph));
+    for (cudaEvent_t e : evs) SINDI_CUDA(cudaEventDestroy(e));
+    for (cudaStream_t l : ls) SINDI_CUDA(cudaStreamDestroy(l));
+    SINDI_CUDA(cudaStreamDestroy(cap));
+    // the launches the capture counted happen at every graph launch instead
+    ix.graph_launches = ix.launches.load() - l0;
+    ix.graph_scan_launches = ix.scan_launches.load() - s0;
+    ix.launches = l0;
+    ix.scan_launches = s0;
+    ix.graph_call = call;
+}
+
 sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
                          const float* q_values, int64_t n_queries, const sindi_search_params& prm,
                          uint32_t* out_ids, float* out_scores, cudaStream_t stream) {
@@ -1515,6 +1615,43 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
     // with its own workspace; query i takes lane i mod lanes. Timed runs keep
     // one lane, so that a scan's measured duration is its own.
     const int lanes = (batched || timing) ? 1 : (int)std::min<int64_t>(kPlainLanes, n_queries);
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    SINDI_CUDA(cudaStreamIsCapturing(stream, &cst));
+    if (lanes > 1 && prm.beta >= 1.0 && cst == cudaStreamCaptureStatusNone) {
+        // A plain call is thousands of launches, which the host issues about as
+        // fast as the GPU runs them. The second identical call (same buffers,
+        // size and parameters) records them as a graph; identical calls after
+        // it launch the graph.
+        IndexImpl::PlainCall call;
+        call.buf[0] = q_indptr;
+        call.buf[1] = q_indices;
+        call.buf[2] = q_values;
+        call.buf[3] = out_ids;
+        call.buf[4] = out_scores;
+        call.n = n_queries;
+        call.k = k;
+        call.gamma = prm.gamma;
+        call.block = prm.block_threads;
+        std::lock_guard<std::mutex> lk(ix.graph_mu);
+        bool failed = false;
+        if (!(ix.graph_exec && ix.graph_call == call) && ix.graph_seen == call) {
+            try {
+                capture_plain_graph(ix, pl, call, lanes, q_indptr, q_indices, q_values, n_queries, k, out_ids,
+                                    out_scores);
+            } catch (const CudaError&) {
+                (void)cudaGetLastError();
+                failed = true;  // launch directly, and do not try this call again
+            }
+        }
+        if (ix.graph_exec && ix.graph_call == call) {
+            SINDI_CUDA(cudaGraphLaunch(ix.graph_exec, stream));
+            ix.launches += ix.graph_launches;
+            ix.scan_launches += ix.graph_scan_launches;
+            ix.queries += (uint64_t)n_queries;
+            return SINDI_OK;
+        }
+        ix.graph_seen = failed ? IndexImpl::PlainCall{} : call;
+    }
     Pool P{ix.pool, stream};
     const size_t ws_one = workspace_bytes(chunk, pl.cand_cap, pl.fcap, pl.top_cap);
     const size_t ws_stride = (ws_one + 255) & ~(size_t)255;
@@ -1566,8 +1703,6 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
     std::vector<cudaEvent_t> evs;
     bool chained = false;
     if (lanes > 1) {
-        // fork: every lane starts after the work already on `stream` (queries,
-        // the zeroed workspaces); join: `stream` continues after every lane
         std::vector<cudaStream_t> ls;
         {
             std::lock_guard<std::mutex> lk(ix.lane_mu);
@@ -1578,26 +1713,10 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
             }
             ls.assign(ix.lanes.begin(), ix.lanes.begin() + lanes);
         }
-        cudaEvent_t fork = nullptr;
-        SINDI_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        SINDI_CUDA(cudaEventRecord(fork, stream));
-        for (cudaStream_t l : ls) SINDI_CUDA(cudaStreamWaitEvent(l, fork, 0));
-        std::vector<char> lane_chained(lanes, 0);
-        for (int64_t q = 0; q < n_queries; q++) {
-            const int l = (int)(q % lanes);
-            bool c = lane_chained[l] != 0;
-            launch_group(ix, pl, wss[l], q_indptr, q_indices, q_values, q, 1, false, k, out_ids, out_scores, ls[l],
-                         &c, nullptr, nullptr, pruned.indptr ? &pruned : nullptr);
-            lane_chained[l] = c ? 1 : 0;
-        }
-        for (cudaStream_t l : ls) {
-            cudaEvent_t join = nullptr;
-            SINDI_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-            SINDI_CUDA(cudaEventRecord(join, l));
-            SINDI_CUDA(cudaStreamWaitEvent(stream, join, 0));
-            SINDI_CUDA(cudaEventDestroy(join));
-        }
-        SINDI_CUDA(cudaEventDestroy(fork));
+        std::vector<cudaEvent_t> evs_lane;
+        enqueue_plain_lanes(ix, pl, wss, q_indptr, q_indices, q_values, n_queries, k, out_ids, out_scores, stream, ls,
+                            pruned.indptr ? &pruned : nullptr, evs_lane);
+        for (cudaEvent_t e : evs_lane) SINDI_CUDA(cudaEventDestroy(e));
     }
     for (int64_t q0 = 0; lanes == 1 && q0 < n_queries; q0 += chunk) {
         const uint32_t nq = (uint32_t)std::min<int64_t>(chunk, n_queries - q0);

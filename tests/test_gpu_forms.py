@@ -94,6 +94,33 @@ def test_plain_chains_in_flight_match_one_query_calls(setup):
         _same(ids, sc, it, st, f"gamma {gamma} timed")
 
 
+def test_repeated_plain_calls_replay_a_graph(setup):
+    """The second identical plain call records its launches as a CUDA graph, later ones launch it: the
+    answers stay those of the direct launches, new query contents in the same buffers are honoured, and
+    the launch counters count every replay."""
+    w, idx, _, (qp, qx, qv) = setup
+    q = [_dev(qp), _dev(qx), _dev(qv)]
+    out = (torch.empty((len(qp) - 1, 50), dtype=torch.int32, device=DEV),
+           torch.empty((len(qp) - 1, 50), dtype=torch.float32, device=DEV))
+    runs = []
+    sindi.sindi_reset_stats(idx.handle)
+    for _ in range(4):
+        idx.search(*q, k=50, gamma=500, mode="plain", out=out)
+        torch.cuda.synchronize()
+        runs.append([t.cpu().numpy().copy() for t in out])
+    idx.check()
+    st = sindi.sindi_get_stats(idx.handle)
+    assert st["queries"] == 4 * (len(qp) - 1)
+    assert st["launches"] % 4 == 0 and st["launches"] >= 4 * 3 * (len(qp) - 1)
+    for r in runs[1:]:
+        _same(r[0], r[1], runs[0][0], runs[0][1], "replay")
+    q[2].mul_(0.5)  # new weights in the same buffers
+    idx.search(*q, k=50, gamma=500, mode="plain", out=out)
+    torch.cuda.synchronize()
+    fresh = [t.cpu().numpy() for t in idx.search(_dev(qp), _dev(qx), _dev(qv * 0.5), k=50, gamma=500, mode="plain")]
+    _same(out[0].cpu().numpy(), out[1].cpu().numpy(), fresh[0], fresh[1], "replay after new contents")
+
+
 def test_autotuner_meets_the_recall_target(setup, tmp_path):
     """The chosen (window, gamma, schedule, block) reaches Recall@50 >= 0.99 against the GPU exact search, and
     the same configuration holds against the FP64 oracle's brute force."""
