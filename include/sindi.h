@@ -160,9 +160,12 @@ typedef struct {
 /*
  * Build an index (Algorithm 3: alpha-mass every document, then Algorithm 1
  * over the pruned documents, with the lists split into windows as in
- * Sec. 3.3.1). Postings are sorted by (dim, document) on the device; inside
- * a list I_{j,w} they are in ascending document id, stored as the 16-bit
- * window-local id i mod lambda beside the value.
+ * Sec. 3.3.1). Postings are sorted by (dim, document) on the device and
+ * stored as the 16-bit window-local id i mod lambda beside the value; inside
+ * a list I_{j,w} they are ordered for the scan's shared-memory scatter-add
+ * (the postings one warp instruction adds sit in different banks), which
+ * changes scores only by FP32 rounding. With prune != MASS the other pruning
+ * methods of Sec. 4.1 apply (see sindi_prune).
  *   indptr/indices/values: the documents (CSR, see conventions), n_docs rows,
  *       n_docs < 2^32 - 1, dims in [0, dim).
  *   params: see sindi_build_params. NULL = window 0, FP32, alpha 1.
@@ -192,6 +195,13 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
  *       through device memory and returns when the results are in place.
  * Malformed queries (dim out of range, duplicate dim, non-finite value) set
  * the index's error word; they never read outside the index.
+ * Plain schedule: several queries' launch chains run at once on streams of
+ * the index (forked from and joined to `stream`). When the same call (same
+ * buffers, n_queries, k, gamma and block shape; beta = 1; timing off; stream
+ * not being captured) comes a second time, its launches are recorded as one
+ * CUDA graph with working memory of its own (held until the index is freed
+ * or another call is recorded); identical calls then launch the graph, which
+ * reads the buffers' current contents.
  */
 sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
                           const float* q_values, int64_t n_queries, const sindi_search_params* params,
