@@ -102,8 +102,10 @@ static void free_index_memory(IndexImpl& ix, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(ix.graph_mu);
     if (ix.graph_exec) (void)cudaGraphExecDestroy(ix.graph_exec);
     if (ix.graph_ws) (void)cudaFree(ix.graph_ws);
+    if (ix.graph_done) (void)cudaEventDestroy(ix.graph_done);
     ix.graph_exec = nullptr;
     ix.graph_ws = nullptr;
+    ix.graph_done = nullptr;
 }
 
 static std::string query_error_text(uint32_t e) {

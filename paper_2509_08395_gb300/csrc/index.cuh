@@ -56,6 +56,7 @@ struct IndexImpl {
     mutable PlainCall graph_call, graph_seen;
     mutable cudaGraphExec_t graph_exec = nullptr;
     mutable void* graph_ws = nullptr;     // the graph's own workspaces (cudaMalloc)
+    mutable cudaEvent_t graph_done = nullptr;  // recorded after every launch of the graph
     mutable uint64_t graph_launches = 0, graph_scan_launches = 0;
 
     // counters

@@ -40,7 +40,7 @@ namespace sindi {
 
 constexpr int kScanThreadsPlain = 512;     // two blocks per SM: the windows of concurrent queries interleave
 constexpr int kScanThreadsBatched = 512;   // many windows: two blocks per SM overlap their phases
-constexpr int kPlainLanes = 16;            // plain schedule: query chains in flight at once
+constexpr int kPlainLanes = 24;            // plain schedule: query chains in flight at once
 constexpr uint32_t kPlainPipeItems = 6;    // plain schedule, pipelined scan: windows per block
 constexpr uint32_t kSplitMinWindows = 8;   // plain schedule: a query of this many windows or more scans
 constexpr uint32_t kSplitFraction = 8;     // its first 1/kSplitFraction windows first
@@ -1528,10 +1528,11 @@ static void capture_plain_graph(const IndexImpl& ix, const Plan& pl, const Index
                                 int64_t n_queries, uint32_t k, uint32_t* out_ids, float* out_scores) {
     configure_search_kernels(ix.device);  // attributes cannot be set during a capture
     if (ix.graph_exec) {
-        SINDI_CUDA(cudaDeviceSynchronize());  // the old graph may still run
+        SINDI_CUDA(cudaEventSynchronize(ix.graph_done));  // its last launch (and its workspaces) is done
         SINDI_CUDA(cudaGraphExecDestroy(ix.graph_exec));
         ix.graph_exec = nullptr;
     }
+    if (!ix.graph_done) SINDI_CUDA(cudaEventCreateWithFlags(&ix.graph_done, cudaEventDisableTiming));
     if (ix.graph_ws) {
         SINDI_CUDA(cudaFree(ix.graph_ws));
         ix.graph_ws = nullptr;
@@ -1645,6 +1646,7 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
         }
         if (ix.graph_exec && ix.graph_call == call) {
             SINDI_CUDA(cudaGraphLaunch(ix.graph_exec, stream));
+            SINDI_CUDA(cudaEventRecord(ix.graph_done, stream));
             ix.launches += ix.graph_launches;
             ix.scan_launches += ix.graph_scan_launches;
             ix.queries += (uint64_t)n_queries;
