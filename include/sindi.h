@@ -323,6 +323,26 @@ sindi_status sindi_check(const sindi_index* index, void* stream);
 sindi_status sindi_index_info(const sindi_index* index, sindi_index_info_t* out);
 
 /*
+ * Write the index (parameters, lists and the unpruned documents) to the file
+ * `path`, in host byte order, so that sindi_index_load can rebuild it without
+ * a new build (checkpoint; the paper reports index sizes only, Sec. 5).
+ * Waits for the device. Returns SINDI_ERR_INVALID_ARG if the file cannot be
+ * written.
+ */
+sindi_status sindi_index_save(const sindi_index* index, const char* path);
+
+/*
+ * Read an index written by sindi_index_save onto the current device (working
+ * on `stream`; the call returns when the index is ready). Every offset and
+ * id the search kernels follow (list offsets, window ids < lambda, document
+ * offsets, dims < dim) is checked on its way in; a file that is not an index
+ * file of this version, is truncated or fails a check gives
+ * SINDI_ERR_INVALID_DATA and no index. `out` receives the new index (free
+ * with sindi_index_free).
+ */
+sindi_status sindi_index_load(const char* path, void* stream, sindi_index** out);
+
+/*
  * Copy the index layout to host buffers (for inspection and tests).
  *   seg:   uint32 [dim * n_windows + 1]; list I_{j,w} is postings
  *          seg[j * n_windows + w] .. seg[j * n_windows + w + 1] - 1.

@@ -19,6 +19,8 @@ from .sindi import (  # noqa: F401
     sindi_index_export,
     sindi_index_free,
     sindi_index_info,
+    sindi_index_load,
+    sindi_index_save,
     sindi_plan_create,
     sindi_plan_free,
     sindi_plan_launch,

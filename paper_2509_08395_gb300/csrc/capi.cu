@@ -3,7 +3,10 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
+#include <cstring>
+#include <vector>
 #include <map>
 #include <mutex>
 #include <new>
@@ -125,6 +128,73 @@ static sindi_status status_of_error_word(uint32_t e) {
     if (e & kErrTimeout) return SINDI_ERR_TIMEOUT;
     return SINDI_ERR_INVALID_DATA;
 }
+
+// ---------------------------------------------------------------------------
+// Index files (sindi_index_save / sindi_index_load): a fixed header, then the
+// device arrays in order, host byte order. Arrays move through one pinned
+// staging buffer in pieces, so an index larger than host memory still fits.
+// ---------------------------------------------------------------------------
+
+constexpr char kFileMagic[8] = {'S', 'I', 'N', 'D', 'I', 'G', 'B', '3'};
+constexpr uint32_t kFileVersion = 1;
+constexpr size_t kStageBytes = (size_t)64 << 20;
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    int64_t n_docs;
+    int32_t dim;
+    uint32_t lambda;
+    uint32_t sigma;
+    int32_t dtype;
+    double alpha;
+    int32_t prune;
+    uint32_t prune_n;
+    int64_t doc_nnz;
+    int64_t postings;
+};
+
+struct File {
+    FILE* f = nullptr;
+    ~File() {
+        if (f) std::fclose(f);
+    }
+};
+
+struct Pinned {
+    void* p = nullptr;
+    ~Pinned() {
+        if (p) (void)cudaFreeHost(p);
+    }
+};
+
+// Device -> file, through the staging buffer.
+static bool write_device(FILE* f, const void* dev, size_t bytes, void* stage) {
+    const unsigned char* d = static_cast<const unsigned char*>(dev);
+    for (size_t off = 0; off < bytes; off += kStageBytes) {
+        const size_t n = bytes - off < kStageBytes ? bytes - off : kStageBytes;
+        SINDI_CUDA(cudaMemcpy(stage, d + off, n, cudaMemcpyDeviceToHost));
+        if (std::fwrite(stage, 1, n, f) != n) return false;
+    }
+    return true;
+}
+
+// File -> device, through the staging buffer; `check` sees every piece on the
+// host first (element-aligned pieces) and may reject it.
+template <typename T, typename Check>
+static bool read_device(FILE* f, T* dev, size_t count, void* stage, const Check& check, cudaStream_t s) {
+    const size_t per = kStageBytes / sizeof(T);
+    for (size_t off = 0; off < count; off += per) {
+        const size_t n = count - off < per ? count - off : per;
+        if (std::fread(stage, sizeof(T), n, f) != n) return false;
+        if (!check(static_cast<const T*>(stage), off, n)) return false;
+        SINDI_CUDA(cudaMemcpyAsync(dev + off, stage, n * sizeof(T), cudaMemcpyHostToDevice, s));
+        SINDI_CUDA(cudaStreamSynchronize(s));
+    }
+    return true;
+}
+
 
 }  // namespace sindi
 
@@ -460,6 +530,192 @@ sindi_status sindi_index_export(const sindi_index* index, uint32_t* seg, uint16_
     } catch (const CudaError& e) {
         return from_cuda(e);
     }
+    return SINDI_OK;
+}
+
+
+sindi_status sindi_index_save(const sindi_index* index, const char* path) {
+    set_last_error("");
+    if (!index || !path) {
+        set_last_error("index and path must not be NULL");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    const IndexImpl& ix = index->impl;
+    DeviceGuard dg(ix.device);
+    File file;
+    file.f = std::fopen(path, "wb");
+    if (!file.f) {
+        set_last_error(std::string("cannot open ") + path + " for writing");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    FileHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kFileMagic, 8);
+    h.version = kFileVersion;
+    h.header_bytes = (uint32_t)sizeof(FileHeader);
+    h.n_docs = ix.n_docs;
+    h.dim = ix.dim;
+    h.lambda = ix.lambda;
+    h.sigma = ix.sigma;
+    h.dtype = ix.dtype;
+    h.alpha = ix.alpha;
+    h.prune = ix.prune;
+    h.prune_n = ix.prune_n;
+    h.doc_nnz = ix.doc_nnz;
+    h.postings = ix.postings;
+    try {
+        Pinned stage;
+        SINDI_CUDA(cudaMallocHost(&stage.p, kStageBytes));
+        SINDI_CUDA(cudaDeviceSynchronize());  // the index is complete before it is read
+        bool ok = std::fwrite(&h, sizeof(h), 1, file.f) == 1;
+        const size_t S = (size_t)ix.dim * ix.sigma + 1, P = (size_t)ix.postings;
+        ok = ok && write_device(file.f, ix.seg, 4 * S, stage.p);
+        ok = ok && write_device(file.f, ix.pid, 2 * P, stage.p);
+        ok = ok && write_device(file.f, ix.pval, ix.value_bytes() * P, stage.p);
+        ok = ok && write_device(file.f, ix.scale, 4 * (size_t)ix.dim, stage.p);
+        ok = ok && write_device(file.f, ix.kept, 4 * (size_t)ix.n_docs, stage.p);
+        ok = ok && write_device(file.f, ix.indptr, 8 * ((size_t)ix.n_docs + 1), stage.p);
+        ok = ok && write_device(file.f, ix.indices, 4 * (size_t)ix.doc_nnz, stage.p);
+        ok = ok && write_device(file.f, ix.values, 4 * (size_t)ix.doc_nnz, stage.p);
+        if (!ok || std::fflush(file.f) != 0) {
+            set_last_error(std::string("write to ") + path + " failed");
+            return SINDI_ERR_INVALID_ARG;
+        }
+    } catch (const CudaError& e) {
+        return from_cuda(e);
+    }
+    return SINDI_OK;
+}
+
+sindi_status sindi_index_load(const char* path, void* stream, sindi_index** out) {
+    set_last_error("");
+    if (!path || !out) {
+        set_last_error("path and out must not be NULL");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    File file;
+    file.f = std::fopen(path, "rb");
+    if (!file.f) {
+        set_last_error(std::string("cannot open ") + path);
+        return SINDI_ERR_INVALID_ARG;
+    }
+    FileHeader h;
+    if (std::fread(&h, sizeof(h), 1, file.f) != 1 || std::memcmp(h.magic, kFileMagic, 8) != 0 ||
+        h.version != kFileVersion || h.header_bytes != sizeof(FileHeader)) {
+        set_last_error(std::string(path) + " is not an index file of this version");
+        return SINDI_ERR_INVALID_DATA;
+    }
+    const uint64_t lam = h.lambda ? h.lambda : 1;
+    if (h.n_docs < 0 || h.n_docs >= (int64_t)0xFFFFFFFFLL || h.dim <= 0 || h.lambda == 0 ||
+        h.lambda > (uint32_t)kMaxWindow || (uint64_t)h.sigma != ((uint64_t)h.n_docs + lam - 1) / lam ||
+        h.dtype < SINDI_F32 || h.dtype > SINDI_F8E4M3 || h.prune < SINDI_PRUNE_MASS ||
+        h.prune > SINDI_PRUNE_MASS_LIST || h.doc_nnz < 0 || h.postings < 0 || h.postings > h.doc_nnz ||
+        !(h.alpha > 0.0 && h.alpha <= 1.0) || (uint64_t)h.dim * h.sigma >= (1ull << 34)) {
+        set_last_error(std::string(path) + ": inconsistent header");
+        return SINDI_ERR_INVALID_DATA;
+    }
+    const size_t vbytes = h.dtype == SINDI_F32 ? 4 : (h.dtype == SINDI_F16 ? 2 : 1);
+    const size_t S = (size_t)h.dim * h.sigma + 1, P = (size_t)h.postings;
+    const size_t want = sizeof(h) + 4 * S + (2 + vbytes) * P + 4 * (size_t)h.dim + 4 * (size_t)h.n_docs +
+                        8 * ((size_t)h.n_docs + 1) + 8 * (size_t)h.doc_nnz;
+    if (std::fseek(file.f, 0, SEEK_END) != 0 || (size_t)std::ftell(file.f) != want ||
+        std::fseek(file.f, (long)sizeof(h), SEEK_SET) != 0) {
+        set_last_error(std::string(path) + ": file size does not match its header");
+        return SINDI_ERR_INVALID_DATA;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        set_last_error("no CUDA device");
+        return SINDI_ERR_CUDA;
+    }
+    sindi_index* hnd = new (std::nothrow) sindi_index;
+    if (!hnd) return SINDI_ERR_OOM;
+    IndexImpl& ix = hnd->impl;
+    try {
+        ix.device = dev;
+        ix.pool = library_pool(dev);
+        ix.n_docs = h.n_docs;
+        ix.dim = h.dim;
+        ix.lambda = h.lambda;
+        ix.sigma = h.sigma;
+        ix.dtype = h.dtype;
+        ix.alpha = h.alpha;
+        ix.prune = h.prune;
+        ix.prune_n = h.prune_n;
+        ix.doc_nnz = h.doc_nnz;
+        ix.postings = h.postings;
+        Pool Pl{ix.pool, s};
+        ix.err = Pl.alloc<uint32_t>(1);
+        SINDI_CUDA(cudaMemsetAsync(ix.err, 0, 4, s));
+        const size_t Pp = (P + 7) & ~(size_t)7;  // the scan reads aligned groups of 8
+        ix.seg = Pl.alloc<uint32_t>(S);
+        ix.pid = Pl.alloc<uint16_t>(Pp);
+        ix.pval = Pl.alloc<uint8_t>(Pp * vbytes);
+        ix.scale = Pl.alloc<float>(h.dim);
+        ix.kept = Pl.alloc<uint32_t>(h.n_docs > 0 ? h.n_docs : 1);
+        ix.indptr = Pl.alloc<int64_t>(h.n_docs + 1);
+        ix.indices = Pl.alloc<int32_t>(h.doc_nnz > 0 ? h.doc_nnz : 1);
+        ix.values = Pl.alloc<float>(h.doc_nnz > 0 ? h.doc_nnz : 1);
+        if (Pp > P) {
+            SINDI_CUDA(cudaMemsetAsync(ix.pid + P, 0, 2 * (Pp - P), s));
+            SINDI_CUDA(cudaMemsetAsync(static_cast<uint8_t*>(ix.pval) + P * vbytes, 0, (Pp - P) * vbytes, s));
+        }
+        Pinned stage;
+        SINDI_CUDA(cudaMallocHost(&stage.p, kStageBytes));
+        // every offset the kernels follow is checked on the host on its way in
+        uint32_t seg_prev = 0;
+        int64_t ip_prev = 0;
+        const uint32_t lambda = h.lambda;
+        const int32_t dim = h.dim;
+        auto any = [](const void*, size_t, size_t) { return true; };
+        bool ok = read_device(file.f, ix.seg, S, stage.p, [&](const uint32_t* v, size_t off, size_t n) {
+            for (size_t t = 0; t < n; t++) {
+                if ((off + t == 0 && v[t] != 0) || v[t] < seg_prev) return false;
+                seg_prev = v[t];
+            }
+            return off + n < S || (uint64_t)seg_prev == (uint64_t)P;
+        }, s);
+        ok = ok && read_device(file.f, ix.pid, P, stage.p, [&](const uint16_t* v, size_t, size_t n) {
+            for (size_t t = 0; t < n; t++)
+                if (v[t] >= lambda) return false;
+            return true;
+        }, s);
+        ok = ok && read_device(file.f, static_cast<uint8_t*>(ix.pval), P * vbytes, stage.p,
+                               [&](const uint8_t* v, size_t o, size_t n) { return any(v, o, n); }, s);
+        ok = ok && read_device(file.f, ix.scale, (size_t)h.dim, stage.p,
+                               [&](const float* v, size_t o, size_t n) { return any(v, o, n); }, s);
+        ok = ok && read_device(file.f, ix.kept, (size_t)h.n_docs, stage.p,
+                               [&](const uint32_t* v, size_t o, size_t n) { return any(v, o, n); }, s);
+        ok = ok && read_device(file.f, ix.indptr, (size_t)h.n_docs + 1, stage.p,
+                               [&](const int64_t* v, size_t off, size_t n) {
+            for (size_t t = 0; t < n; t++) {
+                if ((off + t == 0 && v[t] != 0) || v[t] < ip_prev) return false;
+                ip_prev = v[t];
+            }
+            return off + n < (size_t)h.n_docs + 1 || ip_prev == h.doc_nnz;
+        }, s);
+        ok = ok && read_device(file.f, ix.indices, (size_t)h.doc_nnz, stage.p, [&](const int32_t* v, size_t, size_t n) {
+            for (size_t t = 0; t < n; t++)
+                if (v[t] < 0 || v[t] >= dim) return false;
+            return true;
+        }, s);
+        ok = ok && read_device(file.f, ix.values, (size_t)h.doc_nnz, stage.p,
+                               [&](const float* v, size_t o, size_t n) { return any(v, o, n); }, s);
+        if (!ok) {
+            free_index_memory(ix, s);
+            delete hnd;
+            set_last_error(std::string(path) + ": truncated, or an offset or id out of range");
+            return SINDI_ERR_INVALID_DATA;
+        }
+        SINDI_CUDA(cudaStreamSynchronize(s));
+    } catch (const CudaError& e) {
+        sindi_status st = from_cuda(e);
+        free_index_memory(ix, s);
+        delete hnd;
+        return st;
+    }
+    *out = hnd;
     return SINDI_OK;
 }
 

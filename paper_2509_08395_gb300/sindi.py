@@ -89,6 +89,8 @@ _SIGS = {
     "sindi_index_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_index_info_t)]),
     "sindi_index_export": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "sindi_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "sindi_index_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "sindi_index_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "sindi_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_stats_t)]),
     "sindi_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "sindi_index_free": (None, [ctypes.c_void_p]),
@@ -226,6 +228,18 @@ def sindi_index_export(index: int) -> dict:
             "info": info}
 
 
+def sindi_index_save(index: int, path: str) -> None:
+    _check(load().sindi_index_save(ctypes.c_void_p(index), os.fsencode(path)), "sindi_index_save")
+
+
+def sindi_index_load(path: str, stream=None) -> int:
+    """Rebuild an index written by sindi_index_save; returns the handle."""
+    out = ctypes.c_void_p()
+    s = stream if stream is not None else 0
+    _check(load().sindi_index_load(os.fsencode(path), ctypes.c_void_p(int(s)), ctypes.byref(out)), "sindi_index_load")
+    return out.value
+
+
 def sindi_set_timing(index: int, enable: bool) -> None:
     _check(load().sindi_set_timing(ctypes.c_void_p(index), 1 if enable else 0), "sindi_set_timing")
 
@@ -275,6 +289,18 @@ class Index:
         sindi_search(self.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma, beta, mode, stream,
                      block)
         return out
+
+    def save(self, path: str) -> None:
+        """Write the index to `path` (sindi_index_save)."""
+        sindi_index_save(self.handle, path)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Index":
+        """An index read back from `path` (sindi_index_load)."""
+        obj = cls.__new__(cls)
+        obj.handle = sindi_index_load(path, stream)
+        obj.info = sindi_index_info(obj.handle)
+        return obj
 
     def check(self, stream=None):
         sindi_check(self.handle, stream)

@@ -57,3 +57,32 @@ def test_calls_without_device_fail_cleanly(lib):
         sindi.SINDI_ERR_INVALID_ARG
     assert b"NULL" in L.sindi_last_error()
     assert L.sindi_version().startswith(b"sindi-gb300")
+
+
+def test_index_load_rejects_files_that_are_not_index_files(lib, tmp_path):
+    """The header is checked before any device work: foreign, truncated or inconsistent files are
+    SINDI_ERR_INVALID_DATA, a missing file INVALID_ARG."""
+    from paper_2509_08395_gb300 import sindi
+
+    L = sindi.load()
+    out = ctypes.c_void_p()
+    junk = tmp_path / "junk.bin"
+    junk.write_bytes(b"not an index" * 10)
+    assert L.sindi_index_load(str(junk).encode(), None, ctypes.byref(out)) == sindi.SINDI_ERR_INVALID_DATA
+    assert out.value is None
+    # the right magic and version, a header whose sizes disagree (sigma != ceil(n_docs / lambda))
+    import struct
+    hdr = struct.pack("<8sIIqiIIidiIqq", b"SINDIGB3", 1, 72, 100, 8, 64, 7, 0, 1.0, 0, 0, 10, 10)
+    assert len(hdr) == 72
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(hdr)
+    assert L.sindi_index_load(str(bad).encode(), None, ctypes.byref(out)) == sindi.SINDI_ERR_INVALID_DATA
+    assert b"header" in L.sindi_last_error()
+    # a consistent header over a truncated body
+    hdr = struct.pack("<8sIIqiIIidiIqq", b"SINDIGB3", 1, 72, 100, 8, 64, 2, 0, 1.0, 0, 0, 10, 10)
+    short = tmp_path / "short.bin"
+    short.write_bytes(hdr + b"\0" * 16)
+    assert L.sindi_index_load(str(short).encode(), None, ctypes.byref(out)) == sindi.SINDI_ERR_INVALID_DATA
+    assert b"size" in L.sindi_last_error()
+    assert L.sindi_index_load(str(tmp_path / "missing.bin").encode(), None, ctypes.byref(out)) == \
+        sindi.SINDI_ERR_INVALID_ARG

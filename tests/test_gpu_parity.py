@@ -147,6 +147,34 @@ def test_other_pruning_methods_search_parity(pruned_small, prune, prune_n, alpha
         check_reranked(rids[r], rsc[r], D, Q, r, I, 20, 300, what=f"{prune} rerank query {r}")
 
 
+def test_index_save_load_roundtrip(tmp_path, pruned_small):
+    """An index written by sindi_index_save and read back by sindi_index_load has the same layout and answers
+    like the original; a file with a window id >= lambda is refused."""
+    w, (ip, ix, v), (qp, qx, qv), D, Q = pruned_small
+    path = str(tmp_path / "index.sindi")
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=4096, alpha=0.5, value_dtype="f16", prune="mass_list",
+                     prune_n=3000) as idx:
+        idx.save(path)
+        ex = idx.export()
+        info = idx.info
+    with sindi.Index.load(path) as idx2:
+        assert idx2.info == info
+        ex2 = idx2.export()
+        for key in ("seg", "ids", "vals", "scale", "kept"):
+            np.testing.assert_array_equal(ex2[key], ex[key])
+        ids, sc = run_search(idx2, qp, qx, qv, k=20, gamma=300, mode="batched")
+    I = oracle.Index(D, window=4096, alpha=0.5, dtype="f16", prune="mass_list", prune_n=3000)
+    for r in range(Q.n):
+        check_reranked(ids[r], sc[r], D, Q, r, I, 20, 300, what=f"loaded index, query {r}")
+    raw = bytearray(open(path, "rb").read())
+    at = 72 + 4 * (w.dim * info["n_windows"] + 1)  # the first window id
+    raw[at:at + 2] = (4096).to_bytes(2, "little")
+    bad = str(tmp_path / "bad.sindi")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(sindi.SindiError, match="INVALID_DATA"):
+        sindi.Index.load(bad)
+
+
 def test_invalid_pruning_parameters():
     ip, ix, v = datagen.random_csr(50, 16, 4.0, seed=3)
     for prune, n in (("vector_number", 0), ("list", 0), ("mass_list", 0)):
