@@ -1,0 +1,62 @@
+"""Host-side logic that needs no GPU: workload generators, autotuner window candidates, bench accounting."""
+import hashlib
+import os
+
+import numpy as np
+
+import datagen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_uniform_sparsity_workloads():
+    """Sec. 5's sparsity sweep stand-in: 120 entries per row, dims unique and uniform over [0, d), values
+    uniform in (0, 1]."""
+    for d in (10, 30, 100):
+        w = datagen.WORKLOADS[f"uniform-1m-d{d}k"].scaled(n_docs=3000, n_queries=20)
+        ip, ix, v = datagen.docs(w)
+        assert np.all(np.diff(ip) == 120)
+        assert ix.min() >= 0 and ix.max() < w.dim
+        for i in range(0, 3000, 97):
+            row = ix[ip[i]:ip[i + 1]]
+            assert len(np.unique(row)) == 120
+        assert v.min() > 0 and v.max() <= 1
+        # dims spread over the whole range (uniform, not Zipf): every decile gets about a tenth
+        counts = np.histogram(ix, bins=10, range=(0, w.dim))[0]
+        assert counts.min() > 0.8 * counts.mean()
+
+
+def test_autotuner_window_candidates():
+    from paper_2509_08395_gb300 import autotune
+
+    for n_docs in (5_000, 1_000_000, 8_800_000):
+        ws = autotune.default_windows(n_docs, 152)
+        assert ws and all(256 <= w <= 32768 and w % 32 == 0 for w in ws)
+        assert ws == sorted(set(ws))
+
+
+def test_bench_postings_accounting():
+    """bench.postings_touched sums |I_j| over a query's terms (all windows) from the offsets table."""
+    import bench
+
+    dim, sigma = 5, 3
+    lens = np.arange(dim * sigma, dtype=np.int64) % 4  # |I_{j,w}|
+    seg = np.zeros(dim * sigma + 1, np.int64)
+    np.cumsum(lens, out=seg[1:])
+    qp = np.array([0, 2, 5], np.int64)
+    qx = np.array([0, 3, 1, 2, 4], np.int32)
+    got = bench.postings_touched(seg, sigma, dim, qp, qx)
+    per_dim = lens.reshape(dim, sigma).sum(axis=1)
+    assert got.tolist() == [per_dim[0] + per_dim[3], per_dim[1] + per_dim[2] + per_dim[4]]
+
+
+def test_bench_traffic_only_for_the_profiled_source():
+    import bench
+
+    assert bench.profile_traffic("0" * 64) is None
+    h = hashlib.sha256()
+    for f in ("search.cu", "primitives.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2509_08395_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    t = bench.profile_traffic(h.hexdigest())
+    assert t is None or t > 0
