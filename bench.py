@@ -349,6 +349,33 @@ def cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, budget_s, gpu_ids=None, k=None):
         done += 1
         elapsed = time.perf_counter() - t0
     qps = done / elapsed if elapsed > 0 else 0.0
+    # the same oracle on every host core: one query per thread at a time (the oracle's C search holds no
+    # shared state and ctypes releases the GIL during it), on the next queries, for about half the budget
+    import concurrent.futures
+    import threading
+
+    cores = os.cpu_count() or 1
+    lock = threading.Lock()
+    nxt = [done % max(1, Q.n)]
+    stop_at = time.perf_counter() + budget_s / 2
+
+    def worker(_):
+        n = 0
+        while n == 0 or time.perf_counter() < stop_at:
+            with lock:
+                r = nxt[0] % Q.n  # the queries in turn, from where the single-thread pass stopped
+                nxt[0] += 1
+            I.search(Q, r, k=w.k, gamma=w.gamma)
+            n += 1
+        return n
+
+    t_all = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=cores) as ex:
+        n_all = sum(ex.map(worker, range(cores)))
+    el_all = time.perf_counter() - t_all
+    all_cores = {"value": n_all / el_all if el_all > 0 else 0.0, "unit": "queries/s", "cores": cores,
+                 "kind": "oracle", "sample": f"{n_all} queries of {w.name} on {cores} threads, one query per thread "
+                                             f"at a time (about {el_all:.0f} s)"}
     recalls = []
     if gpu_ids is not None:
         # FP64 exact ground truth on an evenly spread sample of the same queries
@@ -359,7 +386,7 @@ def cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, budget_s, gpu_ids=None, k=None):
             recalls.append(oracle.recall(gpu_ids[r], truth))
             if time.perf_counter() - t1 > budget_s:
                 break
-    return qps, done, recalls
+    return qps, done, recalls, all_cores
 
 
 def run_reference(args):
@@ -626,7 +653,8 @@ def main():
     recall = None
     score_error = None
     if rank == 0:
-        qps_cpu, n_cpu, recalls = cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, args.cpu_seconds, gpu_ids, w.k)
+        qps_cpu, n_cpu, recalls, cpu_all = cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, args.cpu_seconds, gpu_ids,
+                                                             w.k)
         if main_dtype != "f32":
             # score error of the reduced-precision main index against FP64 (coarse and final)
             import oracle
@@ -724,6 +752,7 @@ def main():
                                       "peak_from": "measured: FP32 shared-memory atomicAdd probe at random slots "
                                                    "of a window-sized array, every SM full (libsindi_probe)"}},
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "clocks": clocks,
         "forms": forms,
         "pruning_ablation": ablation,
