@@ -276,10 +276,16 @@ def sparsity_sweep(sindi, torch, dev, steps, flush, stream):
 
 
 def source_sha():
+    """sha256 of the scan's sources without their comments and blank lines (a comment edit does not change
+    the kernel an ncu capture measured)."""
     h = hashlib.sha256()
     for f in ("search.cu", "primitives.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2509_08395_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2509_08395_gb300", "csrc", f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
     return h.hexdigest()
 
 
