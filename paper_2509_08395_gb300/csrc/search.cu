@@ -9,18 +9,21 @@
 //       the bin that holds its g-th best slot (the window's share of the heap
 //       update of Alg. 2). When ties crowd that bin, an exact radix select
 //       emits exactly the best g. Each block adds the histogram of what it
-//       emitted to a per-query histogram; in batched schedules it first reads
-//       that histogram, and a bin reached by g already emitted slots bounds
-//       what can still enter the answer.
-//   merge        (a few blocks per query): from the per-query histogram, the
-//       bin of the global g-th best candidate; candidates below it are
-//       dropped, the rest (about g) gathered; the last block of the query
-//       selects the exact best g in shared memory (the heap H of Alg. 2
-//       across windows). With gamma = 0 these are the sorted results;
-//       otherwise they are the gamma reorder candidates.
-//   rerank       (one warp per candidate): delta(x_i, q) from the unpruned
-//       document and the unpruned query (Alg. 4, the reorder loop); the last
-//       block of a query sorts the scores and writes the top k.
+//       emitted to a per-query histogram H. Where earlier windows of the query
+//       are complete (batched schedules: a snapshot taken at the block's
+//       start; the plain schedule's second launch: H read after the
+//       accumulation), a bin reached by g already emitted slots bounds what
+//       can still enter the answer, and a window whose slots above that bound
+//       fit its budget emits them in one pass, with no cut.
+//   merge        (one block per query up to 16384 candidates, a few above):
+//       from H, the bin of the global g-th best candidate; candidates below
+//       it are dropped, the rest (about g) gathered and the exact best g
+//       selected in shared memory (the heap H of Alg. 2 across windows).
+//       With gamma = 0 these are the sorted results; otherwise they are the
+//       gamma reorder candidates.
+//   rerank       (one half-warp per candidate): delta(x_i, q) from the
+//       unpruned document and the unpruned query (Alg. 4, the reorder loop);
+//       the last block of a query sorts the scores and writes the top k.
 //
 // Order keys (common.cuh) make every comparison exact: (score desc, id asc).
 #include <cuda_fp16.h>
