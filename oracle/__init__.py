@@ -29,23 +29,30 @@ _DTYPES = {"f32": F32, "f16": F16, "f8": E4M3, "e4m3": E4M3}
 _i64p = ctypes.c_void_p
 
 
+def compile_library(src: str, out: str) -> None:
+    """gcc with no FMA contraction and no fast-math: every FP64 operation rounds as written."""
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", src, "-o", out, "-lm"])
+
+
 def build(force: bool = False) -> str:
-    """Compile oracle.c (gcc, no FMA contraction, no fast-math)."""
+    """Compile oracle.c into liboracle.so beside it (when missing or older than the source)."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                                   "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+            compile_library(_SRC, tmp)
             os.replace(tmp, _LIB)
     return _LIB
 
 
 def _load():
+    """Load liboracle.so, or the library ORACLE_LIBRARY names: another build of
+    an oracle.c (the mutation tests load copies with planted mistakes)."""
     global _lib
     if _lib is not None:
         return _lib
-    build()
-    L = ctypes.CDLL(_LIB)
+    path = os.environ.get("ORACLE_LIBRARY") or build()
+    L = ctypes.CDLL(path)
     vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     L.orc_dataset_create.argtypes = [vp, vp, vp, i64, i32, ctypes.POINTER(ctypes.c_int)]
     L.orc_dataset_create.restype = vp

@@ -160,6 +160,21 @@ def test_alpha_mass_brute_force_subsets():
     assert checked > 250
 
 
+def test_alpha_one_keeps_entries_below_fp64_resolution():
+    """alpha = 1: with every entry non-zero, no proper prefix reaches the whole mass in exact arithmetic, so
+    r = nnz, also when the tail lies below the FP64 resolution of the mass (an FP64 prefix sum would
+    reach the mass after the first entry)."""
+    dims = [0, 3, 7]
+    vals = np.array([1.0, 2.0 ** -60, 2.0 ** -70], np.float32)
+    mags = [Fraction(float(x)) for x in vals]
+    assert sum(mags[:2], Fraction(0)) < sum(mags, Fraction(0))
+    assert 1.0 + 2.0 ** -60 + 2.0 ** -70 == 1.0             # the FP64 sum loses the tail
+    assert sorted(int(p) for p in oracle.alpha_mass(dims, vals, 1.0)) == [0, 1, 2]
+    D = oracle.Dataset(np.array([0, 3], np.int64), np.array(dims, np.int32), vals, 8)
+    _, kept = _entries(oracle.Index(D, window=4, alpha=1.0))
+    assert kept.tolist() == [3]
+
+
 # --------------------------------------------------------------------------
 # Definition 2 / 3 against library routines and hand-computed values
 # --------------------------------------------------------------------------
@@ -311,7 +326,7 @@ def test_vector_number_pruning_invariants():
     dim stays); vn >= every nnz leaves the unpruned index."""
     ip, ix, v = datagen.random_csr(400, 60, 10.0, seed=41)
     v = np.round(v * 4) / 4 + 0.25  # coarse values: many equal |x| within a row
-    v = v.astype(np.float32)
+    v = np.where(np.arange(len(v)) % 3 == 1, -v, v).astype(np.float32)   # |x| ranks, not x
     D = oracle.Dataset(ip, ix, v, 60)
     rows = _doc_rows(ip, ix, v)
     full, _ = _entries(oracle.Index(D, window=32, alpha=1.0))
@@ -332,7 +347,8 @@ def test_list_pruning_invariants():
     lower doc stays); the kept counts per document add up; l' >= every list length leaves the unpruned
     index; alpha-mass followed by list pruning is list pruning of the alpha-mass lists."""
     ip, ix, v = datagen.random_csr(500, 30, 9.0, seed=43)
-    v = (np.round(v * 4) / 4 + 0.25).astype(np.float32)
+    v = np.round(v * 4) / 4 + 0.25
+    v = np.where(np.arange(len(v)) % 3 == 1, -v, v).astype(np.float32)   # |x| ranks, not x
     D = oracle.Dataset(ip, ix, v, 30)
     full, _ = _entries(oracle.Index(D, window=64, alpha=1.0))
     mass, _ = _entries(oracle.Index(D, window=64, alpha=0.6))
