@@ -107,3 +107,50 @@ def check_reranked(gids, gsc, D, Q, r, I, k, gamma, tol=REL_TOL, what="", beta=1
                        set(int(x) for x in cids[:g])), key=lambda t: (-t[0], t[1]))
         check_ranked(gids, gsc, np.array([c for _, c in full]), np.array([s for s, _ in full]), k, D.n, tol, what)
     return touched
+
+
+U32 = 2.0 ** -24   # unit roundoff of FP32
+
+
+def fp32_sum_bound(a, m):
+    """Largest error of an FP32 evaluation of a sum of at most m products, in any order and with each
+    product rounded at most twice: gamma_{m+1} * a, where a = sum of |products| (exact) and
+    gamma_n = n u / (1 - n u) (the dot-product bound of Higham, Accuracy and Stability of Numerical
+    Algorithms, 2nd ed., Sec. 3.1). A small FP64 allowance covers the rounding of the exact side."""
+    g = (m + 1) * U32 / (1 - (m + 1) * U32)
+    return g * np.asarray(a, np.float64) * (1 + 1e-9) + 1e-300
+
+
+def check_ranked_conditioned(gids, gsc, s, a, m, k, what=""):
+    """GPU top-k over signed data against the exact FP64 scores s[i] of every document i.
+
+    With signed values a score can cancel to near zero, so no relative tolerance holds. Each document gets
+    its own bound b[i] = fp32_sum_bound(a[i], m), a[i] = sum of |q_j x_j| over its products. The GPU's
+    scores must be within b of the exact ones and non-increasing, its ids distinct, and no document it
+    left out may certainly beat one it returned: max over the rest of (s - b) <= min over the answer of
+    (s + b)."""
+    s = np.asarray(s, np.float64)
+    b = fp32_sum_bound(a, m)
+    n = min(k, len(s))
+    gids = np.asarray(gids).astype(np.int64)[:n] & 0xFFFFFFFF
+    gsc = np.asarray(gsc, np.float64)[:n]
+    assert np.all(gids < len(s)), f"{what}: id out of range"
+    assert len(set(gids.tolist())) == n, f"{what}: duplicate ids"
+    err = np.abs(gsc - s[gids])
+    bad = np.nonzero(err > b[gids])[0]
+    assert len(bad) == 0, (f"{what}: rank {bad[0]} id {gids[bad[0]]}: gpu {gsc[bad[0]]!r} exact "
+                           f"{s[gids[bad[0]]]!r} bound {b[gids[bad[0]]]!r}")
+    assert np.all(np.diff(gsc) <= 0), f"{what}: scores not in descending order"
+    rest = np.ones(len(s), bool)
+    rest[gids] = False
+    if rest.any():
+        hi_out = np.max((s - b)[rest])
+        lo_in = np.min((s + b)[gids])
+        assert hi_out <= lo_in, f"{what}: a left-out document ({hi_out!r}) certainly beats a returned one ({lo_in!r})"
+
+
+def signed_copy(values, every=3):
+    """The same values with every `every`-th one negated (signed test data; no method arithmetic)."""
+    v = np.array(values, np.float32, copy=True)
+    v[1::every] = -v[1::every]
+    return v

@@ -4,7 +4,7 @@ import pytest
 
 import datagen
 import oracle
-from parity import REL_TOL, check_ranked, check_reranked
+from parity import REL_TOL, check_ranked, check_ranked_conditioned, check_reranked, signed_copy
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -128,6 +128,56 @@ def test_device_index_other_pruning_methods_equal_oracle_lists(prune, prune_n, a
     if dtype == "f8":
         np.testing.assert_array_equal(ex["scale"], scale)
     np.testing.assert_array_equal(_dequant(vals, dtype, ex["scale"], ex["seg"], I.sigma, 97), pval)
+
+
+@pytest.mark.parametrize("prune,prune_n,alpha,dtype", [("mass", 0, 0.5, "f32"), ("mass", 0, 0.7, "f8"),
+                                                       ("vector_number", 5, 1.0, "f16"), ("list", 3, 1.0, "f8"),
+                                                       ("mass_list", 25, 0.5, "f32")])
+def test_device_index_signed_values_equal_oracle_lists(prune, prune_n, alpha, dtype):
+    """Signed values: every pruning method ranks entries by |x| (Sec. 4.1), the FP8 list scale is max |x| / 448
+    and the codecs keep the sign; the device lists equal the oracle's bit for bit, ties in |x| between
+    opposite signs included."""
+    ip, ix, v = datagen.random_csr(3000, 97, 14.0, seed=61, zipf_s=1.05, val_sigma=1.2)
+    v = signed_copy(np.round(v * 8) / 8 + 0.125, 3)
+    D = oracle.Dataset(ip, ix, v, 97)
+    I = oracle.Index(D, window=256, alpha=alpha, dtype=dtype, prune=prune, prune_n=prune_n)
+    seg, pid, pval, scale, kept = I.export()
+    assert np.any(pval < 0)
+    with sindi.Index(dev(ip), dev(ix), dev(v), 97, window=256, alpha=alpha, value_dtype=dtype, prune=prune,
+                     prune_n=prune_n) as idx:
+        ex = idx.export()
+    assert ex["info"]["postings"] == I.postings
+    np.testing.assert_array_equal(ex["seg"].astype(np.int64), seg)
+    np.testing.assert_array_equal(ex["kept"].astype(np.int64), kept)
+    ids, vals = _in_id_order(ex["seg"], ex["ids"], ex["vals"])
+    np.testing.assert_array_equal(ids.astype(np.int64), pid % 256)
+    if dtype == "f8":
+        np.testing.assert_array_equal(ex["scale"], scale)
+    np.testing.assert_array_equal(_dequant(vals, dtype, ex["scale"], ex["seg"], I.sigma, 97), pval)
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_signed_values_coarse_parity(mode):
+    """Signed documents and queries, so scores cancel: the FP32 coarse top-k against the oracle's exact FP64
+    score of every document, each within the FP32 dot-product bound of its sum of |q_j x_j|."""
+    w = datagen.WORKLOADS["pruned-1m"].scaled(n_docs=40_000, n_queries=24)
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    v, qv = signed_copy(v, 3), signed_copy(qv, 5)
+    D, Q = oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+    Da, Qa = oracle.Dataset(ip, ix, np.abs(v), w.dim), oracle.Dataset(qp, qx, np.abs(qv), w.dim)
+    I = oracle.Index(D, window=4096, alpha=0.5)
+    Ia = oracle.Index(Da, window=4096, alpha=0.5)   # alpha-mass ranks |x|: the same kept entries
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=4096, alpha=0.5) as idx:
+        assert idx.info["postings"] == I.postings
+        ids, sc = run_search(idx, qp, qx, qv, k=100, gamma=0, mode=mode)
+    for r in range(Q.n):
+        s, a = np.empty(D.n), np.empty(D.n)
+        oi, os_ = I.search(Q, r, k=D.n, gamma=0)
+        s[oi] = os_
+        oi, os_ = Ia.search(Qa, r, k=D.n, gamma=0)
+        a[oi] = os_
+        check_ranked_conditioned(ids[r], sc[r], s, a, int(qp[r + 1] - qp[r]), 100, what=f"query {r}")
 
 
 @pytest.mark.parametrize("prune,prune_n,alpha", [("vector_number", 12, 1.0), ("list", 2000, 1.0),

@@ -1,0 +1,93 @@
+"""The comparison rules of tests/parity.py, checked on the CPU against an FP32 emulation of the scan.
+
+The GPU tests trust these rules, so they are tested here first. Each rule must accept every correct FP32
+evaluation, whatever the order of its additions. It must also reject a planted error: an id swapped for a
+worse one, a score off by more than its bound, or a repeated id.
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from parity import check_ranked_conditioned, fp32_sum_bound, signed_copy
+
+
+def _fp32_scan(seg, pid, pval, sigma, n, qd, qv, rng):
+    """Score every document in FP32 from the lists, one term after another in a random order (each
+    addition rounded to FP32, as the shared-memory scatter-add does)."""
+    A = np.zeros(n, np.float32)
+    for t in rng.permutation(len(qd)):
+        j = int(qd[t])
+        lo, hi = seg[j * sigma], seg[(j + 1) * sigma]
+        prod = np.float32(qv[t]) * pval[lo:hi].astype(np.float32)   # FP32 product, rounded once
+        A[pid[lo:hi]] += prod                                         # ids unique within I_j
+    return A
+
+
+@pytest.fixture(scope="module")
+def signed_case():
+    w = datagen.WORKLOADS["pruned-1m"].scaled(n_docs=3000, n_queries=8)
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    v, qv = signed_copy(v, 3), signed_copy(qv, 5)
+    D, Q = oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+    Da = oracle.Dataset(ip, ix, np.abs(v), w.dim)
+    Qa = oracle.Dataset(qp, qx, np.abs(qv), w.dim)
+    I = oracle.Index(D, window=1024, alpha=0.5)
+    Ia = oracle.Index(Da, window=1024, alpha=0.5)     # alpha-mass ranks |x|: the same kept entries
+    return w, (qp, qx, qv), D, Q, I, Qa, Ia
+
+
+def _exact(I, Q, r, n):
+    ids, sc = I.search(Q, r, k=n, gamma=0)
+    s = np.empty(n)
+    s[ids] = sc
+    return s
+
+
+def test_conditioned_rule_accepts_fp32_and_rejects_planted_errors(signed_case):
+    w, (qp, qx, qv), D, Q, I, Qa, Ia = signed_case
+    seg, pid, pval, _, _ = I.export()
+    k, n = 50, D.n
+    rng = np.random.default_rng(11)
+    cancelled = 0
+    for r in range(Q.n):
+        s, a = _exact(I, Q, r, n), _exact(Ia, Qa, r, n)
+        assert np.all(np.abs(s) <= a * (1 + 1e-12))
+        cancelled += int(np.sum((a > 0) & (np.abs(s) < 0.5 * a)))
+        m = int(qp[r + 1] - qp[r])
+        qd, qvv = qx[qp[r]:qp[r + 1]], qv[qp[r]:qp[r + 1]]
+        for _ in range(3):                                            # three orders of the additions
+            A = _fp32_scan(seg, pid, pval, I.sigma, n, qd, qvv, rng)
+            order = np.lexsort((np.arange(n), -A.astype(np.float64)))
+            gids, gsc = order[:k], A[order[:k]]
+            check_ranked_conditioned(gids, gsc, s, a, m, k, what=f"query {r}")
+        # planted: the k-th id replaced by a much worse document (its own score keeps the order)
+        bad_ids, bad_sc = gids.copy(), gsc.astype(np.float64).copy()
+        bad_ids[-1], bad_sc[-1] = order[k + 300], A[order[k + 300]]
+        with pytest.raises(AssertionError):
+            check_ranked_conditioned(bad_ids, bad_sc, s, a, m, k)
+        # planted: the best score off by 1e-3 of its value (far above the bound)
+        bad_sc = gsc.astype(np.float64).copy()
+        bad_sc[0] *= 1 + 1e-3
+        with pytest.raises(AssertionError):
+            check_ranked_conditioned(gids, bad_sc, s, a, m, k)
+        # planted: a repeated id
+        bad_ids = gids.copy()
+        bad_ids[1] = bad_ids[0]
+        with pytest.raises(AssertionError):
+            check_ranked_conditioned(bad_ids, gsc, s, a, m, k)
+    assert cancelled > 100          # the data really has cancelling scores
+
+
+def test_fp32_bound_is_tight_enough_to_order_documents(signed_case):
+    """The per-document bound stays near m * 2^-24 of the absolute sum, far below the score gaps that decide
+    the top-k (so the rule still pins the ids)."""
+    w, (qp, qx, qv), D, Q, I, Qa, Ia = signed_case
+    s, a = _exact(I, Q, 0, D.n), _exact(Ia, Qa, 0, D.n)
+    m = int(qp[1] - qp[0])
+    b = fp32_sum_bound(a, m)
+    assert np.all(b <= (m + 2) * 2.0 ** -24 * a + 1e-300)
+    top = np.sort(s)[::-1][:60]
+    gaps = -np.diff(top)
+    assert np.median(gaps) > 100 * np.max(b[np.argsort(-s)[:60]])
