@@ -152,14 +152,32 @@ def _ptr(a, dtype):
     return a.data_ptr()
 
 
+def _numel(a) -> int:
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _require(a, n: int, what: str):
+    """The C calls get bare pointers and cannot see buffer sizes: check them here, before the call."""
+    if a is not None and _numel(a) < n:
+        raise ValueError(f"{what} holds {_numel(a)} elements, the call needs {n}")
+
+
 def _stream(stream, *tensors):
+    """A raw cudaStream_t: the given one (an int or a torch.cuda.Stream), else the current stream of the first
+    device tensor, else None (the legacy default stream)."""
     if stream is not None:
-        return stream
+        return getattr(stream, "cuda_stream", stream)
     for t in tensors:
         if t is not None and not isinstance(t, np.ndarray) and t.is_cuda:
             import torch
             return torch.cuda.current_stream(t.device).cuda_stream
     return None
+
+
+def _require_search(q_indptr, out_ids, out_scores, n_queries: int, k: int):
+    _require(q_indptr, int(n_queries) + 1, "q_indptr")
+    _require(out_ids, int(n_queries) * int(k), "out_ids")
+    _require(out_scores, int(n_queries) * int(k), "out_scores")
 
 
 # ---- the C entry points, same names -------------------------------------------------
@@ -169,6 +187,7 @@ def sindi_build(indptr, indices, values, n_docs: int, dim: int, window: int = 0,
     lib = load()
     prm = sindi_build_params(window=int(window), value_dtype=DTYPES[value_dtype], alpha=float(alpha),
                              prune=PRUNES[prune], prune_n=int(prune_n))
+    _require(indptr, int(n_docs) + 1, "indptr")
     out = ctypes.c_void_p()
     st = lib.sindi_build(_ptr(indptr, np.int64), _ptr(indices, np.int32), _ptr(values, np.float32), int(n_docs),
                          int(dim), ctypes.byref(prm), _stream(stream, indptr), ctypes.byref(out))
@@ -181,6 +200,7 @@ def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_
     """Algorithm 4 for every query row; writes out_ids (uint32/int32) and out_scores (float32), [n_queries, k]."""
     lib = load()
     prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block))
+    _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     st = lib.sindi_search(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                           _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm), _ptr(out_ids, np.uint32),
                           _ptr(out_scores, np.float32), _stream(stream, q_indptr, out_ids))
@@ -194,6 +214,7 @@ def sindi_search_noalloc(index: int, q_indptr, q_indices, q_values, n_queries: i
     static 8 MiB device array. Device tensors only; calls that overlap on the GPU race on that array."""
     lib = load()
     prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block))
+    _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     st = lib.sindi_search_noalloc(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                                   _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm),
                                   _ptr(out_ids, np.uint32), _ptr(out_scores, np.float32),
@@ -202,7 +223,7 @@ def sindi_search_noalloc(index: int, q_indptr, q_indices, q_values, n_queries: i
 
 
 def sindi_check(index: int, stream=None) -> None:
-    _check(load().sindi_check(ctypes.c_void_p(index), stream), "sindi_check")
+    _check(load().sindi_check(ctypes.c_void_p(index), _stream(stream)), "sindi_check")
 
 
 def sindi_index_info(index: int) -> dict:
@@ -235,8 +256,9 @@ def sindi_index_save(index: int, path: str) -> None:
 def sindi_index_load(path: str, stream=None) -> int:
     """Rebuild an index written by sindi_index_save; returns the handle."""
     out = ctypes.c_void_p()
-    s = stream if stream is not None else 0
-    _check(load().sindi_index_load(os.fsencode(path), ctypes.c_void_p(int(s)), ctypes.byref(out)), "sindi_index_load")
+    s = _stream(stream)
+    _check(load().sindi_index_load(os.fsencode(path), ctypes.c_void_p(int(s or 0)), ctypes.byref(out)),
+           "sindi_index_load")
     return out.value
 
 
@@ -330,6 +352,7 @@ class Index:
 def sindi_plan_create(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
                       gamma: int = 0, beta: float = 1.0, block: int = 0) -> int:
     prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=SINDI_MODE_BATCHED, block_threads=int(block))
+    _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     out = ctypes.c_void_p()
     _check(load().sindi_plan_create(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                                     _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm),
@@ -342,6 +365,7 @@ def sindi_plan_launch(plan: int, stream=None) -> None:
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
+    stream = _stream(stream)
     _check(load().sindi_plan_launch(ctypes.c_void_p(plan), stream), "sindi_plan_launch")
 
 

@@ -86,3 +86,27 @@ def test_index_load_rejects_files_that_are_not_index_files(lib, tmp_path):
     assert b"size" in L.sindi_last_error()
     assert L.sindi_index_load(str(tmp_path / "missing.bin").encode(), None, ctypes.byref(out)) == \
         sindi.SINDI_ERR_INVALID_ARG
+
+
+def test_binding_checks_buffer_sizes_before_the_call(lib):
+    """The C calls get bare pointers; the binding refuses undersized buffers before calling them, and takes
+    a stream as a raw handle or as an object with a cuda_stream attribute."""
+    import numpy as np
+    import pytest
+    from paper_2509_08395_gb300 import sindi
+
+    qp, qx, qv = np.array([0, 1, 2], np.int64), np.array([1, 2], np.int32), np.ones(2, np.float32)
+    ids, sc = np.empty((2, 10), np.uint32), np.empty((2, 10), np.float32)
+    with pytest.raises(ValueError, match="out_ids"):
+        sindi.sindi_search(1, qp, qx, qv, 2, ids[:1], sc, k=10)
+    with pytest.raises(ValueError, match="out_scores"):
+        sindi.sindi_search_noalloc(1, qp, qx, qv, 2, ids, sc[:, :5].copy(), k=10)
+    with pytest.raises(ValueError, match="q_indptr"):
+        sindi.sindi_search(1, qp, qx, qv, 3, np.empty((3, 10), np.uint32), np.empty((3, 10), np.float32), k=10)
+    with pytest.raises(ValueError, match="indptr"):
+        sindi.sindi_build(np.zeros(3, np.int64), qx, qv, 5, 4)
+
+    class FakeStream:
+        cuda_stream = 1234
+
+    assert sindi._stream(FakeStream()) == 1234 and sindi._stream(77) == 77 and sindi._stream(None, qp) is None
