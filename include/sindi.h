@@ -175,7 +175,7 @@ typedef struct {
  * Returns SINDI_ERR_INVALID_DATA for a malformed CSR (decreasing indptr, dim
  * out of range, duplicate dim in a row, non-finite value) and
  * SINDI_ERR_UNSUPPORTED for a row with more than 16384 entries or more than
- * 2^32 - 1 kept entries in total.
+ * 2^32 - 4096 kept entries in total.
  */
 sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const float* values,
                          int64_t n_docs, int32_t dim, const sindi_build_params* params,

@@ -486,9 +486,9 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     int64_t* kept_off = P.alloc<int64_t>(n + 1);
     exclusive_scan<uint32_t, int64_t>(kept, kept_off, n, P);
     const int64_t Pn0 = read_i64(kept_off + n, stream);
-    if (Pn0 >= (int64_t)0xFFFFFFFFLL) {
+    if (Pn0 > kMaxPostings) {
         P.free(kdim); P.free(kval); P.free(kept_off);
-        set_last_error("more than 2^32 - 1 kept entries");
+        set_last_error("more than 2^32 - 4096 kept entries");
         return SINDI_ERR_UNSUPPORTED;
     }
     int64_t Pn = Pn0;

@@ -609,7 +609,7 @@ sindi_status sindi_index_load(const char* path, void* stream, sindi_index** out)
     if (h.n_docs < 0 || h.n_docs >= (int64_t)0xFFFFFFFFLL || h.dim <= 0 || h.lambda == 0 ||
         h.lambda > (uint32_t)kMaxWindow || (uint64_t)h.sigma != ((uint64_t)h.n_docs + lam - 1) / lam ||
         h.dtype < SINDI_F32 || h.dtype > SINDI_F8E4M3 || h.prune < SINDI_PRUNE_MASS ||
-        h.prune > SINDI_PRUNE_MASS_LIST || h.doc_nnz < 0 || h.postings < 0 || h.postings > h.doc_nnz ||
+        h.prune > SINDI_PRUNE_MASS_LIST || h.doc_nnz < 0 || h.postings < 0 || h.postings > h.doc_nnz || h.postings > kMaxPostings ||
         !(h.alpha > 0.0 && h.alpha <= 1.0) || (uint64_t)h.dim * h.sigma >= (1ull << 34)) {
         set_last_error(std::string(path) + ": inconsistent header");
         return SINDI_ERR_INVALID_DATA;

@@ -9,6 +9,11 @@
 
 namespace sindi {
 
+// Kept entries an index may hold. Posting positions are uint32 in the scan,
+// which rounds segment ends up to groups of 8 and chunks of 256; the margin
+// keeps every such position below 2^32.
+constexpr int64_t kMaxPostings = 0xFFFFFFFFLL - 4096;
+
 struct IndexImpl {
     int device = 0;
     int64_t n_docs = 0;

@@ -78,6 +78,11 @@ def test_index_load_rejects_files_that_are_not_index_files(lib, tmp_path):
     bad.write_bytes(hdr)
     assert L.sindi_index_load(str(bad).encode(), None, ctypes.byref(out)) == sindi.SINDI_ERR_INVALID_DATA
     assert b"header" in L.sindi_last_error()
+    # a consistent header that claims more postings than uint32 scan positions can address
+    big = struct.pack("<8sIIqiIIidiIqq", b"SINDIGB3", 1, 72, 100, 8, 64, 2, 0, 1.0, 0, 0, 1 << 33, 1 << 32)
+    bad.write_bytes(big)
+    assert L.sindi_index_load(str(bad).encode(), None, ctypes.byref(out)) == sindi.SINDI_ERR_INVALID_DATA
+    assert b"inconsistent header" in L.sindi_last_error()
     # a consistent header over a truncated body
     hdr = struct.pack("<8sIIqiIIidiIqq", b"SINDIGB3", 1, 72, 100, 8, 64, 2, 0, 1.0, 0, 0, 10, 10)
     short = tmp_path / "short.bin"
