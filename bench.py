@@ -90,6 +90,20 @@ def barrier(ws):
         dist.barrier()
 
 
+def rank_queries(w, rank, ws):
+    """Weak scaling: the global query set holds the workload's queries once per rank, and every rank
+    searches its contiguous share as CSR (rank 0's share is the workload's own query set)."""
+    from paper_2509_08395_gb300.shard import shard_range
+
+    per_rank = w.queries.n_rows
+    gqp, gqx, gqv = datagen.queries(w.scaled(n_queries=per_rank * ws))
+    q_lo, q_hi = shard_range(per_rank * ws, rank, ws)
+    qp = gqp[q_lo: q_hi + 1] - gqp[q_lo]
+    qx = np.ascontiguousarray(gqx[gqp[q_lo]: gqp[q_hi]])
+    qv = np.ascontiguousarray(gqv[gqp[q_lo]: gqp[q_hi]])
+    return qp, qx, qv
+
+
 def max_over_ranks(x, ws):
     if ws == 1:
         return x
@@ -453,17 +467,8 @@ def main():
         w = w.scaled(window=args.window)
     if args.queries:
         w = w.scaled(n_queries=args.queries)
-    # weak scaling: the global query set holds the workload's queries once per rank, and every rank
-    # searches its contiguous share (rank 0's share is the workload's own query set)
-    from paper_2509_08395_gb300.shard import shard_range
-
-    per_rank = w.queries.n_rows
     ip, ix, v = datagen.docs(w)
-    gqp, gqx, gqv = datagen.queries(w.scaled(n_queries=per_rank * ws))
-    q_lo, q_hi = shard_range(per_rank * ws, rank, ws)
-    qp = gqp[q_lo: q_hi + 1] - gqp[q_lo]
-    qx = np.ascontiguousarray(gqx[gqp[q_lo]: gqp[q_hi]])
-    qv = np.ascontiguousarray(gqv[gqp[q_lo]: gqp[q_hi]])
+    qp, qx, qv = rank_queries(w, rank, ws)
     nq = len(qp) - 1
 
     t_b0 = time.perf_counter()

@@ -87,3 +87,41 @@ def test_document_shards_merge_to_the_global_topk(tmp_path):
         np.testing.assert_array_equal(out["sc"][r], b.astype(np.float32))
     qr = out["qranges"]
     assert qr[0][0] == 0 and qr[-1][1] == Q.n and qr[0][1] == qr[1][0]
+
+
+def _bench_worker(rank, world, port, result_path):
+    """bench.py's multi-rank pieces on gloo ranks: the query share of each rank, the barrier and the
+    max over ranks that the timed region's duration goes through."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    w = datagen.WORKLOADS["exact-10k"].scaled(n_queries=37)
+    qp, qx, qv = bench.rank_queries(w, rank, world)
+    bench.barrier(world)
+    slowest = bench.max_over_ranks(10.0 + rank, world)
+    np.savez(f"{result_path}.{rank}.npz", qp=qp, qx=qx, qv=qv, slowest=slowest)
+    bench.barrier(world)
+    dist.destroy_process_group()
+
+
+def test_bench_ranks_split_the_weak_scaling_query_set(tmp_path):
+    """Every rank searches its own share of the global query set (the workload's queries once per rank),
+    the shares together are that set in order, rank 0's share is the workload's own query set, and every
+    rank reports the slowest rank's time."""
+    world = 2
+    path = str(tmp_path / "bench")
+    mp.spawn(_bench_worker, args=(world, _free_port(), path), nprocs=world, join=True)
+    parts = [np.load(f"{path}.{r}.npz") for r in range(world)]
+    assert all(float(p["slowest"]) == 10.0 + world - 1 for p in parts)
+    w = datagen.WORKLOADS["exact-10k"].scaled(n_queries=37)
+    gqp, gqx, gqv = datagen.queries(w.scaled(n_queries=37 * world))
+    assert [len(p["qp"]) - 1 for p in parts] == [37] * world
+    np.testing.assert_array_equal(np.concatenate([p["qx"] for p in parts]), gqx)
+    np.testing.assert_array_equal(np.concatenate([p["qv"] for p in parts]), gqv)
+    starts = np.concatenate([[0], np.cumsum([len(p["qx"]) for p in parts])])
+    for r, p in enumerate(parts):
+        np.testing.assert_array_equal(p["qp"] + starts[r], gqp[37 * r: 37 * (r + 1) + 1])
+    own = datagen.queries(w)
+    for a, b in zip((parts[0]["qp"], parts[0]["qx"], parts[0]["qv"]), own):
+        np.testing.assert_array_equal(a, b)
