@@ -261,3 +261,16 @@ def recall(found, truth) -> float:
     if not truth:
         return 1.0
     return len(truth.intersection(int(f) for f in found)) / len(truth)
+
+
+def recall_tie_aware(found, truth, truth_scores, D: Dataset, Q: Dataset, r: int) -> float:
+    """Recall that also counts a returned document whose exact score delta (Definition 2) reaches the exact
+    k-th score of R* = truth (best-first, with its FP64 scores): documents tied with the k-th one are equally
+    correct answers, whichever of them the tie rule put into R*. Capped at 1."""
+    truth = [int(t) for t in truth]
+    if not truth:
+        return 1.0
+    tset, kth = set(truth), float(truth_scores[len(truth) - 1])
+    hits = sum(1 for f in dict.fromkeys(int(x) for x in found)
+               if 0 <= f < D.n and (f in tset or inner_product(D, f, Q, r) >= kth))
+    return min(hits, len(truth)) / len(truth)

@@ -60,3 +60,24 @@ def test_bench_traffic_only_for_the_profiled_source():
             h.update(fh.read())
     t = bench.profile_traffic(h.hexdigest())
     assert t is None or t > 0
+
+
+def test_cpu_oracle_sample_reports_recall_and_tie_aware_recall():
+    """bench.py's CPU leg: the oracle timed on a bounded sample, and both recalls of GPU-shaped answers
+    against FP64 brute force (exact answers score 1; answers taken from ranks k..2k-1 score below 1)."""
+    import bench
+    import oracle
+
+    w = datagen.WORKLOADS["exact-10k"].scaled(n_docs=2000, n_queries=30)
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    D, Q = oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+    top = [oracle.brute_force(D, Q, r, 2 * w.k)[0] for r in range(Q.n)]
+    exact = np.stack([t[: w.k] for t in top]).astype(np.uint32)
+    qps, done, recalls, all_cores, tie = bench.cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, 0.5, exact, w.k)
+    assert qps > 0 and done >= 1 and all_cores["cores"] >= 1 and all_cores["value"] > 0
+    assert recalls and len(tie) == len(recalls)
+    assert all(r == 1.0 for r in recalls) and all(t == 1.0 for t in tie)
+    worse = np.stack([t[w.k: 2 * w.k] for t in top]).astype(np.uint32)
+    _, _, recalls, _, tie = bench.cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, 0.2, worse, w.k)
+    assert np.mean(recalls) < 0.5 and all(t >= r for r, t in zip(recalls, tie))

@@ -544,3 +544,21 @@ def test_quantised_lists_store_dequantised_values():
 def test_recall_definition():
     assert oracle.recall([1, 2, 3], [3, 2, 9, 8]) == 0.5
     assert oracle.recall([], [1]) == 0.0
+
+
+def test_tie_aware_recall_hand_example():
+    """Docs 1 and 3 are the same vector, so they tie at the k-th score. R* (k = 2) takes doc 1, the lower id.
+    Returning doc 3 instead is a miss for plain recall and a hit for the tie-aware one. A doc below the k-th
+    score, a repeated id and an id outside the dataset count for nothing."""
+    ip, ix, v = _csr_from_dicts([{"0": 4.0}, {"0": 1.0, "1": 1.0}, {"1": 0.5}, {"0": 1.0, "1": 1.0}])
+    D = oracle.Dataset(ip, ix, v, 2)
+    qp, qx, qv = _csr_from_dicts([{"0": 1.0, "1": 1.0}])
+    Q = oracle.Dataset(qp, qx, qv, 2)
+    truth, ts = oracle.brute_force(D, Q, 0, 2)
+    assert truth.tolist() == [0, 1] and ts.tolist() == [4.0, 2.0]      # scores 4, 2, 0.5, 2
+    assert oracle.recall([0, 3], truth) == 0.5
+    assert oracle.recall_tie_aware([0, 3], truth, ts, D, Q, 0) == 1.0
+    assert oracle.recall_tie_aware([3, 2], truth, ts, D, Q, 0) == 0.5
+    assert oracle.recall_tie_aware([3, 3], truth, ts, D, Q, 0) == 0.5
+    assert oracle.recall_tie_aware([1, 3, 0], truth, ts, D, Q, 0) == 1.0   # capped at 1
+    assert oracle.recall_tie_aware([0, 0xFFFFFFFF], truth, ts, D, Q, 0) == 0.5
