@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "index.cuh"
+#include "nvtx.cuh"
 #include "primitives.cuh"
 
 namespace sindi {
@@ -208,6 +209,7 @@ const char* sindi_version(void) { return "sindi-gb300 0.1 (sm_103a)"; }
 
 sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const float* values, int64_t n_docs,
                          int32_t dim, const sindi_build_params* params, void* stream, sindi_index** out) {
+    NvtxRange range("sindi_build n_docs=%lld dim=%lld", (long long)n_docs, (long long)dim);
     SINDI_TRACE_MSG("sindi_build: enter n_docs=%lld dim=%d", (long long)n_docs, (int)dim);
     set_last_error("");
     if (!out) {
@@ -327,6 +329,8 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
 sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
                           const float* q_values, int64_t n_queries, const sindi_search_params* params,
                           uint32_t* out_ids, float* out_scores, void* stream) {
+    NvtxRange range("sindi_search n_queries=%lld mode=%lld", (long long)n_queries,
+                    params ? (long long)params->mode : -1LL);
     set_last_error("");
     if (!index || !params) {
         set_last_error("index / params is NULL");
@@ -437,6 +441,8 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
 sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
                                   const float* q_values, int64_t n_queries, const sindi_search_params* params,
                                   uint32_t* out_ids, float* out_scores, void* stream) {
+    NvtxRange range("sindi_search_noalloc n_queries=%lld mode=%lld", (long long)n_queries,
+                    params ? (long long)params->mode : -1LL);
     set_last_error("");
     if (!index || !params) {
         set_last_error("index / params is NULL");
@@ -535,6 +541,7 @@ sindi_status sindi_index_export(const sindi_index* index, uint32_t* seg, uint16_
 
 
 sindi_status sindi_index_save(const sindi_index* index, const char* path) {
+    NvtxRange range("sindi_index_save");
     set_last_error("");
     if (!index || !path) {
         set_last_error("index and path must not be NULL");
@@ -588,6 +595,7 @@ sindi_status sindi_index_save(const sindi_index* index, const char* path) {
 }
 
 sindi_status sindi_index_load(const char* path, void* stream, sindi_index** out) {
+    NvtxRange range("sindi_index_load");
     set_last_error("");
     if (!path || !out) {
         set_last_error("path and out must not be NULL");

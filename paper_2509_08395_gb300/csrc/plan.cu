@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "index.cuh"
+#include "nvtx.cuh"
 
 namespace sindi {
 
@@ -43,6 +44,8 @@ extern "C" {
 sindi_status sindi_plan_create(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
                                const float* q_values, int64_t n_queries, const sindi_search_params* params,
                                uint32_t* out_ids, float* out_scores, sindi_plan** out) {
+    NvtxRange range("sindi_plan_create n_queries=%lld k=%lld", (long long)n_queries,
+                    params ? (long long)params->k : -1LL);
     set_last_error("");
     if (!index || !params || !out || !q_indptr || !q_indices || !q_values || !out_ids || !out_scores ||
         n_queries <= 0 || n_queries > 65535) {
@@ -107,6 +110,7 @@ sindi_status sindi_plan_create(const sindi_index* index, const int64_t* q_indptr
 }
 
 sindi_status sindi_plan_launch(sindi_plan* plan, void* stream) {
+    NvtxRange range("sindi_plan_launch");
     if (!plan || !plan->impl.exec) return SINDI_ERR_INVALID_ARG;
     cudaError_t e = cudaGraphLaunch(plan->impl.exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {

@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "index.cuh"
+#include "nvtx.cuh"
 
 namespace sindi {
 
@@ -206,6 +207,8 @@ void Server::run() {
             }
         }
         for (auto& st : starts) {
+            NvtxRange range("sindi_server batch of %lld (slot %lld)", (long long)st.second.size(),
+                            (long long)(st.first - slots.data()));
             if (!launch(*st.first, std::move(st.second))) finish(*st.first);
         }
     }

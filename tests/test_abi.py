@@ -115,3 +115,38 @@ def test_binding_checks_buffer_sizes_before_the_call(lib):
         cuda_stream = 1234
 
     assert sindi._stream(FakeStream()) == 1234 and sindi._stream(77) == 77 and sindi._stream(None, qp) is None
+
+
+def test_entry_points_push_nvtx_ranges(lib, tmp_path):
+    """Every entry point opens an NVTX range named for the call (a timeline tool shows which call a kernel
+    belongs to). A recording NVTX injection library (tests/nvtx_recorder.c) captures them in a child
+    process; the calls fail their argument checks, so nothing touches a device."""
+    import shutil
+    import subprocess
+    import sys
+
+    import pytest
+
+    cuda_inc = "/usr/local/cuda/include"
+    if not os.path.exists(os.path.join(cuda_inc, "nvtx3", "nvToolsExt.h")) or not shutil.which("gcc"):
+        pytest.skip("needs gcc and the CUDA NVTX headers")
+    rec = str(tmp_path / "librecorder.so")
+    subprocess.check_call(["gcc", "-O1", "-fPIC", "-shared", f"-I{cuda_inc}",
+                           os.path.join(ROOT, "tests", "nvtx_recorder.c"), "-o", rec])
+    log = tmp_path / "ranges.txt"
+    child = (
+        "import ctypes, sys\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from paper_2509_08395_gb300 import sindi\n"
+        "L = sindi.load()\n"
+        "out = ctypes.c_void_p()\n"
+        "assert L.sindi_build(None, None, None, 10, 4, None, None, ctypes.byref(out)) != 0\n"
+        "prm = sindi.sindi_search_params(k=5, gamma=0, beta=1.0, mode=1, block_threads=0)\n"
+        "assert L.sindi_search(None, None, None, None, 3, ctypes.byref(prm), None, None, None) != 0\n"
+        "assert L.sindi_index_load(b'/nonexistent/index.bin', None, ctypes.byref(out)) != 0\n"
+    )
+    env = dict(os.environ, NVTX_INJECTION64_PATH=rec, NVTX_RECORD_PATH=str(log))
+    subprocess.run([sys.executable, "-c", child], check=True, env=env, timeout=120)
+    lines = log.read_text().splitlines()
+    assert lines == ["push sindi_build n_docs=10 dim=4", "pop", "push sindi_search n_queries=3 mode=1", "pop",
+                     "push sindi_index_load", "pop"], lines
