@@ -154,3 +154,60 @@ def signed_copy(values, every=3):
     v = np.array(values, np.float32, copy=True)
     v[1::every] = -v[1::every]
     return v
+
+
+def _beat_counts(s, b, exact0):
+    """For every document i: how many others certainly beat it (certain[i]) and how many might (might[i]),
+    for scores known to within +-b. Documents with no common term (exact0) score exactly 0 on both sides, so
+    between two of them the lower id wins, as the search's order rule says."""
+    s = np.asarray(s, np.float64)
+    lo, hi = s - b, s + b
+    n = len(s)
+    los, his = np.sort(lo), np.sort(hi)
+    certain = n - np.searchsorted(los, hi, side="right")            # #{j : lo_j > hi_i}
+    might = n - np.searchsorted(his, lo, side="left") - 1            # #{j != i : hi_j >= lo_i}
+    z = np.nonzero(exact0)[0]                                        # ascending ids
+    rank = np.arange(len(z))
+    certain[z] += rank                                               # lower-id exact zeros beat i
+    might[z] -= len(z) - 1 - rank                                    # higher-id exact zeros cannot
+    return certain, might
+
+
+def check_reranked_conditioned(gids, gsc, sc, ac, mc, sf, af, mf, k, gamma, what=""):
+    """GPU results of Algorithm 4 over signed data, for one query.
+
+    sc, ac: the exact coarse score of every document (pruned document, pruned query) and its sum of
+    |products|; mc: the coarse query's term count. sf, af, mf: the same for the exact reorder score (full
+    document, full query). The GPU takes the exact best gamma of its FP32 coarse scores, then the exact
+    best k of their FP32 reorder scores. So: every returned id must be a possible candidate (fewer than
+    gamma documents certainly beat it on the coarse score); its score must lie within the FP32 bound of
+    sf; the scores must descend; and no certain candidate (fewer than gamma documents might beat it) that
+    was left out may certainly beat a returned one on sf."""
+    sc, sf = np.asarray(sc, np.float64), np.asarray(sf, np.float64)
+    n_docs = len(sc)
+    g, n = min(gamma, n_docs), min(k, n_docs)
+    bc, bf = fp32_sum_bound(ac, mc), fp32_sum_bound(af, mf)
+    certain_c, might_c = _beat_counts(sc, bc, np.asarray(ac) == 0)
+    possible, certain = certain_c < g, might_c < g
+    gids = np.asarray(gids).astype(np.int64)[:n] & 0xFFFFFFFF
+    gsc = np.asarray(gsc, np.float64)[:n]
+    assert np.all(gids < n_docs), f"{what}: id out of range"
+    assert len(set(gids.tolist())) == n, f"{what}: duplicate ids"
+    bad = np.nonzero(~possible[gids])[0]
+    assert len(bad) == 0, f"{what}: id {gids[bad[0]]} at rank {bad[0]} cannot be a coarse candidate"
+    err = np.abs(gsc - sf[gids])
+    bad = np.nonzero(err > bf[gids])[0]
+    assert len(bad) == 0, (f"{what}: rank {bad[0]} id {gids[bad[0]]}: gpu {gsc[bad[0]]!r} exact "
+                           f"{sf[gids[bad[0]]]!r} bound {bf[gids[bad[0]]]!r}")
+    assert np.all(np.diff(gsc) <= 0), f"{what}: scores not in descending order"
+    left = certain.copy()
+    left[gids] = False
+    if left.any():
+        hi_out = np.max((sf - bf)[left])
+        lo_in = np.min((sf + bf)[gids])
+        assert hi_out <= lo_in, (f"{what}: a certain candidate left out ({hi_out!r}) certainly beats a returned "
+                                 f"document ({lo_in!r})")
+        z_in = [int(i) for i in gids if af[i] == 0]
+        z_out = np.nonzero(left & (np.asarray(af) == 0))[0]
+        if z_in and len(z_out):
+            assert z_out.min() > max(z_in), f"{what}: exact-zero ties must go to the lower ids"

@@ -91,3 +91,67 @@ def test_fp32_bound_is_tight_enough_to_order_documents(signed_case):
     top = np.sort(s)[::-1][:60]
     gaps = -np.diff(top)
     assert np.median(gaps) > 100 * np.max(b[np.argsort(-s)[:60]])
+
+
+def _fp32_dot(row_d, row_v, qd, qv, rng):
+    """delta(x, q) in FP32: each common term's product rounded, then added in a random order."""
+    common, xi, qi = np.intersect1d(row_d, qd, return_indices=True)
+    prods = (row_v[xi].astype(np.float32) * qv[qi].astype(np.float32)).astype(np.float32)
+    acc = np.float32(0.0)
+    for p in prods[rng.permutation(len(prods))]:
+        acc = np.float32(acc + p)
+    return acc
+
+
+def test_conditioned_reorder_rule_accepts_fp32_and_rejects_planted_errors(signed_case):
+    from parity import check_reranked_conditioned
+
+    w, (qp, qx, qv), D, Q, I, Qa, Ia = signed_case
+    ip, ix, v = D.export()
+    Da = oracle.Dataset(ip, ix, np.abs(v).astype(np.float32), D.dim)
+    seg, pid, pval, _, _ = I.export()
+    k, gamma, n = 10, 200, D.n
+    rng = np.random.default_rng(5)
+    for r in range(Q.n):
+        qd, qvv = qx[qp[r]:qp[r + 1]], qv[qp[r]:qp[r + 1]]
+        m = len(qd)
+        sc, ac = _exact(I, Q, r, n), _exact(Ia, Qa, r, n)
+        sf, af = oracle.all_scores(D, Q, r), oracle.all_scores(Da, Qa, r)
+        A = _fp32_scan(seg, pid, pval, I.sigma, n, qd, qvv, rng)
+        cand = np.lexsort((np.arange(n), -A.astype(np.float64)))[:gamma]
+        fin = np.array([_fp32_dot(ix[ip[i]:ip[i + 1]], v[ip[i]:ip[i + 1]], qd, qvv, rng) for i in cand], np.float32)
+        order = np.lexsort((cand, -fin.astype(np.float64)))[:k]
+        gids, gsc = cand[order], fin[order]
+        check_reranked_conditioned(gids, gsc, sc, ac, m, sf, af, m, k, gamma, what=f"query {r}")
+        # planted: a returned id replaced by a document far below the coarse pool
+        far = int(np.lexsort((np.arange(n), -sc))[gamma + 400])
+        bad = gids.copy()
+        bad[-1] = far
+        with pytest.raises(AssertionError, match="cannot be a coarse candidate"):
+            check_reranked_conditioned(bad, gsc, sc, ac, m, sf, af, m, k, gamma)
+        # planted: the best reordered document dropped for the candidate ranked k + 20 by its FP32 score
+        full = np.lexsort((cand, -fin.astype(np.float64)))
+        worse_ids = np.concatenate([gids[1:], cand[full[k + 20:k + 21]]])
+        worse_sc = np.concatenate([gsc[1:], fin[full[k + 20:k + 21]]])
+        with pytest.raises(AssertionError, match="certainly beats"):
+            check_reranked_conditioned(worse_ids, worse_sc, sc, ac, m, sf, af, m, k, gamma)
+        # planted: a score off by 1e-3 of its value
+        off = gsc.astype(np.float64).copy()
+        off[0] *= 1 + 1e-3
+        with pytest.raises(AssertionError, match="bound"):
+            check_reranked_conditioned(gids, off, sc, ac, m, sf, af, m, k, gamma)
+
+
+def test_beat_counts_hand_example():
+    """Scores 3, 0, 0, 1, 0 known to +-0.1 except the three exact zeros (no common term), which tie exactly
+    and rank by id: counts of documents that certainly / might beat each one, worked by hand."""
+    from parity import _beat_counts
+
+    s = np.array([3.0, 0.0, 0.0, 1.0, 0.0])
+    b = np.array([0.1, 1e-300, 1e-300, 0.1, 1e-300])
+    certain, might = _beat_counts(s, b, s == 0)
+    assert certain.tolist() == [0, 2, 3, 1, 4]
+    assert might.tolist() == [0, 2, 3, 1, 4]
+    # no longer exact: the zeros might beat one another but certainly beat none of each other
+    certain, might = _beat_counts(s, np.full(5, 0.1), np.zeros(5, bool))
+    assert certain.tolist() == [0, 2, 2, 1, 2] and might.tolist() == [0, 4, 4, 1, 4]
