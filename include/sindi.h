@@ -303,7 +303,8 @@ sindi_status sindi_server_submit(sindi_server* server, const int32_t* q_indices,
 /* Wait up to wait_ms (0 = just look, < 0 = no limit) for a request. When it is
    done, copies its k ids and scores (as sindi_search writes one row) into the
    host buffers, sets *latency_ms if not NULL, forgets the ticket and returns
-   SINDI_OK or the request's own error status. Returns SINDI_ERR_TIMEOUT while
+   SINDI_OK or the request's own error status (its reason then in
+   sindi_last_error of the polling thread). Returns SINDI_ERR_TIMEOUT while
    it is still running, SINDI_ERR_INVALID_ARG for an unknown ticket. */
 sindi_status sindi_server_poll(sindi_server* server, uint64_t ticket, int32_t wait_ms, uint32_t* ids, float* scores,
                                double* latency_ms);
@@ -311,7 +312,8 @@ sindi_status sindi_server_poll(sindi_server* server, uint64_t ticket, int32_t wa
 /* Counters and latency percentiles; reset = 1 clears the latency record and counters. */
 sindi_status sindi_server_stats(sindi_server* server, sindi_server_stats_t* out, int reset);
 
-/* Stop accepting requests, finish the ones queued or in flight, free everything. */
+/* Stop accepting requests, finish the ones queued or in flight, free everything.
+   No other call on the same server may run concurrently with it or after it. */
 void sindi_server_destroy(sindi_server* server);
 
 /* Synchronise `stream`, then return (and clear) the device error word of the

@@ -11,6 +11,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -32,6 +33,7 @@ struct Request {
     std::vector<float> scores;
     int state = 0;  // 0 queued, 1 on the device, 2 finished
     sindi_status status = SINDI_OK;
+    std::string error;  // why it failed (the worker's own last-error string is not the poller's)
 };
 
 struct Slot {
@@ -128,7 +130,11 @@ bool Server::launch(Slot& s, std::vector<std::shared_ptr<Request>>&& batch) {
     s.batch = std::move(batch);
     s.busy = true;
     if (st != SINDI_OK) {
-        for (auto& r : s.batch) r->status = st;
+        const std::string why = "batch of " + std::to_string(nb) + " failed: " + sindi_last_error();
+        for (auto& r : s.batch) {
+            r->status = st;
+            r->error = why;
+        }
     }
     return st == SINDI_OK;
 }
@@ -169,7 +175,10 @@ void Server::run() {
             if (q == cudaSuccess) {
                 finish(s);
             } else if (q != cudaErrorNotReady) {
-                for (auto& r : s.batch) r->status = SINDI_ERR_CUDA;
+                for (auto& r : s.batch) {
+                    r->status = SINDI_ERR_CUDA;
+                    r->error = std::string("batch failed on the device: ") + cudaGetErrorString(q);
+                }
                 finish(s);
             } else {
                 any_busy = true;
@@ -350,7 +359,10 @@ sindi_status sindi_server_poll(sindi_server* server, uint64_t ticket, int32_t wa
     if (!ready()) return SINDI_ERR_TIMEOUT;
     S.live.erase(it);
     lk.unlock();
-    if (r->status != SINDI_OK) return r->status;
+    if (r->status != SINDI_OK) {
+        set_last_error(r->error);
+        return r->status;
+    }
     if (ids) std::copy(r->ids.begin(), r->ids.end(), ids);
     if (scores) std::copy(r->scores.begin(), r->scores.end(), scores);
     if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
