@@ -246,7 +246,7 @@ sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_ind
  *   addresses, n_queries or the total number of query entries beyond what the
  *   buffers hold. Device pointers only; 1 <= n_queries <= 65535.
  *   The plan owns its workspace (allocated here). Launches of one plan must
- *   not overlap each other on the GPU.
+ *   not overlap each other on the GPU. The index must outlive the plan.
  */
 typedef struct sindi_plan sindi_plan;
 sindi_status sindi_plan_create(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
@@ -364,7 +364,9 @@ sindi_status sindi_get_stats(const sindi_index* index, sindi_stats_t* out);
 sindi_status sindi_reset_stats(const sindi_index* index);
 
 /* Free an index and everything it owns. NULL is ignored. Waits for work
-   queued on the index's streams to finish. */
+   queued on the index's streams to finish. Plans and servers over the index
+   must be freed first, and no search on it may still be running on a
+   caller's stream. */
 void sindi_index_free(sindi_index* index);
 
 /* Message of the last failed call on this thread ("" if none). */
