@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -292,6 +293,7 @@ class Index:
     def __init__(self, indptr, indices, values, dim: int, window: int = 0, alpha: float = 1.0,
                  value_dtype: str = "f32", stream=None, prune: str = "mass", prune_n: int = 0):
         n_docs = (indptr.shape[0] if hasattr(indptr, "shape") else len(indptr)) - 1
+        self._dependents = weakref.WeakSet()  # plans and servers over this index
         self.handle = sindi_build(indptr, indices, values, n_docs, dim, window, alpha, value_dtype, stream, prune,
                                   prune_n)
         self.info = sindi_index_info(self.handle)
@@ -320,6 +322,7 @@ class Index:
     def load(cls, path: str, stream=None) -> "Index":
         """An index read back from `path` (sindi_index_load)."""
         obj = cls.__new__(cls)
+        obj._dependents = weakref.WeakSet()
         obj.handle = sindi_index_load(path, stream)
         obj.info = sindi_index_info(obj.handle)
         return obj
@@ -331,6 +334,9 @@ class Index:
         return sindi_index_export(self.handle)
 
     def close(self):
+        """Free the index; plans and servers still open over it are closed first (they must not outlive it)."""
+        for dep in list(getattr(self, "_dependents", ())):
+            dep.close()
         if getattr(self, "handle", None):
             sindi_index_free(self.handle)
             self.handle = None
@@ -389,6 +395,7 @@ class Plan:
         self.out = out
         self.handle = sindi_plan_create(index.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma,
                                         block=block)
+        index._dependents.add(self)
 
     def launch(self, stream=None):
         sindi_plan_launch(self.handle, stream)
@@ -467,6 +474,7 @@ class Server:
         self.index = index  # keeps the index alive
         self.k = k
         self.handle = sindi_server_create(index.handle, k, gamma, **kw)
+        index._dependents.add(self)
 
     def submit(self, q_indices, q_values) -> int:
         return sindi_server_submit(self.handle, q_indices, q_values)

@@ -150,3 +150,28 @@ def test_entry_points_push_nvtx_ranges(lib, tmp_path):
     lines = log.read_text().splitlines()
     assert lines == ["push sindi_build n_docs=10 dim=4", "pop", "push sindi_search n_queries=3 mode=1", "pop",
                      "push sindi_index_load", "pop"], lines
+
+
+def test_closing_an_index_closes_its_plans_and_servers_first(lib):
+    """A plan or server must not outlive its index: Index.close() closes those still open, then frees."""
+    import weakref
+
+    from paper_2509_08395_gb300 import sindi
+
+    order = []
+
+    class Dependent:
+        def __init__(self, name):
+            self.name = name
+
+        def close(self):
+            order.append(self.name)
+
+    idx = sindi.Index.__new__(sindi.Index)
+    idx.handle = None                       # nothing to free on the device
+    idx._dependents = weakref.WeakSet()
+    plan, server = Dependent("plan"), Dependent("server")
+    idx._dependents.add(plan)
+    idx._dependents.add(server)
+    idx.close()
+    assert sorted(order) == ["plan", "server"]
