@@ -201,7 +201,9 @@ sindi_status sindi_build(const int64_t* indptr, const int32_t* indices, const fl
  * not being captured) comes a second time, its launches are recorded as one
  * CUDA graph with working memory of its own (held until the index is freed
  * or another call is recorded); identical calls then launch the graph, which
- * reads the buffers' current contents.
+ * reads the buffers' current contents. A plain call on a stream that is not
+ * being captured first waits (on the GPU) for the graph's previous launch, so
+ * launches from different streams never share its working memory at once.
  */
 sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,
                           const float* q_values, int64_t n_queries, const sindi_search_params* params,

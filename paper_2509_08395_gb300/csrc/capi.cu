@@ -201,6 +201,23 @@ static bool read_device(FILE* f, T* dev, size_t count, void* stage, const Check&
 
 using namespace sindi;
 
+// Replays of the recorded plain graph share its workspace: a plain call on
+// another stream must not start before the previous replay has ended. A
+// stream being captured never replays the graph and may not wait on an
+// event recorded outside its capture.
+static void after_last_graph_replay(const IndexImpl& ix, const sindi_search_params& prm, cudaStream_t s) {
+    if (prm.mode != SINDI_MODE_PLAIN || prm.beta < 1.0) return;
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    SINDI_CUDA(cudaStreamIsCapturing(s, &cst));
+    if (cst != cudaStreamCaptureStatusNone) return;
+    cudaEvent_t last = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ix.graph_mu);
+        last = ix.graph_exec ? ix.graph_done : nullptr;
+    }
+    if (last) SINDI_CUDA(cudaStreamWaitEvent(s, last, 0));
+}
+
 extern "C" {
 
 const char* sindi_last_error(void) { return g_last_error.c_str(); }
@@ -364,6 +381,7 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
             return SINDI_ERR_INVALID_ARG;
         }
         try {
+            after_last_graph_replay(ix, prm, s);
             return search_impl(ix, q_indptr, q_indices, q_values, n_queries, prm, out_ids, out_scores, s);
         } catch (const CudaError& e) {
             return from_cuda(e);
@@ -413,6 +431,7 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
             oi = d_ids;
             os = d_sc;
         }
+        after_last_graph_replay(ix, prm, s);
         st = search_impl(ix, ip, qi, qv, n_queries, prm, oi, os, s);
         if (st == SINDI_OK && !out_dev) {
             SINDI_CUDA(cudaMemcpyAsync(out_ids, d_ids, 4 * nout, cudaMemcpyDeviceToHost, s));
