@@ -5,7 +5,10 @@ wrong sign, index or operand, a boundary off by one, a tie broken the other
 way. The test builds the copy and runs the pin suite (test_oracle_pins.py)
 against it with ORACLE_LIBRARY pointing at the copy. The pins must fail on
 every mutant. The real oracle is never touched. Each mutant keeps every memory
-access in bounds, so a failure is a failed assertion and not a crash.
+access in bounds, so a failure is a failed assertion and not a crash, and each
+changes what the oracle computes (a planted change that cannot alter any
+result, such as narrowing a codec's search range below a value a branch before
+it already handles, is not a mutant).
 """
 import concurrent.futures
 import os
@@ -97,6 +100,26 @@ MUTANTS = [
     ("binary16 posting values stored unrounded", "reduced-precision lists",
      "for (int64_t t = 0; t < P; t++) I->pval[t] = (double)orc_f16_decode(orc_f16_encode((float)I->pval[t]));",
      ""),
+    ("dim == d accepted", "Def. 1",
+     "if (j < 0 || j >= d || !isfinite(v))", "if (j < 0 || j > d || !isfinite(v))"),
+    ("non-finite values accepted", "Def. 1",
+     "if (j < 0 || j >= d || !isfinite(v))", "if (j < 0 || j >= d)"),
+    ("brute force skips the last document", "Def. 3",
+     "    for (int64_t i = 0; i < D->n; i++) {\n        orc_hit x = { orc_inner_product(D, i, Q, r), i };",
+     "    for (int64_t i = 0; i + 1 < D->n; i++) {\n        orc_hit x = { orc_inner_product(D, i, Q, r), i };"),
+    ("inner product advances the wrong cursor", "Def. 2",
+     "if (xd[a] < qd[b]) a++;\n        else if (xd[a] > qd[b]) b++;",
+     "if (xd[a] < qd[b]) b++;\n        else if (xd[a] > qd[b]) a++;"),
+    ("results drained worst first", "result order",
+     "if (better(a, b)) return -1;\n    if (better(b, a)) return 1;",
+     "if (better(a, b)) return 1;\n    if (better(b, a)) return -1;"),
+    ("list offsets miss the last prefix step", "Alg. 1",
+     "for (int64_t s = 0; s < d * sigma; s++) I->seg[s + 1] += I->seg[s];",
+     "for (int64_t s = 0; s + 1 < d * sigma; s++) I->seg[s + 1] += I->seg[s];"),
+    ("list pruning leaves the kept counts unchanged", "Sec. 4.1 LP",
+     "else I->kept_count[lw[t].doc]--;", ""),
+    ("E4M3 subnormals scaled by 2^-10", "OCP E4M3",
+     "if (e == 0) v = ldexp((double)m, -9);", "if (e == 0) v = ldexp((double)m, -10);"),
 ]
 
 

@@ -224,6 +224,8 @@ def test_dataset_rejects_malformed_and_drops_zeros():
     bad = [
         (np.array([0, 2, 1], np.int64), np.array([0, 1], np.int32), np.ones(2, np.float32)),   # decreasing
         (np.array([0, 2], np.int64), np.array([0, 9], np.int32), np.ones(2, np.float32)),      # dim >= d
+        (np.array([0, 1], np.int64), np.array([4], np.int32), np.ones(1, np.float32)),         # dim == d
+        (np.array([0, 1], np.int64), np.array([2], np.int32), np.array([np.inf], np.float32)),  # infinity
         (np.array([0, 2], np.int64), np.array([3, 3], np.int32), np.ones(2, np.float32)),      # duplicate
         (np.array([0, 1], np.int64), np.array([1], np.int32), np.array([np.nan], np.float32)),  # NaN
         (np.array([0, 1], np.int64), np.array([-1], np.int32), np.ones(1, np.float32)),        # negative dim
