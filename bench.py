@@ -587,79 +587,101 @@ def main():
     gpu_ids = out_ids.cpu().numpy().view(np.uint32)
     assert np.array_equal(gpu_ids, h_ids.numpy().view(np.uint32)), "host-buffer results differ from device results"
 
-    # ---- side forms on the same queries (batched schedule; FP16 / FP8 postings)
+    # ---- side forms on the same queries (batched schedule; FP16 / FP8 postings). The optional legs run
+    # after the headline measurement; a leg that fails is reported in side_errors and the line still prints.
+    side_errors = []
+
+    def side_failed(leg, e):
+        side_errors.append(f"{leg}: {type(e).__name__}: {e}")
+        print(f"bench: {leg} failed: {e!r}", file=sys.stderr, flush=True)
+
     forms = {}
     if not args.no_forms:
-        def timed(fn, reps):
-            for _ in range(3):  # warm: a repeated plain call is recorded as a graph on its second run
-                fn()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            tot = 0.0
-            for _ in range(reps):
-                flush.zero_()
-                e0.record(stream)
-                fn()
-                e1.record(stream)
+        try:
+            def timed(fn, reps):
+                for _ in range(3):  # warm: a repeated plain call is recorded as a graph on its second run
+                    fn()
                 torch.cuda.synchronize()
-                tot += e0.elapsed_time(e1)
-            return nq * reps / (tot / 1000.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                tot = 0.0
+                for _ in range(reps):
+                    flush.zero_()
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    tot += e0.elapsed_time(e1)
+                return nq * reps / (tot / 1000.0)
 
-        other = "batched" if args.mode == "plain" else "plain"
-        forms[other] = {"qps": timed(lambda: step(other), args.steps)}
-        forms[other]["ids_equal_to_main"] = float(np.mean(out_ids.cpu().numpy().view(np.uint32) == gpu_ids))
-        if nq <= 65535:
-            # the batched search captured once as a CUDA graph: one graph launch per step
-            with sindi.Plan(idx, *q_dev, k=w.k, gamma=w.gamma) as plan:
-                forms["batched_graph"] = {"qps": timed(lambda: plan.launch(stream.cuda_stream), args.steps)}
-                gids = plan.out[0].cpu().numpy().view(np.uint32)
-                forms["batched_graph"]["ids_equal_to_main"] = float(np.mean(gids == gpu_ids))
-        # the autotuner on the same documents and queries
-        from paper_2509_08395_gb300 import autotune
+            other = "batched" if args.mode == "plain" else "plain"
+            forms[other] = {"qps": timed(lambda: step(other), args.steps)}
+            forms[other]["ids_equal_to_main"] = float(np.mean(out_ids.cpu().numpy().view(np.uint32)
+                                                              == gpu_ids))
+            if nq <= 65535:
+                # the batched search captured once as a CUDA graph: one graph launch per step
+                with sindi.Plan(idx, *q_dev, k=w.k, gamma=w.gamma) as plan:
+                    forms["batched_graph"] = {"qps": timed(lambda: plan.launch(stream.cuda_stream), args.steps)}
+                    gids = plan.out[0].cpu().numpy().view(np.uint32)
+                    forms["batched_graph"]["ids_equal_to_main"] = float(np.mean(gids == gpu_ids))
+            # the autotuner on the same documents and queries
+            from paper_2509_08395_gb300 import autotune
 
-        dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
-        tuned = autotune.autotune(dip, dix, dv, w.dim, *q_dev, k=w.k, alpha=w.alpha, recall_target=0.99)
-        del dip, dix, dv
-        forms["autotuned"] = dict(tuned["choice"] or {}, seconds=tuned["seconds"],
-                                  recall_vs="GPU exact search (alpha = 1, gamma = 0)")
-        if not tuned["choice"]:
-            forms["autotuned"]["table"] = tuned["table"]
-        for dt in ("f16", "f8"):
             dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
-            with sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=w.alpha, value_dtype=dt) as lp:
-                del dip, dix, dv
-                oi = torch.empty_like(out_ids)
-                os_ = torch.empty_like(out_sc)
-                # the other schedule too: reduced precision is a posting format, either schedule reads it
-                oth = "batched" if args.mode == "plain" else "plain"
-                forms[dt + "_" + oth] = {"qps": timed(lambda: lp.search(*q_dev, k=w.k, gamma=w.gamma, mode=oth,
-                                                                        out=(oi, os_)), args.steps)}
-                qps = timed(lambda: lp.search(*q_dev, k=w.k, gamma=w.gamma, mode=args.mode, out=(oi, os_)),
-                            args.steps)
-                lp.check()
-                # coarse scores alone (gamma = 0) of the first queries, for the quantisation error
-                n_err = min(8, nq)
-                cq = [torch.from_numpy(a).to(dev) for a in (qp[: n_err + 1], qx[: qp[n_err]], qv[: qp[n_err]])]
-                _, csc = lp.search(*cq, k=w.k, gamma=0)
-                forms[dt + "_" + args.mode] = {"qps": qps, "_ids": oi.cpu().numpy().view(np.uint32),
-                                               "_sc": os_.cpu().numpy(), "_coarse": csc.cpu().numpy()}
+            tuned = autotune.autotune(dip, dix, dv, w.dim, *q_dev, k=w.k, alpha=w.alpha, recall_target=0.99)
+            del dip, dix, dv
+            forms["autotuned"] = dict(tuned["choice"] or {}, seconds=tuned["seconds"],
+                                      recall_vs="GPU exact search (alpha = 1, gamma = 0)")
+            if not tuned["choice"]:
+                forms["autotuned"]["table"] = tuned["table"]
+            for dt in ("f16", "f8"):
+                dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
+                with sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=w.alpha, value_dtype=dt) as lp:
+                    del dip, dix, dv
+                    oi = torch.empty_like(out_ids)
+                    os_ = torch.empty_like(out_sc)
+                    # the other schedule too: reduced precision is a posting format, either schedule reads it
+                    oth = "batched" if args.mode == "plain" else "plain"
+                    forms[dt + "_" + oth] = {"qps": timed(lambda: lp.search(*q_dev, k=w.k, gamma=w.gamma, mode=oth,
+                                                                            out=(oi, os_)), args.steps)}
+                    qps = timed(lambda: lp.search(*q_dev, k=w.k, gamma=w.gamma, mode=args.mode, out=(oi, os_)),
+                                args.steps)
+                    lp.check()
+                    # coarse scores alone (gamma = 0) of the first queries, for the quantisation error
+                    n_err = min(8, nq)
+                    cq = [torch.from_numpy(a).to(dev) for a in (qp[: n_err + 1], qx[: qp[n_err]], qv[: qp[n_err]])]
+                    _, csc = lp.search(*cq, k=w.k, gamma=0)
+                    forms[dt + "_" + args.mode] = {"qps": qps, "_ids": oi.cpu().numpy().view(np.uint32),
+                                                   "_sc": os_.cpu().numpy(), "_coarse": csc.cpu().numpy()}
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            side_failed("forms", e)
+            forms = {name: f for name, f in forms.items() if "_ids" not in f}
 
     ablation = None
     if args.ablation and rank == 0:
-        ablation = pruning_ablation(sindi, torch, dev, w, ip, ix, v, q_dev, nq, args.steps, flush, stream)
+        try:
+            ablation = pruning_ablation(sindi, torch, dev, w, ip, ix, v, q_dev, nq, args.steps, flush, stream)
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            side_failed("pruning_ablation", e)
     sweep = None
     if args.sparsity_sweep and rank == 0:
-        sweep = sparsity_sweep(sindi, torch, dev, args.steps, flush, stream)
+        try:
+            sweep = sparsity_sweep(sindi, torch, dev, args.steps, flush, stream)
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            side_failed("sparsity_sweep", e)
 
     serving = None
     if rank == 0 and (args.serve_sweep or not args.no_forms):
         rows = [(qx[qp[r]:qp[r + 1]], qv[qp[r]:qp[r + 1]]) for r in range(nq)]
         base = value if args.mode == "batched" else forms.get("batched", {}).get("qps", value)
-        if args.serve_sweep:
-            serving = [serve_open_loop(sindi, idx, rows, w.k, w.gamma, float(f) * base, args.serve_seconds)
-                       for f in args.serve_sweep.split(",")]
-        else:
-            serving = serve_open_loop(sindi, idx, rows, w.k, w.gamma, args.serve_load * base, args.serve_seconds)
+        try:
+            if args.serve_sweep:
+                serving = [serve_open_loop(sindi, idx, rows, w.k, w.gamma, float(f) * base, args.serve_seconds)
+                           for f in args.serve_sweep.split(",")]
+            else:
+                serving = serve_open_loop(sindi, idx, rows, w.k, w.gamma, args.serve_load * base,
+                                          args.serve_seconds)
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            side_failed("serving", e)
 
     # ---- CPU baseline (oracle) + recall against FP64 exact, rank 0 only
     cpu = None
@@ -774,6 +796,7 @@ def main():
         "sparsity_sweep": sweep,
         "serving": serving,
         "scan_source_sha256": sha,
+        "side_errors": side_errors,
     }
     print(json.dumps(line), flush=True)
     idx.close()
