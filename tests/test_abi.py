@@ -175,3 +175,37 @@ def test_closing_an_index_closes_its_plans_and_servers_first(lib):
     idx._dependents.add(server)
     idx.close()
     assert sorted(order) == ["plan", "server"]
+
+
+def test_build_parameter_checks_come_before_any_device_work(lib):
+    """Each invalid build parameter is refused with its status and a message, before the device is touched
+    (this machine may have none); valid arguments reach the device check and fail cleanly without one."""
+    import numpy as np
+
+    from paper_2509_08395_gb300 import sindi
+
+    L = sindi.load()
+    ip = np.array([0, 2, 3], np.int64)
+    ix = np.array([0, 1, 2], np.int32)
+    v = np.ones(3, np.float32)
+    out = ctypes.c_void_p()
+
+    def build(n_docs=2, dim=4, **kw):
+        prm = sindi.sindi_build_params(**dict(dict(window=0, value_dtype=0, alpha=1.0, prune=0, prune_n=0), **kw))
+        return L.sindi_build(ip.ctypes.data, ix.ctypes.data, v.ctypes.data, n_docs, dim, ctypes.byref(prm), None,
+                             ctypes.byref(out))
+
+    invalid = [dict(alpha=0.0), dict(alpha=1.5), dict(alpha=float("nan")), dict(window=32769), dict(value_dtype=3),
+               dict(value_dtype=-1), dict(prune=4), dict(prune=-1), dict(prune=1, prune_n=0),
+               dict(prune=2, prune_n=0), dict(prune=3, prune_n=0), dict(n_docs=-1), dict(dim=0)]
+    for kw in invalid:
+        assert build(**kw) == sindi.SINDI_ERR_INVALID_ARG, kw
+        assert L.sindi_last_error(), kw
+        assert out.value is None
+    # an offset table of 2^34 entries or more is refused as unsupported
+    assert build(n_docs=(1 << 32) - 2, dim=1 << 20, window=1) == sindi.SINDI_ERR_UNSUPPORTED
+    assert b"offset table" in L.sindi_last_error()
+    import torch
+
+    if not torch.cuda.is_available():
+        assert build() == sindi.SINDI_ERR_CUDA and out.value is None
