@@ -155,3 +155,74 @@ def test_beat_counts_hand_example():
     # no longer exact: the zeros might beat one another but certainly beat none of each other
     certain, might = _beat_counts(s, np.full(5, 0.1), np.zeros(5, bool))
     assert certain.tolist() == [0, 2, 2, 1, 2] and might.tolist() == [0, 4, 4, 1, 4]
+
+
+@pytest.fixture(scope="module")
+def plain_case():
+    w = datagen.WORKLOADS["pruned-1m"].scaled(n_docs=3000, n_queries=8)
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    D, Q = oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+    I = oracle.Index(D, window=1024, alpha=0.5)
+    return w, (ip, ix, v), (qp, qx, qv), D, Q, I
+
+
+def test_ranked_rule_accepts_fp32_and_rejects_planted_errors(plain_case):
+    """check_ranked (the coarse rule of the GPU tests, non-negative data) against FP32 scans of the oracle's
+    own lists in random addition orders, and against answers with one planted error each."""
+    from parity import PAD_ID, check_ranked
+
+    w, _, (qp, qx, qv), D, Q, I = plain_case
+    seg, pid, pval, _, _ = I.export()
+    k, n = 50, D.n
+    rng = np.random.default_rng(21)
+    for r in range(Q.n):
+        oi, os_ = I.search(Q, r, k=k + 64, gamma=0)
+        A = _fp32_scan(seg, pid, pval, I.sigma, n, qx[qp[r]:qp[r + 1]], qv[qp[r]:qp[r + 1]], rng)
+        order = np.lexsort((np.arange(n), -A.astype(np.float64)))[:k]
+        gids, gsc = order.astype(np.int64), A[order]
+        check_ranked(gids, gsc, oi, os_, k, n, what=f"query {r}")
+        bad = gids.copy()
+        bad[0] = oi[k + 40]                                  # a document far outside the top-k
+        with pytest.raises(AssertionError):
+            check_ranked(bad, gsc, oi, os_, k, n)
+        off = gsc.astype(np.float64).copy()
+        off[k // 2] *= 1 + 1e-4                              # ten times the tolerance
+        with pytest.raises(AssertionError):
+            check_ranked(gids, off, oi, os_, k, n)
+        with pytest.raises(AssertionError):                  # padding where a document belongs
+            check_ranked(np.concatenate([gids[:-1], [PAD_ID]]), np.concatenate([gsc[:-1], [-np.inf]]),
+                         oi, os_, k, n)
+
+
+def test_reranked_rule_accepts_fp32_and_rejects_planted_errors(plain_case):
+    """check_reranked (the reorder rule of the GPU tests) against an FP32 emulation of Algorithm 4 (coarse
+    top-gamma of an FP32 scan, FP32 exact scores of the candidates, top-k), and against planted errors."""
+    from parity import check_reranked
+
+    w, (ip, ix, v), (qp, qx, qv), D, Q, I = plain_case
+    seg, pid, pval, _, _ = I.export()
+    k, gamma, n = 10, 200, D.n
+    rng = np.random.default_rng(22)
+    for r in range(Q.n):
+        qd, qvv = qx[qp[r]:qp[r + 1]], qv[qp[r]:qp[r + 1]]
+        A = _fp32_scan(seg, pid, pval, I.sigma, n, qd, qvv, rng)
+        cand = np.lexsort((np.arange(n), -A.astype(np.float64)))[:gamma]
+        fin = np.array([_fp32_dot(ix[ip[i]:ip[i + 1]], v[ip[i]:ip[i + 1]], qd, qvv, rng) for i in cand], np.float32)
+        order = np.lexsort((cand, -fin.astype(np.float64)))
+        gids, gsc = cand[order[:k]], fin[order[:k]]
+        check_reranked(gids, gsc, D, Q, r, I, k, gamma, what=f"query {r}")
+        outside = np.setdiff1d(np.arange(n), cand)
+        far = int(outside[np.argmin(A[outside])])           # the worst coarse score: never a candidate
+        bad = gids.copy()
+        bad[-1] = far
+        with pytest.raises(AssertionError, match="not a coarse candidate"):
+            check_reranked(bad, gsc, D, Q, r, I, k, gamma)
+        off = gsc.astype(np.float64).copy()
+        off[0] *= 1 + 1e-4
+        with pytest.raises(AssertionError, match="score of"):
+            check_reranked(gids, off, D, Q, r, I, k, gamma)
+        worse = np.concatenate([gids[1:], cand[order[k + 30:k + 31]]])
+        worse_sc = np.concatenate([gsc[1:], fin[order[k + 30:k + 31]]])
+        with pytest.raises(AssertionError):
+            check_reranked(worse, worse_sc, D, Q, r, I, k, gamma)
