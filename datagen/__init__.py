@@ -51,7 +51,8 @@ def build(force: bool = False) -> str:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
             subprocess.check_call(
-                ["gcc", "-O2", "-std=c11", "-fno-math-errno", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+                ["gcc", "-O2", "-std=c11", "-fno-math-errno", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp", _SRC,
+                 "-o", tmp, "-lm"]
             )
             os.replace(tmp, _LIB)
     return _LIB
