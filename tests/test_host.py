@@ -81,3 +81,16 @@ def test_cpu_oracle_sample_reports_recall_and_tie_aware_recall():
     worse = np.stack([t[w.k: 2 * w.k] for t in top]).astype(np.uint32)
     _, _, recalls, _, tie = bench.cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, 0.2, worse, w.k)
     assert np.mean(recalls) < 0.5 and all(t >= r for r, t in zip(recalls, tie))
+
+
+def test_bench_command_line():
+    """bench.py parses its command line without a GPU: the driver's flags and the documented extras."""
+    import subprocess
+    import sys
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr
+    for flag in ("--gpus", "--steps", "--warmup", "--impl", "--mode", "--workload", "--ablation",
+                 "--sparsity-sweep", "--no-forms", "--cpu-seconds"):
+        assert flag in r.stdout, flag
