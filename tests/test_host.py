@@ -94,3 +94,32 @@ def test_bench_command_line():
     for flag in ("--gpus", "--steps", "--warmup", "--impl", "--mode", "--workload", "--ablation",
                  "--sparsity-sweep", "--no-forms", "--cpu-seconds"):
         assert flag in r.stdout, flag
+
+
+def test_pruned_1m_inputs_follow_their_recipe():
+    """The pruned-1m stand-in draws what its recipe states (a 200k-document sample): document nnz
+    lognormal with mean 120 and sigma_ln 0.5 in [10, 400], query nnz mean 45 in [5, 150], values
+    lognormal(0, 0.8), dims unique within a row and Zipf(1.05) over ranks (slope of the mid ranks'
+    frequencies on a log-log scale), and the same rows for the same seed."""
+    w = datagen.WORKLOADS["pruned-1m"].scaled(n_docs=200_000)
+    ip, ix, v = datagen.docs(w)
+    nnz = np.diff(ip)
+    assert nnz.min() >= 10 and nnz.max() <= 400
+    assert abs(nnz.mean() - 120) < 1.5
+    assert abs(np.log(nnz).std() - 0.5) < 0.02
+    qp, qx, qv = datagen.queries(w)
+    qn = np.diff(qp)
+    assert qn.min() >= 5 and qn.max() <= 150 and abs(qn.mean() - 45) < 3
+    lv = np.log(v.astype(np.float64))
+    assert np.all(v > 0) and abs(lv.mean()) < 0.01 and abs(lv.std() - 0.8) < 0.01
+    assert ix.min() >= 0 and ix.max() < w.dim
+    rows = np.repeat(np.arange(len(nnz)), nnz)
+    assert np.all(np.diff(np.sort(rows.astype(np.int64) * w.dim + ix)) > 0)   # unique dims per row
+    freq = np.bincount(ix, minlength=w.dim).astype(np.float64)
+    r = np.arange(1000, 10000)                                                 # dim = rank - 1
+    slope = np.polyfit(np.log(r + 1.0), np.log(freq[r]), 1)[0]
+    assert abs(slope + 1.05) < 0.1, slope
+    ip2, ix2, v2 = datagen.docs(w)
+    assert np.array_equal(ip, ip2) and np.array_equal(ix, ix2) and np.array_equal(v, v2)
+    ip3, _, _ = datagen.generate(w.docs, w.dim, w.zipf_s, w.doc_seed + 1)
+    assert not np.array_equal(ip, ip3)
