@@ -123,3 +123,80 @@ def test_pruned_1m_inputs_follow_their_recipe():
     assert np.array_equal(ip, ip2) and np.array_equal(ix, ix2) and np.array_equal(v, v2)
     ip3, _, _ = datagen.generate(w.docs, w.dim, w.zipf_s, w.doc_seed + 1)
     assert not np.array_equal(ip, ip3)
+
+
+class _FakeTensor:
+    """Just enough of a tensor for the autotuner's host logic (shape, device, .cpu().numpy())."""
+
+    def __init__(self, a):
+        self.a = np.asarray(a)
+        self.shape = self.a.shape
+        self.device = "fake"
+
+    def cpu(self):
+        return self
+
+    def numpy(self):
+        return self.a
+
+
+def test_autotuner_choice_logic(monkeypatch, tmp_path):
+    """The tuner's selection, with a fake index and timer: per window the smallest gamma of the grid that
+    reaches the recall target, then the fastest (mode, block) at that gamma; the cache serves a repeated
+    call; an unreachable target leaves no choice and reports the table."""
+    import types
+
+    import torch
+
+    from paper_2509_08395_gb300 import autotune
+
+    n_q, k = 20, 10
+    truth = np.arange(n_q * k, dtype=np.uint32).reshape(n_q, k)
+    # recall of a (window, gamma): a window of 4096 reaches 0.99 at gamma 300, 8192 already at 200
+    need = {4096: 300, 8192: 200}
+
+    class FakeIndex:
+        def __init__(self, ip, ix, v, dim, window, alpha, value_dtype="f32"):
+            self.window, self.alpha = window, alpha
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            return False
+
+        def search(self, *q, k, gamma, mode="batched", block=0, out=None):
+            if self.alpha == 1.0 and gamma == 0:          # the exact reference
+                return _FakeTensor(truth.view(np.int32)), None
+            ids = truth.copy()
+            if gamma < need[self.window]:
+                ids[:, -1] += 10_000                      # one miss per query: recall 0.9
+            return _FakeTensor(ids.view(np.int32)), None
+
+    speed = {("plain", 0): 100.0, ("batched", 0): 150.0, ("batched", 512): 170.0, ("plain", 512): 90.0}
+
+    def fake_time(idx, q, k_, gamma, mode, block, repeats):
+        return speed[(mode, block)] * (2.0 if idx.window == 8192 else 1.0) / (gamma / 100.0), None
+
+    monkeypatch.setattr(autotune.sindi, "Index", FakeIndex)
+    monkeypatch.setattr(autotune, "_time_search", fake_time)
+    monkeypatch.setattr(torch.cuda, "get_device_properties",
+                        lambda dev: types.SimpleNamespace(name="fake GPU", multi_processor_count=152))
+    q = (_FakeTensor(np.zeros(n_q + 1)), _FakeTensor(np.zeros(1)), _FakeTensor(np.zeros(1)))
+    docs = (_FakeTensor(np.zeros(1001)), _FakeTensor(np.zeros(5)), _FakeTensor(np.zeros(5)))
+    cache = str(tmp_path / "tune.json")
+    res = autotune.autotune(*docs, 64, *q, k=k, alpha=0.5, windows=[4096, 8192], gammas=(100, 200, 300, 500),
+                            blocks=(0, 512), modes=("plain", "batched"), cache=cache)
+    ch = res["choice"]
+    # window 8192 reaches the target at gamma 200: 170 * 2 / 2 = 170 QPS beats window 4096 at gamma 300 (56.7)
+    assert (ch["window"], ch["gamma"], ch["mode"], ch["block"]) == (8192, 200, "batched", 512)
+    assert ch["recall"] == 1.0 and res["gpu"] == "fake GPU"
+    tried = {(r["window"], r["gamma"]) for r in res["table"] if "qps" not in r}
+    assert tried == {(4096, 100), (4096, 200), (4096, 300), (8192, 100), (8192, 200)}
+    monkeypatch.setattr(autotune, "_time_search", lambda *a, **kw: (_ for _ in ()).throw(AssertionError("timed")))
+    again = autotune.autotune(*docs, 64, *q, k=k, alpha=0.5, windows=[4096, 8192], gammas=(100, 200, 300, 500),
+                              blocks=(0, 512), modes=("plain", "batched"), cache=cache)
+    assert again["choice"] == ch                          # served from the cache, nothing timed
+    none = autotune.autotune(*docs, 64, *q, k=k, alpha=0.5, windows=[4096], gammas=(100, 200), blocks=(0,),
+                             modes=("plain",))
+    assert none["choice"] is None and len(none["table"]) == 2
