@@ -200,3 +200,23 @@ def test_autotuner_choice_logic(monkeypatch, tmp_path):
     none = autotune.autotune(*docs, 64, *q, k=k, alpha=0.5, windows=[4096], gammas=(100, 200), blocks=(0,),
                              modes=("plain",))
     assert none["choice"] is None and len(none["table"]) == 2
+
+
+def test_bench_clock_summary(tmp_path):
+    """The clock record of the timed region: median SM clock, the maximum, and the throttle reasons that
+    were active in any sample (nvidia-smi's csv,noheader,nounits rows; unreadable rows are skipped)."""
+    import bench
+
+    path = tmp_path / "clocks.csv"
+    path.write_text(
+        "0, 2070, 2070, 910.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]\n"
+        "0, 2040, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n")
+    c = bench.Clocks.__new__(bench.Clocks)
+    c.proc, c.path = object(), str(path)
+    s = c.summary()
+    assert s == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
+    c2 = bench.Clocks.__new__(bench.Clocks)
+    c2.proc, c2.path = None, str(tmp_path / "none.csv")
+    assert c2.summary()["reasons"] == ["nvidia-smi unavailable"]
