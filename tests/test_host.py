@@ -220,3 +220,23 @@ def test_bench_clock_summary(tmp_path):
     c2 = bench.Clocks.__new__(bench.Clocks)
     c2.proc, c2.path = None, str(tmp_path / "none.csv")
     assert c2.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_bench_hbm_peak_source(tmp_path, monkeypatch):
+    """The roofline's HBM denominator: the measured copy rate when the peaks file has it, else the stated
+    fallback, and the line says which."""
+    import json
+
+    import bench
+
+    good = tmp_path / "peaks.json"
+    good.write_text(json.dumps({"hbm_gbs": 6780.7, "bf16_tflops": 1890.1}))
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(good))
+    assert bench.measured_hbm_peak() == (6780.7, "measured")
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "missing.json"))
+    assert bench.measured_hbm_peak() == (bench.FALLBACK_HBM_GBS, "fallback")
+    bad = tmp_path / "bad.json"
+    bad.write_text("{}")
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(bad))
+    assert bench.measured_hbm_peak()[1] == "fallback"
+    assert bench.FALLBACK_HBM_GBS == 6800.0
