@@ -209,3 +209,46 @@ def test_build_parameter_checks_come_before_any_device_work(lib):
 
     if not torch.cuda.is_available():
         assert build() == sindi.SINDI_ERR_CUDA and out.value is None
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "sindi.h"
+
+int main(void) {
+    sindi_index* idx = NULL;
+    int64_t indptr[3] = {0, 1, 2};
+    int32_t indices[2] = {0, 1};
+    float values[2] = {1.0f, 2.0f};
+    sindi_build_params bad = {0, SINDI_F32, 2.0, SINDI_PRUNE_MASS, 0};   /* alpha out of range */
+    sindi_status s = sindi_build(indptr, indices, values, 2, 4, &bad, NULL, &idx);
+    if (s != SINDI_ERR_INVALID_ARG || idx != NULL || strlen(sindi_last_error()) == 0) return 1;
+    sindi_search_params sp = {10, 0, 1.0, SINDI_MODE_PLAIN, 0};
+    if (sindi_search(NULL, NULL, NULL, NULL, 1, &sp, NULL, NULL, NULL) != SINDI_ERR_INVALID_ARG) return 2;
+    sindi_index_free(NULL);
+    printf("%s\n", sindi_version());
+    return 0;
+}
+"""
+
+
+def test_plain_c_caller(lib, tmp_path):
+    """The header is C (not only C++) and the library links and answers from a C program: argument errors
+    come back as status codes with a message, before any device work."""
+    import shutil
+    import subprocess
+
+    import pytest
+
+    if not shutil.which("gcc"):
+        pytest.skip("needs gcc")
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(lib._name)
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", f"-I{os.path.join(ROOT, 'include')}", str(src),
+                           "-o", str(exe), f"-L{libdir}", "-lsindi", f"-Wl,-rpath,{libdir}"])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.startswith("sindi-gb300")
