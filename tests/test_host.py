@@ -240,3 +240,21 @@ def test_bench_hbm_peak_source(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PEAKS_FILE", str(bad))
     assert bench.measured_hbm_peak()[1] == "fallback"
     assert bench.FALLBACK_HBM_GBS == 6800.0
+
+
+def test_generator_rows_do_not_depend_on_thread_count():
+    """Rows come from a counter-based generator keyed by (seed, row): one thread or many draw the same
+    matrix."""
+    import subprocess
+    import sys
+
+    code = ("import sys, hashlib; sys.path.insert(0, %r); import datagen; "
+            "w = datagen.WORKLOADS['pruned-1m'].scaled(n_docs=30000); ip, ix, v = datagen.docs(w); "
+            "print(hashlib.sha256(ip.tobytes() + ix.tobytes() + v.tobytes()).hexdigest())" % ROOT)
+    out = []
+    for threads in ("1", "8"):
+        env = dict(os.environ, OMP_NUM_THREADS=threads)
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=120)
+        assert r.returncode == 0, r.stderr
+        out.append(r.stdout.strip())
+    assert out[0] == out[1] and len(out[0]) == 64
