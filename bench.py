@@ -56,11 +56,16 @@ def parse():
                    help="add the pruning-method ablation (mass / vector-number / list / mass+list) of the workload")
     p.add_argument("--sparsity-sweep", action="store_true",
                    help="add the uniform-random sparsity sweep (1M docs x d in 10k..100k), autotuned to recall 0.99")
-    p.add_argument("--serve-load", type=float, default=0.5,
-                   help="serving leg: offered load as a fraction of the batched schedule's QPS")
-    p.add_argument("--serve-seconds", type=float, default=4.0)
+    p.add_argument("--serve-seconds", type=float, default=2.0, help="length of each offered load's schedule")
+    p.add_argument("--no-scale", action="store_true",
+                   help="skip the full-size side legs of configs 3-5 (8.8M and 25M documents)")
+    p.add_argument("--scale-steps", type=int, default=3, help="timed graph launches per full-size leg")
+    p.add_argument("--scale-queries", type=int, default=0, help="0 = every query of configs 3-5 (10,000)")
+    p.add_argument("--scale-serve-sweep", default="0.25,0.5,0.75,0.9,1.1",
+                   help="offered loads of config 5's serving leg (fractions of its batched capacity)")
     p.add_argument("--serve-sweep", default=None,
-                   help="comma-separated offered loads (fractions of batched QPS) for the serving leg")
+                   help="comma-separated offered loads (fractions of batched QPS) for the serving leg "
+                        "(default 0.25,0.5,0.75,0.9,1.1)")
     return p.parse_args()
 
 
@@ -203,11 +208,27 @@ def profile_traffic(kernel_src_sha):
     return None
 
 
+def bench_native_lib(name):
+    """Path of a bench helper library (bench_native/build.py builds them), or None if it cannot be built."""
+    import importlib.util
+
+    try:
+        spec = importlib.util.spec_from_file_location("sindi_bench_native_build",
+                                                      os.path.join(ROOT, "bench_native", "build.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        mod.build()
+    except Exception as e:  # noqa: BLE001 - the leg that needs it reports None
+        print(f"bench: bench_native build failed: {e!r}", file=sys.stderr, flush=True)
+    path = os.path.join(ROOT, "bench_native", "lib", name)
+    return path if os.path.exists(path) else None
+
+
 def scatter_peak(window: int, block: int = 512):
     """Measured FP32 shared-memory atomicAdd rate (adds/s) of this GPU: the probe library fills every SM with
     `block`-thread blocks that each add at random slots of a `window`-float shared array, as the scan does."""
-    path = os.path.join(ROOT, "paper_2509_08395_gb300", "lib", "libsindi_probe.so")
-    if not os.path.exists(path):
+    path = bench_native_lib("libsindi_probe.so")
+    if path is None:
         return None
     lib = ctypes.CDLL(path)
     f = lib.sindi_probe_scatter_peak
@@ -314,43 +335,214 @@ def postings_touched(seg, sigma, dim, qp, qx):
 
 
 # ---------------------------------------------------------------------------
-def serve_open_loop(sindi, idx, rows, k, gamma, offered_qps, seconds, seed=7):
-    """Open-loop Poisson arrivals into the continuous-batching server; latency submit -> results on host."""
-    import threading
+class _LoadResult(ctypes.Structure):
+    _fields_ = [("offered_qps", ctypes.c_double), ("achieved_qps", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("requests", ctypes.c_int64), ("failed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("server_p50_ms", ctypes.c_double), ("server_p99_ms", ctypes.c_double),
+                ("lag_p99_ms", ctypes.c_double), ("lag_max_ms", ctypes.c_double)]
 
-    rng = np.random.default_rng(seed)
-    n = max(1, int(offered_qps * seconds))
-    gaps = rng.exponential(1.0 / offered_qps, n)
-    tickets = [None] * n
-    lat = [None] * n
-    with sindi.Server(idx, k=k, gamma=gamma, max_batch=128, max_slots=8, max_wait_us=200) as srv:
-        srv.stats(reset=True)
 
-        def poller():
-            for i in range(n):
-                while tickets[i] is None:
-                    time.sleep(0.0001)
-                res = srv.poll(tickets[i], wait_ms=-1)
-                lat[i] = res[2]
-
-        th = threading.Thread(target=poller)
-        th.start()
-        t0 = time.perf_counter()
-        due = t0
-        for i in range(n):
-            due += gaps[i]
-            while time.perf_counter() < due:
-                pass
-            qi, qv = rows[i % len(rows)]
-            tickets[i] = srv.submit(qi, qv)
-        th.join()
-        wall = time.perf_counter() - t0
+def serve_open_loop(sindi, idx, qp, qx, qv, k, gamma, offered_qps, seconds, seed=7, max_batch=128, slots=8):
+    """Open-loop Poisson arrivals into the continuous-batching server, driven by the native load generator
+    (bench_native/serve_load.c: a submitting thread on the schedule and a polling thread, no GIL). Latency runs
+    from each request's scheduled arrival to its results on the host."""
+    path = bench_native_lib("libsindi_load.so")
+    if path is None:
+        raise RuntimeError("bench_native/lib/libsindi_load.so could not be built")
+    gen = ctypes.CDLL(path)
+    gen.sindi_load_open_loop.restype = ctypes.c_int
+    gen.sindi_load_open_loop.argtypes = [ctypes.c_void_p] * 6 + [ctypes.c_int64, ctypes.c_uint32, ctypes.c_double,
+                                                                 ctypes.c_double, ctypes.c_uint64,
+                                                                 ctypes.POINTER(_LoadResult)]
+    lib = sindi.load()
+    submit = ctypes.cast(lib.sindi_server_submit, ctypes.c_void_p)
+    poll = ctypes.cast(lib.sindi_server_poll, ctypes.c_void_p)
+    qp = np.ascontiguousarray(qp, np.int64)
+    qx = np.ascontiguousarray(qx, np.int32)
+    qv = np.ascontiguousarray(qv, np.float32)
+    res = _LoadResult()
+    with sindi.Server(idx, k=k, gamma=gamma, max_batch=max_batch, max_slots=slots, max_wait_us=200,
+                      max_query_nnz=int(np.diff(qp).max())) as srv:
+        rc = gen.sindi_load_open_loop(ctypes.c_void_p(srv.handle), submit, poll, qp.ctypes.data, qx.ctypes.data,
+                                      qv.ctypes.data, len(qp) - 1, k, float(offered_qps), float(seconds), seed,
+                                      ctypes.byref(res))
         st = srv.stats()
-    l = np.array(lat)
-    return {"offered_qps": offered_qps, "achieved_qps": n / wall, "requests": n,
-            "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99)),
-            "max_ms": float(l.max()), "mean_batch": st["mean_batch"], "slots": st["n_slots"],
-            "peak_in_flight": st["peak_in_flight"]}
+    if rc != 0:
+        raise RuntimeError("sindi_load_open_loop refused its arguments")
+    out = {f: getattr(res, f) for f, _ in _LoadResult._fields_}
+    out.update({"mean_batch": st["mean_batch"], "slots": st["n_slots"], "peak_in_flight": st["peak_in_flight"],
+                "max_batch": max_batch, "latency_from": "scheduled arrival (open loop)"})
+    return out
+
+
+def serve_sweep(sindi, idx, qp, qx, qv, k, gamma, capacity_qps, fractions, seconds):
+    """Offered loads as fractions of the batched schedule's measured capacity, up to and past saturation."""
+    return [serve_open_loop(sindi, idx, qp, qx, qv, k, gamma, f * capacity_qps, seconds, seed=7 + i)
+            for i, f in enumerate(fractions)]
+
+
+# ---------------------------------------------------------------------------
+# Configs 3-5 of the workload list at full size (side legs of the default run)
+def _fp64_truth(D, Q, rows, k):
+    """FP64 exact top-k (Definition 3) of the sampled query rows, one row per host thread (the oracle's C calls
+    release the GIL)."""
+    import concurrent.futures
+
+    import oracle
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        res = list(ex.map(lambda r: oracle.brute_force(D, Q, r, k), rows))
+    return dict(zip(rows, res))
+
+
+def _recall_vs_fp64(ids, truth, D, Q):
+    import oracle
+
+    plain = [oracle.recall(ids[r], t[0]) for r, t in truth.items()]
+    tie = [oracle.recall_tie_aware(ids[r], t[0], t[1], D, Q, r) for r, t in truth.items()]
+    return float(np.mean(plain)), float(np.mean(tie))
+
+
+def _score_errors(idx, torch, dev, w, ip, ix, v, qp, qx, qv, D, Q, rows, final_ids, final_sc):
+    """Max relative score error against FP64 on sampled rows: coarse (the GPU's gamma = 0 scores, quantised
+    postings, against the FP64 dot product of the same document's alpha-mass subvector with the query) and
+    final (the reordered FP32 scores against exact delta)."""
+    import oracle
+
+    sub = [torch.from_numpy(a).to(dev) for a in (np.concatenate([[0], np.cumsum([qp[r + 1] - qp[r] for r in rows])]),
+                                                  np.concatenate([qx[qp[r]:qp[r + 1]] for r in rows]),
+                                                  np.concatenate([qv[qp[r]:qp[r + 1]] for r in rows]))]
+    cids, csc = idx.search(*sub, k=w.k, gamma=0, mode="batched")
+    cids, csc = cids.cpu().numpy().view(np.uint32), csc.cpu().numpy()
+    ce = fe = 0.0
+    for n, r in enumerate(rows):
+        qd = dict(zip(qx[qp[r]:qp[r + 1]].tolist(), qv[qp[r]:qp[r + 1]].astype(np.float64).tolist()))
+        for i, sc in zip(cids[n], csc[n]):
+            a, b = ip[i], ip[i + 1]
+            pos = oracle.alpha_mass(ix[a:b], v[a:b], w.alpha)
+            ref = sum(qd.get(int(j), 0.0) * float(x) for j, x in zip(ix[a:b][pos], v[a:b][pos]))
+            if ref != 0.0:
+                ce = max(ce, abs(float(sc) - ref) / abs(ref))
+        for i, sc in zip(final_ids[r], final_sc[r]):
+            ex = oracle.inner_product(D, int(i), Q, r)
+            if ex != 0.0:
+                fe = max(fe, abs(float(sc) - ex) / abs(ex))
+    return {"coarse_max_rel_err_vs_fp64": ce, "final_max_rel_err_vs_fp64": fe, "queries": len(rows)}
+
+
+def plan_leg(sindi, torch, dev, w, dd, qp, qx, qv, dtype, steps, warmup, flush, stream, D, Q, truth, host_docs):
+    """One config at full size: build, then every query of the batch in one graph launch (sindi_plan), timed with
+    CUDA events on the launching stream; recall@k against FP64 on the sampled rows of `truth`."""
+    ip, ix, v = host_docs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    idx = sindi.Index(*dd, w.dim, window=w.window, alpha=w.alpha, value_dtype=dtype)
+    torch.cuda.synchronize()
+    build_ms = 1000 * (time.perf_counter() - t0)
+    try:
+        q_dev = [torch.from_numpy(a).to(dev) for a in (qp, qx, qv)]
+        nq = len(qp) - 1
+        with sindi.Plan(idx, *q_dev, k=w.k, gamma=w.gamma) as plan:
+            for _ in range(warmup):
+                plan.launch(stream.cuda_stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                e0.record(stream)
+                plan.launch(stream.cuda_stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            idx.check()
+            ids = plan.out[0].cpu().numpy().view(np.uint32)
+            sc = plan.out[1].cpu().numpy()
+        step_ms = float(np.mean(ms))
+        info = idx.info
+        seg = idx.export(parts=("seg",))["seg"]
+        touched = postings_touched(seg, info["n_windows"], w.dim, qp, qx)
+        vbytes = {0: 4, 1: 2, 2: 1}[info["value_dtype"]]
+        scan_bytes = float(touched.sum() * (2 + vbytes) + np.diff(qp).sum() * (info["n_windows"] * 8 + 8))
+        recall, recall_tie = _recall_vs_fp64(ids, truth, D, Q)
+        errs = _score_errors(idx, torch, dev, w, ip, ix, v, qp, qx, qv, D, Q, sorted(truth)[:4], ids, sc)
+        out = {"workload": w.name, "posting_dtype": dtype, "n_docs": w.docs.n_rows, "dim": w.dim, "queries": nq,
+               "k": w.k, "gamma": w.gamma, "alpha": w.alpha, "window": info["window"],
+               "n_windows": info["n_windows"], "postings": info["postings"], "build_ms": build_ms,
+               "qps": nq / (step_ms / 1000.0), "ms_per_step": step_ms, "steps": steps,
+               "schedule": "batched, one graph launch per step (sindi_plan)",
+               "recall_at_k_vs_fp64": recall, "recall_at_k_tie_aware_vs_fp64": recall_tie,
+               "recall_sample": f"{len(truth)} queries evenly spread, FP64 oracle brute force",
+               "postings_per_query": float(touched.mean()),
+               "scan_bytes_per_s": scan_bytes / (step_ms / 1000.0),
+               "scan_bytes_basis": "posting bytes (id + value) of every query's lists plus offsets, per step "
+                                   "time (lists shared by queries are read once from HBM and served from L2)",
+               "adds_per_s": float(touched.sum()) / (step_ms / 1000.0)}
+        out.update(errs)
+        return out, idx
+    except Exception:
+        idx.close()
+        raise
+
+
+def scale_legs(sindi, torch, dev, args, flush, stream, base_qps_fn=None):
+    """Configs 3 (batched, 8.8M docs, 10k uneven queries), 4 (FP16 / FP8 postings on that index, gamma 1,000)
+    and 5 (25M docs x 250k dims, FP16, open-loop serving) at full size."""
+    import oracle
+
+    out = {}
+    n_truth = 16
+    # configs 3 and 4 share their 8.8M documents
+    w3, w4 = datagen.WORKLOADS["batched-8.8m"], datagen.WORKLOADS["lowprec-8.8m"]
+    t0 = time.perf_counter()
+    ip, ix, v = datagen.docs(w3)
+    gen_s = time.perf_counter() - t0
+    dd = [torch.from_numpy(a).to(dev) for a in (ip, ix, v)]
+    D = oracle.Dataset(ip, ix, v, w3.dim)
+    for w, dtypes in ((w3, ("f32",)), (w4, ("f16", "f8"))):
+        qp, qx, qv = datagen.queries(w)
+        if args.scale_queries:
+            n = min(args.scale_queries, len(qp) - 1)
+            qp, qx, qv = qp[: n + 1], qx[: qp[n]], qv[: qp[n]]
+        Q = oracle.Dataset(qp, qx, qv, w.dim)
+        rows = list(range(0, Q.n, max(1, Q.n // n_truth)))[:n_truth]
+        truth = _fp64_truth(D, Q, rows, w.k)
+        for dt in dtypes:
+            leg, idx = plan_leg(sindi, torch, dev, w, dd, qp, qx, qv, dt, args.scale_steps, 1, flush, stream, D, Q,
+                                truth, (ip, ix, v))
+            idx.close()
+            leg["docs_generated_s"] = gen_s
+            out[f"{w.name}/{dt}"] = leg
+    del dd, D
+    torch.cuda.empty_cache()
+    # config 5: 25M documents, FP16 postings; batched capacity, then open-loop serving up to saturation
+    w5 = datagen.WORKLOADS["serve-25m"]
+    t0 = time.perf_counter()
+    ip, ix, v = datagen.docs(w5)
+    gen_s = time.perf_counter() - t0
+    dd = [torch.from_numpy(a).to(dev) for a in (ip, ix, v)]
+    D = oracle.Dataset(ip, ix, v, w5.dim)
+    qp, qx, qv = datagen.queries(w5)
+    if args.scale_queries:
+        n = min(args.scale_queries, len(qp) - 1)
+        qp, qx, qv = qp[: n + 1], qx[: qp[n]], qv[: qp[n]]
+    Q = oracle.Dataset(qp, qx, qv, w5.dim)
+    rows = list(range(0, Q.n, max(1, Q.n // 8)))[:8]
+    truth = _fp64_truth(D, Q, rows, w5.k)
+    leg, idx = plan_leg(sindi, torch, dev, w5, dd, qp, qx, qv, w5.value_dtype, args.scale_steps, 1, flush, stream,
+                        D, Q, truth, (ip, ix, v))
+    del dd
+    try:
+        leg["docs_generated_s"] = gen_s
+        fractions = [float(f) for f in args.scale_serve_sweep.split(",")]
+        leg["serving"] = {"capacity_qps": leg["qps"], "capacity_from": "the batched plan leg above",
+                          "points": serve_sweep(sindi, idx, qp, qx, qv, w5.k, w5.gamma, leg["qps"], fractions,
+                                                args.serve_seconds)}
+    finally:
+        idx.close()
+    out[f"{w5.name}/{w5.value_dtype}"] = leg
+    return out
 
 
 def cpu_oracle_sample(w, ip, ix, v, qp, qx, qv, budget_s, gpu_ids=None, k=None):
@@ -671,15 +863,12 @@ def main():
 
     serving = None
     if rank == 0 and (args.serve_sweep or not args.no_forms):
-        rows = [(qx[qp[r]:qp[r + 1]], qv[qp[r]:qp[r + 1]]) for r in range(nq)]
         base = value if args.mode == "batched" else forms.get("batched", {}).get("qps", value)
+        fractions = [float(f) for f in (args.serve_sweep or "0.25,0.5,0.75,0.9,1.1").split(",")]
         try:
-            if args.serve_sweep:
-                serving = [serve_open_loop(sindi, idx, rows, w.k, w.gamma, float(f) * base, args.serve_seconds)
-                           for f in args.serve_sweep.split(",")]
-            else:
-                serving = serve_open_loop(sindi, idx, rows, w.k, w.gamma, args.serve_load * base,
-                                          args.serve_seconds)
+            serving = {"capacity_qps": base, "capacity_from": "batched schedule of the main leg",
+                       "points": serve_sweep(sindi, idx, qp, qx, qv, w.k, w.gamma, base, fractions,
+                                             args.serve_seconds)}
         except Exception as e:  # noqa: BLE001 - reported in the line
             side_failed("serving", e)
 

@@ -130,6 +130,16 @@ typedef struct {
                               that overlaps the scatter-add of one window with
                               the cut of the previous (lambda <= 16384; larger
                               windows take the default)                         */
+    uint32_t group;        /* batched schedule: queries per scan block, 0..8. One
+                              block owns a window for a group of this many queries
+                              (their score windows side by side in shared memory)
+                              and loads each posting of a list segment I_{j,w} once
+                              for every query of the group that holds term j.
+                              0 or 1 = one block per (query, window), the default.
+                              A value larger than shared memory holds (its group's
+                              windows and 36 KiB of tables within 207 KiB) is
+                              reduced to what fits. Ignored by the plain schedule
+                              and by SINDI_SCAN_PIPELINED                         */
 } sindi_search_params;
 
 typedef struct {
@@ -222,10 +232,15 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
  *   no cudaMalloc, no pool, no staging.
  *   Arguments and results are those of sindi_search, except that the queries
  *   and both outputs must be device memory (SINDI_ERR_INVALID_ARG otherwise).
- *   A search whose working memory for one query exceeds the array (about
- *   n_windows * min(max(gamma, k), window) * 8 bytes) returns
- *   SINDI_ERR_UNSUPPORTED with the sizes in sindi_last_error(). Batched mode
- *   processes as many queries per launch group as fit.
+ *   A search whose working memory for one query exceeds the array returns
+ *   SINDI_ERR_UNSUPPORTED with the sizes in sindi_last_error(). One query
+ *   needs, with g = min(gamma (k when gamma = 0), n_docs) and each term
+ *   rounded up to 256 bytes: 16,404 bytes of counters and histogram, plus
+ *   n_windows * 2 * min(g, window) * 8 bytes of window candidates, plus
+ *   f * 8 bytes of merge filter (f = the smallest power of two >= 4096 and
+ *   >= 2 g, at most 16384), plus 2 * g * 8 bytes of reorder keys (16 bytes
+ *   when gamma = 0). Batched mode processes as many queries per launch group
+ *   as fit.
  *   The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress, with that device current) and keeps it; make that
  *   first call before any stream capture.
@@ -247,8 +262,11 @@ sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_ind
  *   the caller may change their contents between launches, but not their
  *   addresses, n_queries or the total number of query entries beyond what the
  *   buffers hold. Device pointers only; 1 <= n_queries <= 65535.
- *   The plan owns its workspace (allocated here). Launches of one plan must
- *   not overlap each other on the GPU. The index must outlive the plan.
+ *   The plan owns its workspace (allocated here, at most 4 GiB or what one
+ *   query needs: a batch whose working memory exceeds that is recorded as
+ *   several launch groups that reuse it, still replayed by one graph launch).
+ *   Launches of one plan must not overlap each other on the GPU. The index
+ *   must outlive the plan.
  */
 typedef struct sindi_plan sindi_plan;
 sindi_status sindi_plan_create(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,

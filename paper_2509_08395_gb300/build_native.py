@@ -1,5 +1,4 @@
-"""Compiles the CUDA sources of this package into ``lib/libsindi.so`` (sm_103a only), and the
-measurement probe (``probe/*.cu``) into ``lib/libsindi_probe.so``.
+"""Compiles the CUDA sources of this package into ``lib/libsindi.so`` (sm_103a only).
 
 Each ``csrc/*.cu`` file is compiled to an object in parallel, then nvcc links
 the shared library with the CUDA runtime linked statically, so the library
@@ -22,8 +21,6 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsindi.so")
-PROBE_SRC = os.path.join(HERE, "probe")
-PROBE_LIB = os.path.join(LIBDIR, "libsindi_probe.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -87,15 +84,6 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
             sys.stderr.write(p.stdout + p.stderr)
             raise RuntimeError("link failed: " + " ".join(cmd))
         os.replace(tmp, LIB)
-    probes = sorted(glob.glob(os.path.join(PROBE_SRC, "*.cu")))
-    if probes and (force or _stale(PROBE_LIB, probes)):
-        tmp = PROBE_LIB + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, *NVCC_FLAGS, "-shared", "-cudart", "static", *probes, "-o", tmp]
-        p = subprocess.run(cmd, capture_output=True, text=True)
-        if p.returncode != 0:
-            sys.stderr.write(p.stdout + p.stderr)
-            raise RuntimeError("probe build failed: " + " ".join(cmd))
-        os.replace(tmp, PROBE_LIB)
     return LIB
 
 

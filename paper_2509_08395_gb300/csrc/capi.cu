@@ -356,8 +356,8 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
     const sindi_search_params prm = *params;
     if (prm.k < 1 || prm.k > kMaxK || (prm.gamma != 0 && (prm.gamma < prm.k || prm.gamma > kMaxGamma)) ||
         !(prm.beta > 0.0 && prm.beta <= 1.0) || prm.mode > SINDI_MODE_BATCHED ||
-        !valid_block_threads(prm.block_threads)) {
-        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; block_threads 0, 1 (pipelined), 256, 512 or 1024");
+        !valid_block_threads(prm.block_threads) || prm.group > kMaxQueryGroup) {
+        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; block_threads 0, 1 (pipelined), 256, 512 or 1024; group 0..8");
         return SINDI_ERR_INVALID_ARG;
     }
 
@@ -470,8 +470,8 @@ sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_ind
     const sindi_search_params prm = *params;
     if (prm.k < 1 || prm.k > kMaxK || (prm.gamma != 0 && (prm.gamma < prm.k || prm.gamma > kMaxGamma)) ||
         !(prm.beta > 0.0 && prm.beta <= 1.0) || prm.mode > SINDI_MODE_BATCHED ||
-        !valid_block_threads(prm.block_threads)) {
-        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; block_threads 0, 1 (pipelined), 256, 512 or 1024");
+        !valid_block_threads(prm.block_threads) || prm.group > kMaxQueryGroup) {
+        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; block_threads 0, 1 (pipelined), 256, 512 or 1024; group 0..8");
         return SINDI_ERR_INVALID_ARG;
     }
     if (prm.beta < 1.0) {

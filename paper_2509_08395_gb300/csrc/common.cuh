@@ -132,4 +132,7 @@ inline bool valid_block_threads(uint32_t b) {
     return b == 0 || b == SINDI_SCAN_PIPELINED || b == 256 || b == 512 || b == 1024;
 }
 
+// sindi_search_params.group: queries per block of the batched scan, 0 (default) .. kMaxQueryGroup.
+constexpr uint32_t kMaxQueryGroup = 8;
+
 }  // namespace sindi

@@ -2,6 +2,7 @@
 // query batch recorded once as a CUDA graph, then replayed with one launch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -10,6 +11,8 @@
 #include "nvtx.cuh"
 
 namespace sindi {
+
+constexpr size_t kPlanWorkspaceBudget = (size_t)4 << 30;  // device bytes of a plan's working memory
 
 struct Plan {
     const IndexImpl* ix = nullptr;
@@ -55,8 +58,8 @@ sindi_status sindi_plan_create(const sindi_index* index, const int64_t* q_indptr
     sindi_search_params prm = *params;
     if (prm.k < 1 || prm.k > kMaxK || (prm.gamma != 0 && (prm.gamma < prm.k || prm.gamma > kMaxGamma)) ||
         !(prm.beta > 0.0 && prm.beta <= 1.0) ||
-        !valid_block_threads(prm.block_threads)) {
-        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; block_threads 0, 1 (pipelined), 256, 512 or 1024");
+        !valid_block_threads(prm.block_threads) || prm.group > kMaxQueryGroup) {
+        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; block_threads 0, 1 (pipelined), 256, 512 or 1024; group 0..8");
         return SINDI_ERR_INVALID_ARG;
     }
     if (prm.beta < 1.0) {
@@ -77,7 +80,10 @@ sindi_status sindi_plan_create(const sindi_index* index, const int64_t* q_indptr
     try {
         configure_search_kernels(ix.device);
         const uint64_t launches0 = ix.launches.load(), scans0 = ix.scan_launches.load();
-        P.ws_bytes = search_workspace_bytes(ix, prm, n_queries);
+        // the whole batch in one launch group when its working memory fits the budget; otherwise the
+        // graph holds several launch groups that reuse one workspace (still one graph launch per run)
+        const size_t one = search_workspace_bytes(ix, prm, 1);
+        P.ws_bytes = std::min(search_workspace_bytes(ix, prm, n_queries), std::max(one, kPlanWorkspaceBudget));
         SINDI_CUDA(cudaMalloc(&P.ws, P.ws_bytes));
         SINDI_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
         SINDI_CUDA(cudaStreamBeginCapture(P.capture_stream, cudaStreamCaptureModeThreadLocal));

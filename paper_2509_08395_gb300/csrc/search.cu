@@ -110,6 +110,11 @@ static Workspace carve_workspace(unsigned char* base, int64_t c, uint32_t cand_c
     return w;
 }
 
+// Floats a window array takes in shared memory: lambda rounded up to 4, so
+// that every window starts 16-byte aligned and the cut reads it 4 slots at a
+// time (the slots past lambda stay zero and are never candidates).
+__host__ __device__ __forceinline__ uint32_t window_stride(uint32_t lambda) { return (lambda + 3u) & ~3u; }
+
 template <int DT>
 __device__ __forceinline__ float load_value(const void* pval, uint32_t p) {
     if (DT == SINDI_F32) {
@@ -182,43 +187,44 @@ __device__ __forceinline__ int term_of(const uint32_t* pre, int n, uint32_t f) {
 
 // One warp chunk of one query term's list in one window, in registers: the
 // lane's postings are q0 + u (a long list) or q0 + 32 u (a short one), u <
-// kChunkU, those in [ps, pe) counted.
+// kChunkU; bit u of lm is set for those inside the segment.
 struct Chunk {
     uint32_t id2[kChunkU / 2];  // window ids, two per word (low half first)
     float v[kChunkU];
-    uint32_t q0, ps, pe;
+    uint32_t lm;
     float wq;
 };
 
-// Loads chunk c. A list of at least kVecMin postings is tiled on 8-aligned
+// Loads the chunk at offset `off` (a multiple of kChunkLen) of the segment
+// [ps, pe). A segment of at least kVecMin postings is tiled on 8-aligned
 // groups, lane l owning the 8 consecutive postings of the chunk's l-th group
-// (one vector load of ids, one or two of values); a shorter list (always a
+// (one vector load of ids, one or two of values); a shorter segment (always a
 // single chunk) keeps the lanes interleaved, which keeps more of them busy.
+// These are the positions the build's bank-aware order is laid out for.
 template <int DT>
-__device__ __forceinline__ void load_chunk(const DevIndex& ix, const uint32_t* t_start, const uint32_t* t_end,
-                                           const float* t_w, const uint32_t* c_pre, const uint16_t* c_term,
-                                           int nc, uint32_t c, int lane, Chunk& k) {
-    const int t = c < (uint32_t)kChunkTable ? (int)c_term[c] : term_of(c_pre, nc, c);
-    k.ps = t_start[t];
-    k.pe = t_end[t];
-    k.wq = t_w[t];
-    const uint32_t off = (c - c_pre[t]) * (uint32_t)kChunkLen;
+__device__ __forceinline__ void load_segment_chunk(const DevIndex& ix, uint32_t ps, uint32_t pe, uint32_t off,
+                                                   int lane, Chunk& k) {
 #pragma unroll
     for (int u = 0; u < kChunkU; u++) k.v[u] = 0.0f;
 #pragma unroll
     for (int u = 0; u < kChunkU / 2; u++) k.id2[u] = 0;
-    if (k.pe - k.ps >= kVecMin) {
-        k.q0 = (k.ps & ~7u) + off + (uint32_t)lane * kChunkU;
-        if (k.q0 < k.pe) {
-            load_ids8(ix.pid, k.q0, k.id2);
-            load_values8<DT>(ix.pval, k.q0, k.v);
+    if (pe - ps >= kVecMin) {
+        const uint32_t q0 = (ps & ~7u) + off + (uint32_t)lane * kChunkU;
+        const uint32_t lo = ps > q0 ? ps - q0 : 0u;  // < 8: only the segment's first group
+        const uint32_t hi = pe > q0 ? min(pe - q0, (uint32_t)kChunkU) : 0u;
+        k.lm = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+        if (k.lm) {
+            load_ids8(ix.pid, q0, k.id2);
+            load_values8<DT>(ix.pval, q0, k.v);
         }
     } else {
-        k.q0 = k.ps + off + (uint32_t)lane;
+        const uint32_t q0 = ps + (uint32_t)lane;
+        const uint32_t n = pe > q0 ? min((pe - q0 + 31u) >> 5, (uint32_t)kChunkU) : 0u;
+        k.lm = (1u << n) - 1u;
 #pragma unroll
         for (int u = 0; u < kChunkU; u++) {
-            const uint32_t p = k.q0 + 32u * u;
-            if (p < k.pe) {
+            const uint32_t p = q0 + 32u * u;
+            if (p < pe) {
                 k.id2[u >> 1] |= (uint32_t)__ldg(ix.pid + p) << (16 * (u & 1));
                 k.v[u] = load_value<DT>(ix.pval, p);
             }
@@ -226,13 +232,31 @@ __device__ __forceinline__ void load_chunk(const DevIndex& ix, const uint32_t* t
     }
 }
 
+// Loads chunk c of a term table (chunks of all its terms, in term order).
+template <int DT>
+__device__ __forceinline__ void load_chunk(const DevIndex& ix, const uint32_t* t_start, const uint32_t* t_end,
+                                           const float* t_w, const uint32_t* c_pre, const uint16_t* c_term,
+                                           int nc, uint32_t c, int lane, Chunk& k) {
+    const int t = c < (uint32_t)kChunkTable ? (int)c_term[c] : term_of(c_pre, nc, c);
+    k.wq = t_w[t];
+    load_segment_chunk<DT>(ix, t_start[t], t_end[t], (c - c_pre[t]) * (uint32_t)kChunkLen, lane, k);
+}
+
+__device__ __forceinline__ uint32_t chunk_slot(const Chunk& k, int u) {
+    return (k.id2[u >> 1] >> (16 * (u & 1))) & 0xFFFFu;
+}
+
+// Adds a chunk with shared-memory atomics (segments of different terms may
+// run at once and meet on a slot).
 __device__ __forceinline__ void add_chunk(float* A, const Chunk& k) {
-    const uint32_t step = k.pe - k.ps >= kVecMin ? 1u : 32u;
 #pragma unroll
-    for (int u = 0; u < kChunkU; u++) {
-        const uint32_t p = k.q0 + step * u;
-        if (p >= k.ps && p < k.pe) atomicAdd(&A[(k.id2[u >> 1] >> (16 * (u & 1))) & 0xFFFFu], k.wq * k.v[u]);
-    }
+    for (int u = 0; u < kChunkU; u++)
+        if (k.lm & (1u << u)) atomicAdd(&A[chunk_slot(k, u)], k.wq * k.v[u]);
+}
+
+// Chunks of a segment of at least kVecMin postings.
+__device__ __forceinline__ uint32_t long_segment_chunks(uint32_t ps, uint32_t pe) {
+    return (((pe + 7u) & ~7u) - (ps & ~7u) + kChunkLen - 1) / kChunkLen;
 }
 
 // Block-wide: the bin holding the g-th largest element of a BINS-bin
@@ -380,6 +404,16 @@ __device__ __forceinline__ void accumulate_table(const DevIndex& ix, const uint3
     }
 }
 
+// The least float whose order key is at least k: a slot's key is >= k
+// exactly when its score is >= this value. -inf when every float's key is
+// (k at or below the key of -inf); a NaN, which compares false with
+// everything, when no finite float's key reaches k.
+__device__ __forceinline__ float key_floor_float(uint32_t k) {
+    if (k <= 0x007FFFFFu) return -INFINITY;
+    if (k > 0xFF800000u) return __int_as_float(0x7FC00000);
+    return order_bits_float(k);
+}
+
 // The cut of one accumulated window w of query row y: emits into the query's
 // candidate list every slot that can still be among its best g, and adds what
 // it emitted to the query's histogram H (ids >= N are not candidates).
@@ -416,15 +450,38 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
         const unsigned lt = (1u << lane) - 1u;
         const uint32_t share = stage_cap / NW;
         uint64_t* mine_st = stage + (size_t)warp * share;
-        uint32_t cnt = 0;
-        for (int base = warp * 32; base < n_eff; base += NT) {
-            const int i = base + lane;
-            const bool ok = i < n_eff && (float_order_bits(A[i]) >> (32 - kHistBits)) >= pbin;
-            const unsigned bal = __ballot_sync(kFull, ok);
-            const uint32_t at = cnt + (uint32_t)__popc(bal & lt);
-            if (ok && at < share) mine_st[at] = key_of(i);
-            cnt += (uint32_t)__popc(bal);
-        }
+        // the window 4 slots per lane (one 16-byte load, one compare each against
+        // the least score in bin pbin); the per-slot work runs only for the rare
+        // 128-slot spans that hold a candidate
+        const float thr = key_floor_float(pbin << (32 - kHistBits));
+        const int n4 = (n_eff + 3) >> 2;
+        const float4* A4 = reinterpret_cast<const float4*>(A);
+        auto scan_bounded = [&](auto&& emit) -> uint32_t {
+            uint32_t cnt = 0;
+            for (int b4 = warp * 32; b4 < n4; b4 += NT) {
+                const int i4 = b4 + lane;
+                uint32_t m = 0;
+                if (i4 < n4) {
+                    const float4 x = A4[i4];
+                    m = (x.x >= thr ? 1u : 0u) | (x.y >= thr ? 2u : 0u) | (x.z >= thr ? 4u : 0u) |
+                        (x.w >= thr ? 8u : 0u);
+                    const int rem = n_eff - 4 * i4;
+                    if (rem < 4) m &= (1u << rem) - 1u;
+                }
+                if (!__any_sync(kFull, m != 0u)) continue;
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const bool ok = (m >> c) & 1u;
+                    const unsigned bal = __ballot_sync(kFull, ok);
+                    if (ok) emit(4 * i4 + c, cnt + (uint32_t)__popc(bal & lt));
+                    cnt += (uint32_t)__popc(bal);
+                }
+            }
+            return cnt;
+        };
+        const uint32_t cnt = scan_bounded([&](int i, uint32_t at) {
+            if (at < share) mine_st[at] = key_of(i);
+        });
         if (lane == 0) warp_off[warp] = cnt;
         S::sync();
         if (tid == 0) {
@@ -453,20 +510,12 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
                 }
             } else {
                 // a warp had more slots than its share: read the window again
-                uint32_t at = at0;
-                for (int base = warp * 32; base < n_eff; base += NT) {
-                    const int i = base + lane;
-                    const uint32_t bin = i < n_eff ? float_order_bits(A[i]) >> (32 - kHistBits) : 0u;
-                    const bool ok = i < n_eff && bin >= pbin;
-                    const unsigned bal = __ballot_sync(kFull, ok);
-                    if (ok) {
-                        const uint32_t pos = at + (uint32_t)__popc(bal & lt);
-                        if (pos < a.ws.cand_cap) cand[pos] = key_of(i);
-                        else atomicOr(ix.err, kErrCandOverflow);
-                        atomicAdd(H + bin, 1u);
-                    }
-                    at += (uint32_t)__popc(bal);
-                }
+                (void)scan_bounded([&](int i, uint32_t at) {
+                    const uint64_t key = key_of(i);
+                    if (at0 + at < a.ws.cand_cap) cand[at0 + at] = key;
+                    else atomicOr(ix.err, kErrCandOverflow);
+                    atomicAdd(H + (uint32_t)(key >> kKeyBinShift), 1u);
+                });
             }
             S::sync();  // warp_off, st and the staging area are reused by the caller's next cut
             return;
@@ -477,9 +526,28 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
     // private histogram of the 256 bins below the window's top bin (no
     // contention between warps); the window histogram is their sum. When the
     // cut falls below that range, a full 4096-bin histogram is used instead.
+    // the slot passes below read 4 slots per thread (thread t: slots 4 (t + k NT) .. + 3),
+    // and a warp's slots are the same in every pass
     uint32_t* priv = reinterpret_cast<uint32_t*>(cs.region) + warp * kRelBins;
+    const int n4w = (n_eff + 3) >> 2;
+    const float4* A4w = reinterpret_cast<const float4*>(A);
+    auto slots4 = [&](int i4, float v[4]) -> uint32_t {  // the group's scores; bit c: slot 4 i4 + c < n_eff
+        const float4 x = A4w[i4];
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+        const int rem = n_eff - 4 * i4;
+        return rem >= 4 ? 15u : (1u << rem) - 1u;
+    };
     uint32_t top_key = 0;
-    for (int i = tid; i < n_eff; i += NT) top_key = max(top_key, float_order_bits(A[i]));
+    for (int i4 = tid; i4 < n4w; i4 += NT) {
+        float v[4];
+        const uint32_t ok = slots4(i4, v);
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            if (ok & (1u << c)) top_key = max(top_key, float_order_bits(v[c]));
+    }
     top_key = __reduce_max_sync(kFull, top_key);
     if (lane == 0) red[warp] = top_key;
     for (int b = tid; b < kSubBins; b += NT) hist2[b] = 0;
@@ -492,9 +560,16 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
     for (int b = lane; b < kRelBins; b += 32) priv[b] = 0;
     S::sync();
     const uint32_t top_bin = st[0] >> (32 - kHistBits);
-    for (int i = tid; i < n_eff; i += NT) {
-        const uint32_t rel = top_bin - (float_order_bits(A[i]) >> (32 - kHistBits));
-        atomicAdd(&priv[rel < (uint32_t)kRelBins ? rel : kRelBins - 1], 1u);
+    for (int i4 = tid; i4 < n4w; i4 += NT) {
+        float v[4];
+        const uint32_t ok = slots4(i4, v);
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            if (ok & (1u << c)) {
+                const uint32_t rel = top_bin - (float_order_bits(v[c]) >> (32 - kHistBits));
+                atomicAdd(&priv[rel < (uint32_t)kRelBins ? rel : kRelBins - 1], 1u);
+            }
+        }
     }
     S::sync();
     for (int b = tid; b < kRelBins; b += NT) {
@@ -559,12 +634,25 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
         S::sync();  // the private histograms are dead from here on
         uint32_t at = warp_off[warp];
         const unsigned lt = (1u << lane) - 1u;
-        for (int base = warp * 32; base < n_eff; base += NT) {
-            const int i = base + lane;
-            const bool ok = i < n_eff && (float_order_bits(A[i]) >> (32 - kHistBits)) >= lo;
-            const unsigned bal = __ballot_sync(kFull, ok);
-            if (ok) stage[at + __popc(bal & lt)] = key_of(i);
-            at += __popc(bal);
+        const float thr_lo = key_floor_float(lo << (32 - kHistBits));
+        for (int b4 = warp * 32; b4 < n4w; b4 += NT) {
+            const int i4 = b4 + lane;
+            uint32_t m = 0;
+            if (i4 < n4w) {
+                float v[4];
+                const uint32_t ok = slots4(i4, v);
+#pragma unroll
+                for (int c = 0; c < 4; c++) m |= (v[c] >= thr_lo ? 1u : 0u) << c;
+                m &= ok;
+            }
+            if (!__any_sync(kFull, m != 0u)) continue;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const bool ok = (m >> c) & 1u;
+                const unsigned bal = __ballot_sync(kFull, ok);
+                if (ok) stage[at + __popc(bal & lt)] = key_of(4 * i4 + c);
+                at += __popc(bal);
+            }
         }
         S::sync();
         n_src = cs.s_staged[0];
@@ -675,7 +763,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     const int64_t qb = a.q_indptr[r];
     const int nt = (int)(a.q_indptr[r + 1] - qb);
 
-    for (uint32_t m = threadIdx.x; m < lambda; m += kScanThreads) A[m] = 0.0f;
+    {
+        float4* A4 = reinterpret_cast<float4*>(A);
+        for (uint32_t m = threadIdx.x; m < window_stride(lambda) / 4; m += kScanThreads)
+            A4[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 
     for (int c0 = 0; c0 < nt; c0 += kTermChunk) {
         const int nc = min(kTermChunk, nt - c0);
@@ -740,7 +832,7 @@ __device__ __forceinline__ void named_arrive(int id) {
 }
 
 static size_t pipe_smem_bytes(uint32_t lambda) {
-    return (((size_t)8 * lambda + 15) & ~(size_t)15) + 2 * (size_t)kPipeTableBytes + kPipeRegionBytes;
+    return (size_t)8 * window_stride(lambda) + 2 * (size_t)kPipeTableBytes + kPipeRegionBytes;
 }
 
 template <int DT>
@@ -758,7 +850,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) scan_pipe_kernel(ScanArgs a) 
     const DevIndex& ix = a.ix;
     const uint32_t lambda = ix.lambda;
     float* buf0 = reinterpret_cast<float*>(dsm);
-    unsigned char* tab = dsm + (((size_t)8 * lambda + 15) & ~(size_t)15);
+    const uint32_t lam4 = window_stride(lambda);  // windows start 16-byte aligned
+    unsigned char* tab = dsm + (size_t)8 * lam4;
     unsigned char* region = tab + 2 * kPipeTableBytes;
     auto t_start = [&](int t) { return reinterpret_cast<uint32_t*>(tab + t * kPipeTableBytes); };
     auto t_end = [&](int t) { return t_start(t) + kPipeTerms; };
@@ -778,7 +871,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) scan_pipe_kernel(ScanArgs a) 
         return nt > 0 ? (nt + kPipeTerms - 1) / kPipeTerms : 1;
     };
 
-    for (uint32_t m = threadIdx.x; m < 2 * lambda; m += kPipeThreads) buf0[m] = 0.0f;
+    for (uint32_t m = threadIdx.x; m < 2 * lam4; m += kPipeThreads) buf0[m] = 0.0f;
     __syncthreads();
 
     if (warp < kPipeAddWarps) {
@@ -792,7 +885,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) scan_pipe_kernel(ScanArgs a) 
                 named_sync(kBarReady + t);
                 if (p == 0 && it >= 2) named_sync(kBarEmpty + b);
                 accumulate_table<DT, kPipeAddWarps>(ix, t_start(t), t_end(t), t_w(t), c_pre(t), c_term(t), t_nc[t],
-                                                    t_total[t], warp, lane, buf0 + (size_t)b * lambda);
+                                                    t_total[t], warp, lane, buf0 + (size_t)b * lam4);
                 named_arrive(kBarFree + t);
                 if (p == np - 1) named_arrive(kBarDone + b);
             }
@@ -856,10 +949,251 @@ __global__ void __launch_bounds__(kPipeThreads, 1) scan_pipe_kernel(ScanArgs a) 
         const bool bounded = st[3] >= a.g;
         const uint32_t pbin = st[0];
         S::sync();
-        float* A = buf0 + (size_t)b * lambda;
+        float* A = buf0 + (size_t)b * lam4;
         select_window<S, kPipeCutWarps>(a, A, w, y, bounded, pbin, cs);
-        for (uint32_t m = (uint32_t)S::tid(); m < lambda; m += S::kThreads) A[m] = 0.0f;
+        for (uint32_t m = (uint32_t)S::tid(); m < lam4 / 4; m += S::kThreads)
+            reinterpret_cast<float4*>(A)[m] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (it + 2 < n_my) named_arrive(kBarEmpty + b);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Query-group window scan (batched schedule). One block owns window w for a
+// group of up to Q queries and holds their Q score windows in shared memory.
+// It walks the union of the group's query terms: each posting of a segment
+// I_{j,w} is loaded once and added into the window of every query of the
+// group that holds term j (Alg. 2's product and accumulation loops for Q
+// queries at once). Each query's window is then cut as in scan_window_kernel.
+//   union: the group's query entries, up to kGroupEntries per pass, go into a
+//       shared-memory hash keyed by dim; an occupied slot is one union term
+//       with the bit mask of the queries holding it and their weights. A dim
+//       that reaches two passes is simply two terms (every (query, term)
+//       entry is still added exactly once).
+//   adds: a warp chunk is 256 postings of one segment (the geometry the
+//       build's bank-aware order is laid out for); the ids are decoded once
+//       and, for every holder, the 8 postings of a lane are added with FP32
+//       shared-memory atomics under one 8-bit lane mask.
+// Groups are consecutive query rows, or the rows of `perm` (queries sorted so
+// that a group shares its heaviest lists).
+// ---------------------------------------------------------------------------
+constexpr int kMaxGroup = (int)kMaxQueryGroup;
+constexpr int kGroupEntries = 512;     // query entries hashed per pass (union terms per pass <= this)
+constexpr int kGroupHash = 1024;       // hash slots (load <= 1/2)
+constexpr int kGroupHashBits = 10;
+
+// Shared-memory region of the group scan: the hash and term tables while
+// postings are added (hash keys and values, term starts, ends, chunk prefix
+// and holder masks, weights [kGroupEntries][kMaxGroup], the chunk -> term
+// table), the cut's scratch afterwards (private histograms, staged keys).
+constexpr size_t kGroupTableBytes = ((size_t)kGroupHash * 8 + (size_t)(4 * kGroupEntries + 1) * 4 +
+                                     (size_t)kGroupEntries * kMaxGroup * 4 + (size_t)kChunkTable * 2 + 15) &
+                                    ~(size_t)15;
+__host__ __device__ constexpr size_t group_region_bytes(int block) {
+    return kGroupTableBytes > (size_t)(block / 32) * kRelBins * 4 ? kGroupTableBytes
+                                                                   : (size_t)(block / 32) * kRelBins * 4;
+}
+// Dynamic shared memory a group-scan block may take (the static arrays take the rest of the 227 KiB).
+constexpr size_t kGroupDynSmemMax = (size_t)(227 - 20) * 1024;
+
+static size_t group_smem_bytes(uint32_t lambda, uint32_t Q, int block) {
+    return (size_t)Q * window_stride(lambda) * 4 + group_region_bytes(block);
+}
+
+struct GroupScanArgs {
+    ScanArgs s;            // index, queries (rows q_first + y), g, win_cap, workspace, w0
+    uint32_t Q;            // queries per group (1..kMaxGroup)
+    uint32_t nq;           // query rows of the launch
+    const uint32_t* perm;  // [nq] row of the i-th query in group order, or null (consecutive rows)
+};
+
+// Adds a chunk of union term t into the window of every query of the group
+// that holds the term (shared-memory atomics: chunks of different terms run
+// at once and may meet on a slot).
+__device__ __forceinline__ void add_chunk_holders(float* A, uint32_t stride, uint32_t mask, const float* w,
+                                                  const Chunk& k) {
+    while (mask) {
+        const int i = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const float wq = w[i];
+        float* Ai = A + (size_t)i * stride;
+#pragma unroll
+        for (int u = 0; u < kChunkU; u++)
+            if (k.lm & (1u << u)) atomicAdd(Ai + chunk_slot(k, u), wq * k.v[u]);
+    }
+}
+
+__device__ __forceinline__ uint32_t group_hash_slot(int32_t j) {
+    return ((uint32_t)j * 2654435761u) >> (32 - kGroupHashBits);
+}
+
+template <int DT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) group_scan_kernel(GroupScanArgs a) {
+    constexpr int NW = BLOCK / 32;
+    using S = SyncBlock<BLOCK>;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    __shared__ uint32_t hist[kHistBins];
+    __shared__ uint32_t hist2[kSubBins];
+    __shared__ uint32_t warp_off[NW];
+    __shared__ uint32_t red[NW + 1];
+    __shared__ uint32_t st[4];
+    __shared__ uint32_t s_staged;
+    __shared__ uint32_t mrow[kMaxGroup];        // query row (within the launch) of each member
+    __shared__ uint32_t mpre[kMaxGroup + 1];    // prefix of the members' term counts
+    __shared__ int64_t mqb[kMaxGroup];          // first entry of each member's query row
+    const ScanArgs& sa = a.s;
+    const DevIndex& ix = sa.ix;
+    const uint32_t lambda = ix.lambda;
+    const uint32_t Q = a.Q;
+    const uint32_t grp = blockIdx.x;
+    const uint32_t w = sa.w0 + blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t first = grp * Q;
+    const uint32_t qn = min(Q, a.nq - first);  // members of this group
+
+    float* A = reinterpret_cast<float*>(gsm);
+    const uint32_t lam4 = window_stride(lambda);  // members' windows start 16-byte aligned
+    unsigned char* region = gsm + (size_t)Q * lam4 * 4;
+    int32_t* hkey = reinterpret_cast<int32_t*>(region);
+    uint32_t* hval = reinterpret_cast<uint32_t*>(hkey + kGroupHash);  // holder mask | union index << 16
+    uint32_t* t_start = hval + kGroupHash;
+    uint32_t* t_end = t_start + kGroupEntries;
+    uint32_t* c_pre = t_end + kGroupEntries;
+    uint32_t* t_mask = c_pre + kGroupEntries + 1;
+    float* t_w = reinterpret_cast<float*>(t_mask + kGroupEntries);
+    uint16_t* c_term = reinterpret_cast<uint16_t*>(t_w + kGroupEntries * kMaxGroup);
+
+    if (tid < (int)qn) {
+        const uint32_t y = a.perm ? a.perm[first + tid] : first + (uint32_t)tid;
+        const int64_t r = sa.q_first + y;
+        mrow[tid] = y;
+        mqb[tid] = sa.q_indptr[r];
+        mpre[tid + 1] = (uint32_t)(sa.q_indptr[r + 1] - sa.q_indptr[r]);
+    }
+    // zero the members' windows, 16 bytes per store
+    {
+        float4* A4 = reinterpret_cast<float4*>(A);
+        const uint32_t n4 = (qn * lam4) >> 2;
+        for (uint32_t m = tid; m < n4; m += BLOCK) A4[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mpre[0] = 0;
+        for (uint32_t i = 0; i < qn; i++) mpre[i + 1] += mpre[i];
+    }
+    __syncthreads();
+    const uint32_t n_ent = mpre[qn];
+
+    for (uint32_t e0 = 0; e0 < n_ent; e0 += kGroupEntries) {
+        // ---- union of the entries e0 .. e0 + kGroupEntries - 1 in the hash
+        for (int s = tid; s < kGroupHash; s += BLOCK) {
+            hkey[s] = -1;
+            hval[s] = 0;
+        }
+        __syncthreads();
+        int my_slot = -1, my_i = 0;
+        float my_w = 0.0f;
+        if (tid < kGroupEntries && e0 + tid < n_ent) {
+            const uint32_t e = e0 + (uint32_t)tid;
+            int i = 0;
+            while (i + 1 < (int)qn && mpre[i + 1] <= e) i++;
+            const int64_t at = mqb[i] + (e - mpre[i]);
+            const int32_t j = sa.q_indices[at];
+            const float qv = sa.q_values[at];
+            // entries the scan skips: dims out of range and non-finite values (the merge
+            // reports them), zero weights (Definition 1: not entries)
+            if (j >= 0 && j < ix.dim && isfinite(qv) && qv != 0.0f) {
+                uint32_t s = group_hash_slot(j);
+                for (int probe = 0; probe < kGroupHash; probe++) {
+                    const int32_t old = atomicCAS(&hkey[s], -1, j);
+                    if (old == -1 || old == j) break;
+                    s = (s + 1) & (kGroupHash - 1);
+                }
+                my_slot = (int)s;
+                my_i = i;
+                my_w = (DT == SINDI_F8E4M3) ? qv * ix.scale[j] : qv;
+                atomicOr(&hval[s], 1u << i);
+            }
+        }
+        __syncthreads();
+        // ---- occupied slots -> union terms 0 .. nu - 1 (slot order)
+        constexpr int SPT = (kGroupHash + BLOCK - 1) / BLOCK;  // slots per thread
+        uint32_t occ = 0;
+#pragma unroll
+        for (int k = 0; k < SPT; k++) {
+            const int s = tid * SPT + k;
+            if (s < kGroupHash && hkey[s] >= 0) occ++;
+        }
+        uint32_t nu;
+        uint32_t u = group_exclusive_sum<uint32_t, S>(occ, &nu, red);
+#pragma unroll
+        for (int k = 0; k < SPT; k++) {
+            const int s = tid * SPT + k;
+            if (s < kGroupHash && hkey[s] >= 0) {
+                const uint32_t hv = hval[s];
+                hval[s] = (hv & 0xFFFFu) | (u << 16);
+                t_start[u] = (uint32_t)hkey[s];  // the dim, for now
+                t_mask[u] = hv & 0xFFFFu;
+                u++;
+            }
+        }
+        for (uint32_t x = tid; x < nu * kMaxGroup; x += BLOCK) t_w[x] = 0.0f;
+        __syncthreads();
+        if (my_slot >= 0) t_w[(hval[my_slot] >> 16) * kMaxGroup + my_i] = my_w;
+        // ---- the segment I_{j,w} of every union term, and the chunks that tile it
+        uint32_t nch = 0;
+        if (tid < (int)nu) {
+            const uint64_t sg = (uint64_t)t_start[tid] * ix.sigma + w;
+            const uint32_t start = ix.seg[sg], len = ix.seg[sg + 1] - start;
+            t_start[tid] = start;
+            t_end[tid] = start + len;
+            nch = len >= kVecMin ? long_segment_chunks(start, start + len) : (len ? 1u : 0u);
+        }
+        uint32_t n_chunks;
+        const uint32_t excl = group_exclusive_sum<uint32_t, S>(nch, &n_chunks, red);
+        if (tid < (int)nu) {
+            c_pre[tid] = excl;
+            for (uint32_t c = excl; c < excl + nch && c < (uint32_t)kChunkTable; c++) c_term[c] = (uint16_t)tid;
+        }
+        __syncthreads();
+        // ---- scatter-add: warp `warp` takes chunks warp, warp + NW, ...; the next
+        // chunk's loads are issued before this chunk's adds
+        {
+            auto load_c = [&](uint32_t c, Chunk& k) -> int {
+                const int t = c < (uint32_t)kChunkTable ? (int)c_term[c] : term_of(c_pre, (int)nu, c);
+                load_segment_chunk<DT>(ix, t_start[t], t_end[t], (c - c_pre[t]) * (uint32_t)kChunkLen, lane, k);
+                return t;
+            };
+            uint32_t c = (uint32_t)warp;
+            Chunk cur;
+            int tc = 0;
+            if (c < n_chunks) tc = load_c(c, cur);
+            while (c < n_chunks) {
+                const uint32_t cn = c + NW;
+                Chunk nxt;
+                int tn = 0;
+                if (cn < n_chunks) tn = load_c(cn, nxt);
+                add_chunk_holders(A, lam4, t_mask[tc], t_w + (size_t)tc * kMaxGroup, cur);
+                cur = nxt;
+                tc = tn;
+                c = cn;
+            }
+        }
+        __syncthreads();  // tables and hash are reused by the next pass
+    }
+
+    allow_next_kernel();
+    wait_previous_kernels();  // the workspace (candidates, H) is free from here on
+    const CutScratch cs{hist, hist2, region, (uint32_t)group_region_bytes(BLOCK), warp_off, red, st, &s_staged};
+    for (uint32_t i = 0; i < qn; i++) {
+        const uint32_t y = mrow[i];
+        // the query's running bound: g candidates emitted at or above some bin (H only
+        // grows while the launch runs, so any read of it bounds the answer)
+        const uint32_t* H = sa.ws.hist + (size_t)y * kHistBins;
+        block_find_bin<kHistBins, BLOCK>([&](int b) { return __ldcg(H + b); }, sa.g, red, st);
+        const bool bounded = st[3] >= sa.g;
+        const uint32_t pbin = st[0];
+        __syncthreads();
+        select_window<S, NW>(sa, A + (size_t)i * lam4, w, y, bounded, pbin, cs);
     }
 }
 
@@ -1218,6 +1552,7 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
 // positions of (pidx, pval), their count to kept[q]. Entries the scan would
 // skip anyway (dim out of range, non-finite, zero) are not entries here.
 constexpr int kPruneQueryWarps = 4;
+constexpr size_t kPruneQuerySmem = (size_t)kPruneQueryWarps * kQueryTermLimit * sizeof(uint64_t);
 __global__ void __launch_bounds__(kPruneQueryWarps * 32) prune_queries_kernel(
     const int64_t* qp, const int32_t* qi, const float* qv, int64_t nq, int32_t dim, double beta, uint32_t* kept,
     int32_t* pidx, float* pval) {
@@ -1292,7 +1627,19 @@ __global__ void pad_results_kernel(uint32_t* out_ids, float* out_scores, int64_t
 struct Plan {
     bool final_stage;
     uint32_t g, win_cap, cand_cap, fcap, top_cap, merge_blocks, block;
+    uint32_t group;  // batched scan: queries per block (1 = one block per (query, window))
 };
+
+// Queries per block of the batched scan: as asked (0: one, the fastest shape
+// measured on the 1M-document workload), at most kMaxGroup and at most what
+// shared memory holds.
+static uint32_t group_size(const IndexImpl& ix, uint32_t asked, uint32_t block) {
+    const int bt = block == 1024 ? 1024 : 512;
+    uint32_t q = asked ? asked : 1u;
+    q = std::min<uint32_t>(q, (uint32_t)kMaxGroup);
+    while (q > 1 && group_smem_bytes(ix.lambda, q, bt) > kGroupDynSmemMax) q--;
+    return q;
+}
 
 static Plan make_plan(const IndexImpl& ix, const sindi_search_params& prm) {
     Plan p;
@@ -1307,6 +1654,7 @@ static Plan make_plan(const IndexImpl& ix, const sindi_search_params& prm) {
     p.top_cap = p.final_stage ? 1 : p.g;
     p.merge_blocks = std::max<uint32_t>(1, std::min<uint32_t>(16, p.cand_cap / 8192));
     p.block = prm.block_threads;
+    p.group = group_size(ix, prm.group, prm.block_threads);
     return p;
 }
 
@@ -1371,6 +1719,33 @@ static void launch_pipe(int dt, const ScanArgs& a, uint32_t blocks, size_t smem,
     else launch_pipe_t<SINDI_F8E4M3>(a, blocks, smem, s, pdl);
 }
 
+template <int DT>
+static void allow_group_smem() {
+    SINDI_CUDA(cudaFuncSetAttribute(group_scan_kernel<DT, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kGroupDynSmemMax));
+    SINDI_CUDA(cudaFuncSetAttribute(group_scan_kernel<DT, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kGroupDynSmemMax));
+}
+
+template <int DT, int BLOCK>
+static void launch_group_scan_t(const GroupScanArgs& a, uint32_t n_groups, uint32_t nwin, size_t smem,
+                                cudaStream_t s, bool pdl) {
+    launch_kernel(group_scan_kernel<DT, BLOCK>, dim3(n_groups, nwin), dim3(BLOCK), smem, s, pdl, a);
+}
+
+static void launch_group_scan(int dt, uint32_t block, const GroupScanArgs& a, uint32_t n_groups, uint32_t nwin,
+                              size_t smem, cudaStream_t s, bool pdl) {
+    if (block == 1024) {
+        if (dt == SINDI_F32) launch_group_scan_t<SINDI_F32, 1024>(a, n_groups, nwin, smem, s, pdl);
+        else if (dt == SINDI_F16) launch_group_scan_t<SINDI_F16, 1024>(a, n_groups, nwin, smem, s, pdl);
+        else launch_group_scan_t<SINDI_F8E4M3, 1024>(a, n_groups, nwin, smem, s, pdl);
+    } else {
+        if (dt == SINDI_F32) launch_group_scan_t<SINDI_F32, 512>(a, n_groups, nwin, smem, s, pdl);
+        else if (dt == SINDI_F16) launch_group_scan_t<SINDI_F16, 512>(a, n_groups, nwin, smem, s, pdl);
+        else launch_group_scan_t<SINDI_F8E4M3, 512>(a, n_groups, nwin, smem, s, pdl);
+    }
+}
+
 // Shared-memory limits of every search kernel, set once per device before the
 // first launch (and before any stream capture, where they cannot be set).
 void configure_search_kernels(int device) {
@@ -1381,8 +1756,13 @@ void configure_search_kernels(int device) {
     allow_window_smem_dt<SINDI_F32>();
     allow_window_smem_dt<SINDI_F16>();
     allow_window_smem_dt<SINDI_F8E4M3>();
+    allow_group_smem<SINDI_F32>();
+    allow_group_smem<SINDI_F16>();
+    allow_group_smem<SINDI_F8E4M3>();
     SINDI_CUDA(cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8));
     SINDI_CUDA(cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxGamma * 8));
+    SINDI_CUDA(cudaFuncSetAttribute(prune_queries_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kPruneQuerySmem));
     done.push_back(device);
 }
 
@@ -1433,7 +1813,7 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
                          cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, const QueryCsr* scan_q = nullptr) {
     configure_search_kernels(ix.device);
     const DevIndex dix = ix.dev();
-    const size_t scan_smem = (size_t)ix.lambda * sizeof(float);
+    const size_t scan_smem = (size_t)window_stride(ix.lambda) * sizeof(float);
     // the coarse scan reads the beta-pruned queries when there are any (Alg. 4, the query-pruning step);
     // merge and rerank check and reorder with the full queries
     ScanArgs sa{dix, scan_q ? scan_q->indptr : q_indptr, scan_q ? scan_q->indices : q_indices,
@@ -1444,7 +1824,14 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
     const bool pipe = pl.block == SINDI_SCAN_PIPELINED && ix.lambda <= kPipeMaxWindow;
     const uint32_t block = pl.block == SINDI_SCAN_PIPELINED ? 0u : pl.block;
     const size_t pipe_smem = pipe_smem_bytes(ix.lambda);
-    if (pipe && batched) {
+    if (batched && !pipe && pl.group > 1 && ix.sigma <= 65535u) {
+        // query groups: one block per (group, window); groups vary fastest, so the
+        // blocks of one window run together and its lists stay in L2
+        const uint32_t bt = pl.block == 1024 ? 1024u : 512u;
+        const GroupScanArgs ga{sa, pl.group, nq, nullptr};
+        launch_group_scan(ix.dtype, bt, ga, (nq + pl.group - 1) / pl.group, ix.sigma,
+                          group_smem_bytes(ix.lambda, pl.group, (int)bt), stream, *chained && !ev0);
+    } else if (pipe && batched) {
         // one resident block per SM walks the (window, query) items in
         // window-major order, so a query's windows come one after another
         const uint64_t items = (uint64_t)nq * ix.sigma;
@@ -1684,13 +2071,8 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
         pq_indptr = P.alloc<int64_t>(n_queries + 1);
         pq_idx = P.alloc<int32_t>(nnz);
         pq_val = P.alloc<float>(nnz);
-        const size_t qsmem = (size_t)kPruneQueryWarps * kQueryTermLimit * sizeof(uint64_t);
-        static bool qconf = false;
-        if (!qconf) {
-            SINDI_CUDA(cudaFuncSetAttribute(prune_queries_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)qsmem));
-            qconf = true;
-        }
+        configure_search_kernels(ix.device);  // the query-pruning kernel's shared-memory limit, per device
+        const size_t qsmem = kPruneQuerySmem;
         const unsigned blocks = (unsigned)std::min<int64_t>((n_queries + kPruneQueryWarps - 1) / kPruneQueryWarps,
                                                             152 * 16);
         prune_queries_kernel<<<blocks, kPruneQueryWarps * 32, qsmem, stream>>>(q_indptr, q_indices, q_values,

@@ -45,7 +45,7 @@ class sindi_build_params(ctypes.Structure):
 
 class sindi_search_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_uint32), ("gamma", ctypes.c_uint32), ("beta", ctypes.c_double),
-                ("mode", ctypes.c_uint32), ("block_threads", ctypes.c_uint32)]
+                ("mode", ctypes.c_uint32), ("block_threads", ctypes.c_uint32), ("group", ctypes.c_uint32)]
 
 
 class sindi_index_info_t(ctypes.Structure):
@@ -197,10 +197,12 @@ def sindi_build(indptr, indices, values, n_docs: int, dim: int, window: int = 0,
 
 
 def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
-                 gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None, block: int = 0) -> None:
+                 gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None, block: int = 0,
+                 group: int = 0) -> None:
     """Algorithm 4 for every query row; writes out_ids (uint32/int32) and out_scores (float32), [n_queries, k]."""
     lib = load()
-    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block))
+    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block),
+                              group=int(group))
     _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     st = lib.sindi_search(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                           _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm), _ptr(out_ids, np.uint32),
@@ -210,11 +212,12 @@ def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_
 
 def sindi_search_noalloc(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
                          gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None,
-                         block: int = 0) -> None:
+                         block: int = 0, group: int = 0) -> None:
     """sindi_search for callers that cannot allocate device memory: all working memory comes from the library's
     static 8 MiB device array. Device tensors only; calls that overlap on the GPU race on that array."""
     lib = load()
-    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block))
+    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block),
+                              group=int(group))
     _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     st = lib.sindi_search_noalloc(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                                   _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm),
@@ -233,21 +236,28 @@ def sindi_index_info(index: int) -> dict:
     return {f: getattr(info, f) for f, _ in sindi_index_info_t._fields_}
 
 
-def sindi_index_export(index: int) -> dict:
-    """Copy the lists to host numpy arrays: seg, ids, vals, scale, kept."""
+def sindi_index_export(index: int, parts=("seg", "ids", "vals", "scale", "kept")) -> dict:
+    """Copy the lists to host numpy arrays: seg, ids, vals, scale, kept (only the named parts)."""
     info = sindi_index_info(index)
     S = info["dim"] * info["n_windows"]
     P = info["postings"]
     vdt = {SINDI_F32: np.float32, SINDI_F16: np.uint16, SINDI_F8E4M3: np.uint8}[info["value_dtype"]]
-    seg = np.empty(S + 1, np.uint32)
-    ids = np.empty(max(P, 1), np.uint16)
-    vals = np.empty(max(P, 1), vdt)
-    scale = np.empty(info["dim"], np.float32)
-    kept = np.empty(max(info["n_docs"], 1), np.uint32)
-    _check(load().sindi_index_export(ctypes.c_void_p(index), seg.ctypes.data, ids.ctypes.data, vals.ctypes.data,
-                                     scale.ctypes.data, kept.ctypes.data), "sindi_index_export")
-    return {"seg": seg, "ids": ids[:P], "vals": vals[:P], "scale": scale, "kept": kept[: info["n_docs"]],
-            "info": info}
+    arrs = {
+        "seg": lambda: np.empty(S + 1, np.uint32),
+        "ids": lambda: np.empty(max(P, 1), np.uint16),
+        "vals": lambda: np.empty(max(P, 1), vdt),
+        "scale": lambda: np.empty(info["dim"], np.float32),
+        "kept": lambda: np.empty(max(info["n_docs"], 1), np.uint32),
+    }
+    out = {name: arrs[name]() for name in parts}
+    ptr = {name: (out[name].ctypes.data if name in out else None) for name in arrs}
+    _check(load().sindi_index_export(ctypes.c_void_p(index), ptr["seg"], ptr["ids"], ptr["vals"], ptr["scale"],
+                                     ptr["kept"]), "sindi_index_export")
+    for name, n in (("ids", P), ("vals", P), ("kept", info["n_docs"])):
+        if name in out:
+            out[name] = out[name][:n]
+    out["info"] = info
+    return out
 
 
 def sindi_index_save(index: int, path: str) -> None:
@@ -299,7 +309,7 @@ class Index:
         self.info = sindi_index_info(self.handle)
 
     def search(self, q_indptr, q_indices, q_values, k: int, gamma: int = 0, beta: float = 1.0,
-               mode: str = "plain", out=None, stream=None, block: int = 0):
+               mode: str = "plain", out=None, stream=None, block: int = 0, group: int = 0):
         """Returns (ids, scores) of shape [n_queries, k]; device tensors for device queries."""
         n_q = (q_indptr.shape[0] if hasattr(q_indptr, "shape") else len(q_indptr)) - 1
         if out is None:
@@ -311,7 +321,7 @@ class Index:
                 out = (torch.empty((n_q, k), dtype=torch.int32, device=dev),
                        torch.empty((n_q, k), dtype=torch.float32, device=dev))
         sindi_search(self.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma, beta, mode, stream,
-                     block)
+                     block, group)
         return out
 
     def save(self, path: str) -> None:
@@ -330,8 +340,8 @@ class Index:
     def check(self, stream=None):
         sindi_check(self.handle, stream)
 
-    def export(self) -> dict:
-        return sindi_index_export(self.handle)
+    def export(self, parts=("seg", "ids", "vals", "scale", "kept")) -> dict:
+        return sindi_index_export(self.handle, parts)
 
     def close(self):
         """Free the index; plans and servers still open over it are closed first (they must not outlive it)."""
@@ -356,8 +366,9 @@ class Index:
 
 # ---- graph-captured batched search -------------------------------------------------
 def sindi_plan_create(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
-                      gamma: int = 0, beta: float = 1.0, block: int = 0) -> int:
-    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=SINDI_MODE_BATCHED, block_threads=int(block))
+                      gamma: int = 0, beta: float = 1.0, block: int = 0, group: int = 0) -> int:
+    prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=SINDI_MODE_BATCHED, block_threads=int(block),
+                              group=int(group))
     _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     out = ctypes.c_void_p()
     _check(load().sindi_plan_create(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
@@ -384,7 +395,7 @@ class Plan:
     """A batched search of fixed device buffers, captured once as a CUDA graph."""
 
     def __init__(self, index: "Index", q_indptr, q_indices, q_values, k: int, gamma: int = 0, out=None,
-                 block: int = 0):
+                 block: int = 0, group: int = 0):
         import torch
         self.index = index
         n_q = q_indptr.shape[0] - 1
@@ -394,7 +405,7 @@ class Plan:
                    torch.empty((n_q, k), dtype=torch.float32, device=q_indptr.device))
         self.out = out
         self.handle = sindi_plan_create(index.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma,
-                                        block=block)
+                                        block=block, group=group)
         index._dependents.add(self)
 
     def launch(self, stream=None):

@@ -1,6 +1,7 @@
 """Host-side logic that needs no GPU: workload generators, autotuner window candidates, bench accounting."""
 import hashlib
 import os
+import sys
 
 import numpy as np
 
@@ -258,3 +259,68 @@ def test_generator_rows_do_not_depend_on_thread_count():
         assert r.returncode == 0, r.stderr
         out.append(r.stdout.strip())
     assert out[0] == out[1] and len(out[0]) == 64
+
+
+def test_serving_load_generator_is_open_loop():
+    """bench_native/serve_load.c against a fake server: one request per scheduled Poisson arrival (rows taken in
+    turn), a failed request counted, and latency measured from the scheduled arrival (it includes the server's
+    own submit-to-results time)."""
+    import ctypes
+    import importlib.util
+    import threading
+    import time
+
+    spec = importlib.util.spec_from_file_location("bench_native_build_t", os.path.join(ROOT, "bench_native", "build.py"))
+    bn = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bn)
+    bn.build()
+    gen = ctypes.CDLL(bn.LOAD_LIB)
+    sys_path = sys.path[:]
+    sys.path.insert(0, ROOT)
+    try:
+        import bench
+    finally:
+        sys.path[:] = sys_path
+    SUBMIT = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64))
+    POLL = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
+                            ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_float),
+                            ctypes.POINTER(ctypes.c_double))
+    lock = threading.Lock()
+    seen, times = [], []
+
+    def submit(_srv, idx, val, nnz, ticket):
+        with lock:
+            ticket[0] = len(seen)
+            seen.append((nnz, idx[0] if nnz else -1))
+            times.append(time.perf_counter())
+        return 0
+
+    def poll(_srv, ticket, _wait, _ids, _sc, lat):
+        lat[0] = 0.5
+        return 6 if ticket == 5 else 0
+
+    fs, fp = SUBMIT(submit), POLL(poll)
+    qp = np.array([0, 2, 5, 6], np.int64)
+    qx = np.array([10, 11, 20, 21, 22, 30], np.int32)
+    qv = np.ones(6, np.float32)
+    gen.sindi_load_open_loop.restype = ctypes.c_int
+    gen.sindi_load_open_loop.argtypes = [ctypes.c_void_p] * 6 + [ctypes.c_int64, ctypes.c_uint32, ctypes.c_double,
+                                                                 ctypes.c_double, ctypes.c_uint64,
+                                                                 ctypes.POINTER(bench._LoadResult)]
+    res = bench._LoadResult()
+    rc = gen.sindi_load_open_loop(ctypes.c_void_p(1), ctypes.cast(fs, ctypes.c_void_p),
+                                  ctypes.cast(fp, ctypes.c_void_p), qp.ctypes.data, qx.ctypes.data, qv.ctypes.data,
+                                  3, 10, 2000.0, 0.5, 11, ctypes.byref(res))
+    assert rc == 0
+    assert res.requests == 1000 == len(seen)
+    assert res.failed == 1
+    assert seen[:6] == [(2, 10), (3, 20), (1, 30), (2, 10), (3, 20), (1, 30)]
+    assert res.p50_ms >= 0.5 and res.server_p50_ms == 0.5 and res.p99_ms >= res.p50_ms
+    # the arrivals follow the schedule: mean gap 1 / 2000 s (Poisson), not the speed of the submitter
+    gaps = np.diff(times)
+    assert 0.35e-3 < gaps.mean() < 0.7e-3, gaps.mean()
+    assert 1200 < res.achieved_qps < 2600, res.achieved_qps
+    # bad arguments are refused before anything is submitted
+    assert gen.sindi_load_open_loop(None, None, None, None, None, None, 0, 10, 1.0, 1.0, 1,
+                                    ctypes.byref(res)) == -1

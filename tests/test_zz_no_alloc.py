@@ -71,7 +71,7 @@ def test_noalloc_matches_search_on_two_calls_in_a_row(index_and_queries, k, gamm
 
 def test_noalloc_refuses_what_does_not_fit_and_host_buffers():
     # 1.2M one-entry documents, window 1,024, gamma 8,192: one query's candidate buffer alone is
-    # 1,172 windows x 1,024 x 8 B = 9.6 MB, more than the 8 MiB array
+    # 1,172 windows x 2 x 1,024 x 8 B = 19.2 MB, more than the 8 MiB array
     n, dim = 1_200_000, 100
     rng = np.random.default_rng(1)
     ip = np.arange(n + 1, dtype=np.int64)
