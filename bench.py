@@ -260,9 +260,30 @@ def _recall_rows(ids, truth):
     return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / max(1, len(b)) for a, b in zip(ids, truth)]))
 
 
-def pruning_ablation(sindi, torch, dev, w, ip, ix, v, q_dev, nq, steps, flush, stream):
+def fp64_truth_sample(ip, ix, v, qp, qx, qv, dim, k, n=40):
+    """FP64 exact top-k (the oracle's brute force, Definition 3) of n query rows spread over the batch, for
+    Recall@k against FP64 exact. Returns (D, Q, {row: (ids, scores)})."""
+    import oracle
+
+    D = oracle.Dataset(ip, ix, v, dim)
+    Q = oracle.Dataset(qp, qx, qv, dim)
+    rows = list(range(0, Q.n, max(1, Q.n // n)))[:n]
+    return D, Q, _fp64_truth(D, Q, rows, k)
+
+
+def _choice_ids(sindi, dd, qd, dim, k, choice):
+    """Result ids of the autotuner's chosen configuration on the given queries."""
+    with sindi.Index(*dd, dim, window=choice["window"], alpha=choice["alpha"]) as idx:
+        ids, _ = idx.search(*qd, k=k, gamma=choice["gamma"], mode=choice["mode"], block=choice["block"],
+                            group=choice.get("group", 1))
+        idx.check()
+        return ids.cpu().numpy().view(np.uint32)
+
+
+def pruning_ablation(sindi, torch, dev, w, ip, ix, v, q_dev, nq, steps, flush, stream, fp64=None):
     """The pruning methods of Sec. 4.1 on the workload (ablation of Sec. 5): postings kept, Recall@k with the
-    workload's reorder depth against the exact GPU search (alpha = 1, no reorder), and plain-schedule QPS."""
+    workload's reorder depth against FP64 exact on sampled queries (`fp64` = (D, Q, truth)) and, on every
+    query, against the exact GPU search (alpha = 1, no reorder; a proxy), and plain-schedule QPS."""
     grid = ([("mass", 0, a) for a in (0.4, 0.5, 0.6)] + [("vector_number", n, 1.0) for n in (15, 25, 40)] +
             [("list", n, 1.0) for n in (2000, 5000, 10000)] + [("mass_list", n, w.alpha) for n in (2000, 5000)])
     dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
@@ -277,20 +298,27 @@ def pruning_ablation(sindi, torch, dev, w, ip, ix, v, q_dev, nq, steps, flush, s
             qps = _timed_qps(torch, lambda: idx.search(*q_dev, k=w.k, gamma=w.gamma, mode="plain", out=(ids, sc)),
                              nq, steps, flush, stream)
             idx.check()
-            rows.append({"prune": prune, "prune_n": n, "alpha": a, "postings": idx.info["postings"],
-                         "recall_at_k": _recall_rows(ids.cpu().numpy().view(np.uint32), truth), "qps": qps,
-                         "gamma": w.gamma})
-    return {"rows": rows, "recall_vs": "GPU exact search (alpha = 1, gamma = 0)", "schedule": "plain"}
+            hids = ids.cpu().numpy().view(np.uint32)
+            row = {"prune": prune, "prune_n": n, "alpha": a, "postings": idx.info["postings"],
+                   "recall_at_k_proxy": _recall_rows(hids, truth), "qps": qps, "gamma": w.gamma}
+            if fp64 is not None:
+                row["recall_at_k_vs_fp64"], row["recall_at_k_tie_aware_vs_fp64"] = _recall_vs_fp64(hids, fp64[2],
+                                                                                                  fp64[0], fp64[1])
+            rows.append(row)
+    return {"rows": rows, "recall_vs": "FP64 oracle brute force on sampled queries (recall_at_k_vs_fp64); the "
+                                       "proxy is the exact GPU search (alpha = 1, gamma = 0) on every query",
+            "schedule": "plain"}
 
 
-def sparsity_sweep(sindi, torch, dev, steps, flush, stream):
+def sparsity_sweep(sindi, torch, dev, steps, flush, stream, dims=(10, 30, 50, 70, 100)):
     """Sec. 5's uniform-random sparsity sweep: for each d, the autotuned (alpha, window, gamma, schedule) with
-    the highest QPS at Recall@50 >= 0.99 against the exact GPU search, and that exact search's own QPS."""
+    the highest QPS at Recall@50 >= 0.99 against the exact GPU search (the tuner's proxy), that choice's
+    Recall@50 against FP64 exact on sampled queries, and the exact search's own QPS."""
     import datagen
     from paper_2509_08395_gb300 import autotune
 
     out = []
-    for d in (10, 30, 50, 70, 100):
+    for d in dims:
         w = datagen.WORKLOADS[f"uniform-1m-d{d}k"]
         ip, ix, v = datagen.docs(w)
         qp, qx, qv = datagen.queries(w)
@@ -299,13 +327,20 @@ def sparsity_sweep(sindi, torch, dev, steps, flush, stream):
         nq = len(qp) - 1
         t0 = time.perf_counter()
         tuned = autotune.autotune(*dd, w.dim, *qd, k=w.k, alpha=w.alpha, alphas=(0.3, 0.5, 0.7, 0.9),
-                                  recall_target=0.99, blocks=(512,))
+                                  recall_target=0.99, blocks=(512,), groups=(1,), window_prior=True)
         with sindi.Index(*dd, w.dim, window=w.window, alpha=1.0) as exact:
             exact_qps = _timed_qps(torch, lambda: exact.search(*qd, k=w.k, gamma=0, mode="batched"), nq, steps,
                                    flush, stream)
             postings_exact = exact.info["postings"]
-        out.append({"workload": w.name, "dim": w.dim, "choice": tuned["choice"], "exact_batched_qps": exact_qps,
-                    "postings_unpruned": postings_exact, "seconds": time.perf_counter() - t0})
+        row = {"workload": w.name, "dim": w.dim, "choice": tuned["choice"], "exact_batched_qps": exact_qps,
+               "postings_unpruned": postings_exact, "window_model": tuned["window_model"],
+               "seconds": time.perf_counter() - t0}
+        if tuned["choice"]:
+            D, Q, truth = fp64_truth_sample(ip, ix, v, qp, qx, qv, w.dim, w.k, n=20)
+            row["recall_at_k_vs_fp64"], row["recall_at_k_tie_aware_vs_fp64"] = _recall_vs_fp64(
+                _choice_ids(sindi, dd, qd, w.dim, w.k, tuned["choice"]), truth, D, Q)
+            row["recall_sample"] = f"{len(truth)} queries, FP64 oracle brute force"
+        out.append(row)
         del dd, qd
     return out
 
@@ -428,7 +463,7 @@ def _score_errors(idx, torch, dev, w, ip, ix, v, qp, qx, qv, D, Q, rows, final_i
             ex = oracle.inner_product(D, int(i), Q, r)
             if ex != 0.0:
                 fe = max(fe, abs(float(sc) - ex) / abs(ex))
-    return {"coarse_max_rel_err_vs_fp64": ce, "final_max_rel_err_vs_fp64": fe, "queries": len(rows)}
+    return {"coarse_max_rel_err_vs_fp64": ce, "final_max_rel_err_vs_fp64": fe, "score_error_queries": len(rows)}
 
 
 def plan_leg(sindi, torch, dev, w, dd, qp, qx, qv, dtype, steps, warmup, flush, stream, D, Q, truth, host_docs):
@@ -500,7 +535,8 @@ def scale_legs(sindi, torch, dev, args, flush, stream, base_qps_fn=None):
     gen_s = time.perf_counter() - t0
     dd = [torch.from_numpy(a).to(dev) for a in (ip, ix, v)]
     D = oracle.Dataset(ip, ix, v, w3.dim)
-    for w, dtypes in ((w3, ("f32",)), (w4, ("f16", "f8"))):
+    # config 4's queries also on FP32 postings: the reduced-precision legs' baseline in the same schedule
+    for w, dtypes in ((w3, ("f32",)), (w4, ("f32", "f16", "f8"))):
         qp, qx, qv = datagen.queries(w)
         if args.scale_queries:
             n = min(args.scale_queries, len(qp) - 1)
@@ -819,12 +855,18 @@ def main():
             from paper_2509_08395_gb300 import autotune
 
             dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
-            tuned = autotune.autotune(dip, dix, dv, w.dim, *q_dev, k=w.k, alpha=w.alpha, recall_target=0.99)
-            del dip, dix, dv
+            tuned = autotune.autotune(dip, dix, dv, w.dim, *q_dev, k=w.k, alpha=w.alpha, recall_target=0.99,
+                                      window_prior=True)
             forms["autotuned"] = dict(tuned["choice"] or {}, seconds=tuned["seconds"],
-                                      recall_vs="GPU exact search (alpha = 1, gamma = 0)")
-            if not tuned["choice"]:
+                                      recall_proxy_vs="GPU exact search (alpha = 1, gamma = 0), every query",
+                                      window_model=tuned["window_model"])
+            if tuned["choice"]:
+                # re-scored below against FP64 exact on the sampled queries
+                forms["autotuned"]["_ids_only"] = _choice_ids(sindi, (dip, dix, dv), q_dev, w.dim, w.k,
+                                                              tuned["choice"])
+            else:
                 forms["autotuned"]["table"] = tuned["table"]
+            del dip, dix, dv
             for dt in ("f16", "f8"):
                 dip, dix, dv = (torch.from_numpy(a).to(dev) for a in (ip, ix, v))
                 with sindi.Index(dip, dix, dv, w.dim, window=w.window, alpha=w.alpha, value_dtype=dt) as lp:
@@ -846,18 +888,21 @@ def main():
                                                    "_sc": os_.cpu().numpy(), "_coarse": csc.cpu().numpy()}
         except Exception as e:  # noqa: BLE001 - reported in the line
             side_failed("forms", e)
-            forms = {name: f for name, f in forms.items() if "_ids" not in f}
+            forms = {name: f for name, f in forms.items() if "_ids" not in f and "_ids_only" not in f}
 
     ablation = None
     if args.ablation and rank == 0:
         try:
-            ablation = pruning_ablation(sindi, torch, dev, w, ip, ix, v, q_dev, nq, args.steps, flush, stream)
+            ablation = pruning_ablation(sindi, torch, dev, w, ip, ix, v, q_dev, nq, args.steps, flush, stream,
+                                        fp64_truth_sample(ip, ix, v, qp, qx, qv, w.dim, w.k))
         except Exception as e:  # noqa: BLE001 - reported in the line
             side_failed("pruning_ablation", e)
     sweep = None
-    if args.sparsity_sweep and rank == 0:
+    if rank == 0 and (args.sparsity_sweep or not args.no_scale):
         try:
-            sweep = sparsity_sweep(sindi, torch, dev, args.steps, flush, stream)
+            # the whole sweep when asked for; otherwise its d = 30k point as a side leg of the default run
+            sweep = sparsity_sweep(sindi, torch, dev, args.steps, flush, stream,
+                                   dims=(10, 30, 50, 70, 100) if args.sparsity_sweep else (30,))
         except Exception as e:  # noqa: BLE001 - reported in the line
             side_failed("sparsity_sweep", e)
 
@@ -871,6 +916,14 @@ def main():
                                              args.serve_seconds)}
         except Exception as e:  # noqa: BLE001 - reported in the line
             side_failed("serving", e)
+
+    # ---- configs 3-5 at full size (rank 0; one GPU holds each index)
+    scale = None
+    if rank == 0 and not args.no_scale:
+        try:
+            scale = scale_legs(sindi, torch, dev, args, flush, stream)
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            side_failed("scale", e)
 
     # ---- CPU baseline (oracle) + recall against FP64 exact, rank 0 only
     cpu = None
@@ -913,6 +966,11 @@ def main():
             truth = {r: oracle.brute_force(D, Q, r, w.k)[0] for r in range(0, nq, step_r)}
             I32 = oracle.Index(D, window=w.window, alpha=w.alpha)
             for name, f in forms.items():
+                if "_ids_only" in f:
+                    f["recall_at_k_vs_fp64"] = float(np.mean([oracle.recall(f["_ids_only"][r], t)
+                                                              for r, t in truth.items()]))
+                    f["recall_sample"] = f"{len(truth)} queries, FP64 oracle brute force"
+                    del f["_ids_only"]
                 if "_ids" in f:
                     f["recall_at_k"] = float(np.mean([oracle.recall(f["_ids"][r], t) for r, t in truth.items()]))
                     # score error against FP64: coarse (quantised postings vs unquantised FP64 Algorithm 2,
@@ -984,6 +1042,7 @@ def main():
         "pruning_ablation": ablation,
         "sparsity_sweep": sweep,
         "serving": serving,
+        "scale": scale,
         "scan_source_sha256": sha,
         "side_errors": side_errors,
     }

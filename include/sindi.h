@@ -255,6 +255,29 @@ sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_ind
                                   uint32_t* out_ids, float* out_scores, void* stream);
 
 /*
+ * Merge the result rows of a document-sharded search (one index per range of
+ * document ids, e.g. one per GPU): the top-k over all documents is the top-k
+ * of the shards' top-k lists, because windows, and so shards aligned to
+ * them, are independent (Sec. 3.3.1; Alg. 2 visits windows one by one and
+ * its heap keeps the best over all of them).
+ *   ids, scores: [n_shards][n_queries][k_in] device arrays, each shard's rows
+ *       as sindi_search writes them (local ids, best first, padding id
+ *       0xFFFFFFFF / score -inf, which is skipped).
+ *   id_offset: int64 [n_shards] host array; shard s's local id i is global id
+ *       id_offset[s] + i (0 <= id_offset[s] < 0xFFFFFFFF; the ranges must not
+ *       overlap and global ids must stay below 0xFFFFFFFF).
+ *   out_ids / out_scores: [n_queries][k] device arrays: the best k entries by
+ *       (score desc, global id asc), padded when fewer exist.
+ *   1 <= n_shards <= 64, n_shards * k_in <= 8192, 1 <= k <= 1024. Runs on the
+ *   current device, queued on `stream`; SINDI_ERR_INVALID_ARG for sizes out
+ *   of range or host pointers. The paper searches one machine; this call
+ *   serves the multi-GPU split only.
+ */
+sindi_status sindi_merge_topk(const uint32_t* ids, const float* scores, int32_t n_shards, int64_t n_queries,
+                              uint32_t k_in, const int64_t* id_offset, uint32_t k, uint32_t* out_ids,
+                              float* out_scores, void* stream);
+
+/*
  * Graph-captured batched search. Records the whole search of one query batch
  * (the batched schedule of sindi_search: every query of the batch in shared
  * launches) as a CUDA graph, so that each later run is one graph launch.

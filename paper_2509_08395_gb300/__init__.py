@@ -21,6 +21,7 @@ from .sindi import (  # noqa: F401
     sindi_index_info,
     sindi_index_load,
     sindi_index_save,
+    sindi_merge_topk,
     sindi_plan_create,
     sindi_plan_free,
     sindi_plan_launch,

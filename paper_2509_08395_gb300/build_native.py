@@ -1,4 +1,6 @@
-"""Compiles the CUDA sources of this package into ``lib/libsindi.so`` (sm_103a only).
+"""Compiles the CUDA sources of this package into ``lib/libsindi.so`` (sm_103a only), and the same sources
+with every bounds check of ``csrc/checks.cuh`` compiled in (``-DSINDI_CHECKS=1``) into
+``lib/libsindi_checked.so``, which tests load through ``SINDI_LIBRARY``.
 
 Each ``csrc/*.cu`` file is compiled to an object in parallel, then nvcc links
 the shared library with the CUDA runtime linked statically, so the library
@@ -19,8 +21,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
+OBJ_CHECKED = os.path.join(HERE, "_build_checked")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsindi.so")
+LIB_CHECKED = os.path.join(LIBDIR, "libsindi_checked.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -50,21 +54,25 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, checked: bool = True) -> str:
+    """Builds lib/libsindi.so (and, with `checked`, lib/libsindi_checked.so); objects compile in parallel."""
     os.makedirs(LIBDIR, exist_ok=True)
     cc = nvcc()
     heads = _headers()
+    variants = [(OBJ, LIB, [])] + ([(OBJ_CHECKED, LIB_CHECKED, ["-DSINDI_CHECKS=1"])] if checked else [])
     jobs = []
-    objs = []
-    for src in _sources():
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        if force or _stale(obj, [src] + heads):
-            cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
-            if verbose_ptxas:
-                cmd += ["-Xptxas", "-v"]
-            jobs.append(cmd)
+    objs = {}
+    for obj_dir, lib, defs in variants:
+        os.makedirs(obj_dir, exist_ok=True)
+        objs[lib] = []
+        for src in _sources():
+            obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
+            objs[lib].append(obj)
+            if force or _stale(obj, [src] + heads):
+                cmd = [cc, *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
+                if verbose_ptxas and not defs:
+                    cmd += ["-Xptxas", "-v"]
+                jobs.append(cmd)
 
     def run(cmd):
         p = subprocess.run(cmd, capture_output=True, text=True)
@@ -76,14 +84,15 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
                 sys.stderr.write(p.stdout + p.stderr)
             if p.returncode != 0:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp]
-        p = subprocess.run(cmd, capture_output=True, text=True)
-        if p.returncode != 0:
-            sys.stderr.write(p.stdout + p.stderr)
-            raise RuntimeError("link failed: " + " ".join(cmd))
-        os.replace(tmp, LIB)
+    for _, lib, _ in variants:
+        if force or jobs or _stale(lib, objs[lib]):
+            tmp = lib + f".tmp{os.getpid()}"
+            cmd = [cc, *ARCH, "-shared", "-cudart", "static", *objs[lib], "-o", tmp]
+            p = subprocess.run(cmd, capture_output=True, text=True)
+            if p.returncode != 0:
+                sys.stderr.write(p.stdout + p.stderr)
+                raise RuntimeError("link failed: " + " ".join(cmd))
+            os.replace(tmp, lib)
     return LIB
 
 

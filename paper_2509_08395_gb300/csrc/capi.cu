@@ -119,6 +119,7 @@ static std::string query_error_text(uint32_t e) {
     if (e & kErrQueryDup) m += "a dim repeated within a query; ";
     if (e & kErrQueryTooLong) m += "a query with more than 2048 entries; ";
     if (e & kErrCandOverflow) m += "candidate buffer overflow; ";
+    if (e & kErrBounds) m += "an offset or id out of bounds (checked build; the access was skipped); ";
     if (e & kErrTimeout) m += "a bounded device wait gave up; ";
     return m;
 }
@@ -455,6 +456,39 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
         return from_cuda(e);
     }
     return st;
+}
+
+sindi_status sindi_merge_topk(const uint32_t* ids, const float* scores, int32_t n_shards, int64_t n_queries,
+                              uint32_t k_in, const int64_t* id_offset, uint32_t k, uint32_t* out_ids,
+                              float* out_scores, void* stream) {
+    NvtxRange range("sindi_merge_topk n_shards=%lld n_queries=%lld", (long long)n_shards, (long long)n_queries);
+    set_last_error("");
+    if (n_shards < 1 || (uint32_t)n_shards > kMaxShards || k_in < 1 || k < 1 || k > kMaxK ||
+        (uint64_t)n_shards * k_in > kMaxShardEntries || n_queries < 0 || n_queries > 0x7FFFFFFFLL || !id_offset) {
+        set_last_error("1 <= n_shards <= 64, k_in >= 1, n_shards * k_in <= 8192, 1 <= k <= 1024, "
+                       "0 <= n_queries < 2^31, id_offset not NULL");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    if (n_queries == 0) return SINDI_OK;
+    if (!ids || !scores || !out_ids || !out_scores || where_is(ids) != Where::Device ||
+        where_is(scores) != Where::Device || where_is(out_ids) != Where::Device ||
+        where_is(out_scores) != Where::Device) {
+        set_last_error("ids, scores and both outputs must be device memory");
+        return SINDI_ERR_INVALID_ARG;
+    }
+    for (int32_t s = 0; s < n_shards; s++) {
+        if (id_offset[s] < 0 || id_offset[s] >= 0xFFFFFFFFLL) {
+            set_last_error("id_offset out of range: 0 <= id_offset < 0xFFFFFFFF");
+            return SINDI_ERR_INVALID_ARG;
+        }
+    }
+    try {
+        merge_shards(ids, scores, (uint32_t)n_shards, n_queries, k_in, id_offset, k, out_ids, out_scores,
+                     static_cast<cudaStream_t>(stream));
+    } catch (const CudaError& e) {
+        return from_cuda(e);
+    }
+    return SINDI_OK;
 }
 
 sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_indptr, const int32_t* q_indices,

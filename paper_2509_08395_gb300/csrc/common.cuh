@@ -8,6 +8,7 @@
 #include <cstring>
 #include <string>
 
+#include "checks.cuh"
 #include "sindi.h"
 
 namespace sindi {
@@ -21,6 +22,8 @@ constexpr int64_t kMaxRowNnz = 16384;        // longest document row the build s
 constexpr uint32_t kMaxK = 1024;
 constexpr uint32_t kMaxGamma = 8192;
 constexpr int kMaxQueryTerms = 4096;         // per query (the smem term table holds them)
+constexpr uint32_t kMaxShards = 64;          // sindi_merge_topk: shards per merge
+constexpr uint32_t kMaxShardEntries = 8192;  // sindi_merge_topk: n_shards * k_in (one block's shared memory)
 
 // Device error word bits (sticky until sindi_check clears them).
 enum : uint32_t {
@@ -34,6 +37,7 @@ enum : uint32_t {
     kErrDocDup = 1u << 11,         // a dim repeated within one document
     kErrDocTooLong = 1u << 12,     // a document row longer than kMaxRowNnz
     kErrCandOverflow = 1u << 16,   // more window candidates than the buffer holds
+    kErrBounds = 1u << 17,         // checked build: an offset or id out of bounds (access skipped)
     kErrTimeout = 1u << 24,        // a bounded wait gave up
 };
 
@@ -48,11 +52,25 @@ struct DevIndex {
     const uint16_t* pid;     // [P] i mod lambda
     const void* pval;        // [P] float | __half | e4m3 code
     const float* scale;      // [dim]
+    uint64_t pcap;           // entries of pid / pval (postings rounded up to 8)
+    int64_t doc_nnz;         // entries of the unpruned documents
     const int64_t* indptr;   // unpruned documents (reordering)
     const int32_t* indices;
     const float* values;
     uint32_t* err;           // device error word
 };
+
+// The checked build's test of one bound: records a failure in the error word
+// and returns false; the normal build returns true and the test compiles away.
+#ifdef __CUDACC__
+__device__ __forceinline__ bool checked(bool ok, uint32_t* err) {
+    if (kChecks && !ok) {
+        atomicOr(err, kErrBounds);
+        return false;
+    }
+    return true;
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // Ordering keys. A result (score s, document id i) maps to a 64-bit key that

@@ -81,6 +81,8 @@ struct IndexImpl {
         d.pid = pid;
         d.pval = pval;
         d.scale = scale;
+        d.pcap = (uint64_t)((postings + 7) & ~(int64_t)7);
+        d.doc_nnz = doc_nnz;
         d.indptr = indptr;
         d.indices = indices;
         d.values = values;
@@ -109,6 +111,10 @@ constexpr size_t kNoAllocScratchBytes = (size_t)SINDI_NOALLOC_SCRATCH_BYTES;
 sindi_status search_noalloc_impl(const IndexImpl& ix, const int64_t* q_indptr, const int32_t* q_indices,
                                  const float* q_values, int64_t n_queries, const sindi_search_params& prm,
                                  uint32_t* out_ids, float* out_scores, cudaStream_t stream);
+
+// sindi_merge_topk on the current device: device arrays, sizes checked by the caller (search.cu).
+void merge_shards(const uint32_t* ids, const float* scores, uint32_t n_shards, int64_t n_queries, uint32_t k_in,
+                  const int64_t* id_offset, uint32_t k, uint32_t* out_ids, float* out_scores, cudaStream_t stream);
 
 // Sets the shared-memory limits of the search kernels on `device` (once).
 void configure_search_kernels(int device);

@@ -208,11 +208,14 @@ __device__ __forceinline__ void load_segment_chunk(const DevIndex& ix, uint32_t 
     for (int u = 0; u < kChunkU; u++) k.v[u] = 0.0f;
 #pragma unroll
     for (int u = 0; u < kChunkU / 2; u++) k.id2[u] = 0;
+    k.lm = 0;
+    if (!checked(segment_in_bounds(ps, pe, ix.pcap), ix.err)) return;
     if (pe - ps >= kVecMin) {
         const uint32_t q0 = (ps & ~7u) + off + (uint32_t)lane * kChunkU;
         const uint32_t lo = ps > q0 ? ps - q0 : 0u;  // < 8: only the segment's first group
         const uint32_t hi = pe > q0 ? min(pe - q0, (uint32_t)kChunkU) : 0u;
         k.lm = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+        if (k.lm && !checked(group_in_bounds(q0, ix.pcap), ix.err)) k.lm = 0;
         if (k.lm) {
             load_ids8(ix.pid, q0, k.id2);
             load_values8<DT>(ix.pval, q0, k.v);
@@ -248,10 +251,11 @@ __device__ __forceinline__ uint32_t chunk_slot(const Chunk& k, int u) {
 
 // Adds a chunk with shared-memory atomics (segments of different terms may
 // run at once and meet on a slot).
-__device__ __forceinline__ void add_chunk(float* A, const Chunk& k) {
+__device__ __forceinline__ void add_chunk(float* A, uint32_t lambda, uint32_t* err, const Chunk& k) {
 #pragma unroll
     for (int u = 0; u < kChunkU; u++)
-        if (k.lm & (1u << u)) atomicAdd(&A[chunk_slot(k, u)], k.wq * k.v[u]);
+        if ((k.lm & (1u << u)) && checked(slot_in_bounds(chunk_slot(k, u), lambda), err))
+            atomicAdd(&A[chunk_slot(k, u)], k.wq * k.v[u]);
 }
 
 // Chunks of a segment of at least kVecMin postings.
@@ -359,7 +363,7 @@ __device__ uint32_t build_term_table(const ScanArgs& a, uint32_t w, int64_t qb, 
         const float qv = a.q_values[qb + c0 + tid];
         uint32_t start = 0, len = 0;
         float wq = 0.0f;
-        if (j >= 0 && j < ix.dim && isfinite(qv)) {
+        if (j >= 0 && j < ix.dim && isfinite(qv) && checked(list_in_bounds(j, w, ix.dim, ix.sigma), ix.err)) {
             const uint64_t sg = (uint64_t)j * ix.sigma + w;
             start = ix.seg[sg];
             len = ix.seg[sg + 1] - start;
@@ -398,7 +402,7 @@ __device__ __forceinline__ void accumulate_table(const DevIndex& ix, const uint3
         const uint32_t cn = c + NW;
         Chunk nxt;
         if (cn < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, cn, lane, nxt);
-        add_chunk(A, cur);
+        add_chunk(A, ix.lambda, ix.err, cur);
         cur = nxt;
         c = cn;
     }
@@ -1009,8 +1013,8 @@ struct GroupScanArgs {
 // Adds a chunk of union term t into the window of every query of the group
 // that holds the term (shared-memory atomics: chunks of different terms run
 // at once and may meet on a slot).
-__device__ __forceinline__ void add_chunk_holders(float* A, uint32_t stride, uint32_t mask, const float* w,
-                                                  const Chunk& k) {
+__device__ __forceinline__ void add_chunk_holders(float* A, uint32_t stride, uint32_t lambda, uint32_t* err,
+                                                  uint32_t mask, const float* w, const Chunk& k) {
     while (mask) {
         const int i = __ffs(mask) - 1;
         mask &= mask - 1u;
@@ -1018,7 +1022,8 @@ __device__ __forceinline__ void add_chunk_holders(float* A, uint32_t stride, uin
         float* Ai = A + (size_t)i * stride;
 #pragma unroll
         for (int u = 0; u < kChunkU; u++)
-            if (k.lm & (1u << u)) atomicAdd(Ai + chunk_slot(k, u), wq * k.v[u]);
+            if ((k.lm & (1u << u)) && checked(slot_in_bounds(chunk_slot(k, u), lambda), err))
+                atomicAdd(Ai + chunk_slot(k, u), wq * k.v[u]);
     }
 }
 
@@ -1142,8 +1147,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) group_scan_kernel(GroupSc
         // ---- the segment I_{j,w} of every union term, and the chunks that tile it
         uint32_t nch = 0;
         if (tid < (int)nu) {
-            const uint64_t sg = (uint64_t)t_start[tid] * ix.sigma + w;
-            const uint32_t start = ix.seg[sg], len = ix.seg[sg + 1] - start;
+            uint32_t start = 0, len = 0;
+            if (checked(list_in_bounds((int32_t)t_start[tid], w, ix.dim, ix.sigma), ix.err)) {
+                const uint64_t sg = (uint64_t)t_start[tid] * ix.sigma + w;
+                start = ix.seg[sg];
+                len = ix.seg[sg + 1] - start;
+            }
             t_start[tid] = start;
             t_end[tid] = start + len;
             nch = len >= kVecMin ? long_segment_chunks(start, start + len) : (len ? 1u : 0u);
@@ -1172,7 +1181,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) group_scan_kernel(GroupSc
                 Chunk nxt;
                 int tn = 0;
                 if (cn < n_chunks) tn = load_c(cn, nxt);
-                add_chunk_holders(A, lam4, t_mask[tc], t_w + (size_t)tc * kMaxGroup, cur);
+                add_chunk_holders(A, lam4, lambda, ix.err, t_mask[tc], t_w + (size_t)tc * kMaxGroup, cur);
                 cur = nxt;
                 tc = tn;
                 c = cn;
@@ -1361,7 +1370,8 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const uint32_t i = base + (uint32_t)(u * kMergeThreads) + threadIdx.x;
-                if (i < C && (uint32_t)(kk[u] >> kKeyBinShift) >= bstar) {
+                if (i < C && (uint32_t)(kk[u] >> kKeyBinShift) >= bstar &&
+                    checked(doc_in_bounds(key_id(kk[u]), a.ix.n_docs), a.ix.err)) {
                     const uint32_t pos = atomicAdd(&s_n, 1u);
                     if (pos < ws.fcap) sbuf[pos] = kk[u];
                 }
@@ -1406,7 +1416,8 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 const uint32_t i = base + (uint32_t)(u * kMergeThreads) + threadIdx.x;
-                if (i < hi && (uint32_t)(kk[u] >> kKeyBinShift) >= bstar) {
+                if (i < hi && (uint32_t)(kk[u] >> kKeyBinShift) >= bstar &&
+                    checked(doc_in_bounds(key_id(kk[u]), a.ix.n_docs), a.ix.err)) {
                     const uint32_t pos = atomicAdd(&s_n, 1u);
                     if (pos < ws.fcap) sbuf[pos] = kk[u];
                 }
@@ -1461,6 +1472,78 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Merge of document-sharded result rows (sindi_merge_topk): shard s searched
+// the documents from id_offset[s] on as an index of its own; its rows hold
+// local ids. One block per query gathers every shard's row with ids made
+// global, keeps the best k by the search's own order (score desc, id asc) and
+// writes them sorted, padded like a search row.
+// ---------------------------------------------------------------------------
+struct MergeShardsArgs {
+    const uint32_t* ids;      // [n_shards][n_queries][k_in]
+    const float* scores;
+    int64_t n_queries;
+    uint32_t n_shards, k_in, k;
+    uint32_t* out_ids;        // [n_queries][k]
+    float* out_scores;
+    int64_t offset[kMaxShards];
+};
+
+constexpr int kShardMergeThreads = 256;
+
+__global__ void __launch_bounds__(kShardMergeThreads) merge_shards_kernel(MergeShardsArgs a) {
+    extern __shared__ uint64_t sk[];          // [n_shards * k_in]
+    __shared__ uint64_t sel[kMaxK];
+    __shared__ uint32_t hist256[256];
+    __shared__ uint32_t st[4];
+    __shared__ uint32_t s_n;
+    const int64_t q = blockIdx.x;
+    const uint32_t n_all = a.n_shards * a.k_in;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    // every shard's valid entries, global ids, as order keys (padding dropped)
+    for (uint32_t i = threadIdx.x; i < n_all; i += kShardMergeThreads) {
+        const uint32_t sh = i / a.k_in, j = i - sh * a.k_in;
+        const size_t at = ((size_t)sh * a.n_queries + q) * a.k_in + j;
+        const uint32_t id = a.ids[at];
+        if (id != 0xFFFFFFFFu) {
+            const int64_t gid = (int64_t)id + a.offset[sh];
+            sk[atomicAdd(&s_n, 1u)] = result_key(a.scores[at], (uint32_t)gid);
+        }
+    }
+    __syncthreads();
+    const uint32_t n = s_n;
+    const uint32_t g = n < a.k ? n : a.k;
+    __syncthreads();
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    auto key_of = [&](int i) -> uint64_t { return sk[i]; };
+    const uint64_t T = n > g ? block_select_threshold<kShardMergeThreads>(key_of, (int)n, (int)g, hist256, st) : 0ull;
+    gather_at_least<kShardMergeThreads>(key_of, n, T, sel, kMaxK, &s_n);
+    write_sorted_results<kShardMergeThreads>(sel, (int)min(s_n, (uint32_t)kMaxK), a.k, a.out_ids, a.out_scores, q);
+}
+
+void merge_shards(const uint32_t* ids, const float* scores, uint32_t n_shards, int64_t n_queries, uint32_t k_in,
+                  const int64_t* id_offset, uint32_t k, uint32_t* out_ids, float* out_scores, cudaStream_t stream) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int device = 0;
+    SINDI_CUDA(cudaGetDevice(&device));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (std::find(done.begin(), done.end(), device) == done.end()) {
+            SINDI_CUDA(cudaFuncSetAttribute(merge_shards_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(kMaxShardEntries * 8)));
+            done.push_back(device);
+        }
+    }
+    MergeShardsArgs a{ids, scores, n_queries, n_shards, k_in, k, out_ids, out_scores, {}};
+    for (uint32_t s = 0; s < n_shards; s++) a.offset[s] = id_offset[s];
+    const size_t smem = (size_t)n_shards * k_in * 8;
+    merge_shards_kernel<<<(unsigned)n_queries, kShardMergeThreads, smem, stream>>>(a);
+    SINDI_CUDA(cudaGetLastError());
+}
+
 struct RerankArgs {
     DevIndex ix;
     const int64_t* q_indptr;
@@ -1502,7 +1585,9 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(RerankArgs a) {
     if (idx < g) {
         const uint64_t key = ws.top[(size_t)y * ws.top_cap + idx];
         const uint32_t id = key_id(key);
-        const int64_t b = a.ix.indptr[id], e = a.ix.indptr[id + 1];
+        const bool id_ok = checked(doc_in_bounds(id, a.ix.n_docs), a.ix.err);
+        const int64_t b = id_ok ? a.ix.indptr[id] : 0, e0 = id_ok ? a.ix.indptr[id + 1] : 0;
+        const int64_t e = checked(row_in_bounds(b, e0, a.ix.doc_nnz), a.ix.err) ? e0 : b;
         float acc = 0.0f;
         // the row's entries, up to 16 * kRerankU at a time, all loads issued before the first is used
         for (int64_t p0 = b; p0 < e; p0 += 16 * kRerankU) {

@@ -89,6 +89,9 @@ _SIGS = {
     "sindi_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sindi_index_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(sindi_index_info_t)]),
     "sindi_index_export": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "sindi_merge_topk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
     "sindi_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sindi_index_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "sindi_index_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -113,11 +116,13 @@ _SIGS = {
 }
 
 
-def load(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load lib/libsindi.so (raises if it has not been built)."""
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load lib/libsindi.so, or the library SINDI_LIBRARY names (e.g. lib/libsindi_checked.so, the build with
+    every bounds check compiled in); raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("SINDI_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"native library missing: {path} (build it with __graft_entry__.build() or "
                            "python -m paper_2509_08395_gb300.build_native)")
@@ -297,6 +302,26 @@ def sindi_version() -> str:
 
 
 # ---- convenience wrapper ------------------------------------------------------------
+def sindi_merge_topk(ids, scores, id_offsets, k: int, out=None, stream=None):
+    """Top-k over document shards: ids/scores are device tensors [n_shards, n_queries, k_in] of per-shard rows
+    (local ids), id_offsets the global id of each shard's first document. Returns (ids, scores) [n_queries, k]."""
+    import torch
+
+    S, nq, k_in = ids.shape
+    off = np.ascontiguousarray(np.asarray(id_offsets, dtype=np.int64))
+    if off.shape != (S,):
+        raise ValueError("one id offset per shard")
+    if out is None:
+        out = (torch.empty((nq, k), dtype=torch.int32, device=ids.device),
+               torch.empty((nq, k), dtype=torch.float32, device=ids.device))
+    ids = ids.contiguous()
+    scores = scores.contiguous()
+    _check(load().sindi_merge_topk(_ptr(ids, np.uint32), _ptr(scores, np.float32), int(S), int(nq), int(k_in),
+                                   off.ctypes.data, int(k), _ptr(out[0], np.uint32), _ptr(out[1], np.float32),
+                                   _stream(stream, ids, out[0])), "sindi_merge_topk")
+    return out
+
+
 class Index:
     """A device-resident SINDI index (owns the C handle)."""
 

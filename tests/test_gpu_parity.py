@@ -516,3 +516,25 @@ def test_full_size_pruned_1m_sampled():
         truth, _ = oracle.brute_force(D, Q, r, w.k)
         recalls.append(oracle.recall(ids[r], truth))
     assert np.mean(recalls) >= 0.99, recalls
+
+
+@pytest.mark.parametrize("d,mode", [(10_000, "plain"), (30_000, "batched"), (100_000, "batched")])
+def test_uniform_sparsity_workload_parity(d, mode):
+    """The uniform-random sparsity sweep's workload (Sec. 5, RANDOM-1M stand-in: 120 entries per row, dims and
+    values uniform), scaled to 60,000 documents: coarse top-k against the oracle, and the reordered answer with
+    pruning (alpha 0.7) against Algorithm 4."""
+    w = datagen.WORKLOADS[f"uniform-1m-d{d // 1000}k"].scaled(n_docs=60_000, n_queries=16)
+    ip, ix, v = datagen.docs(w)
+    qp, qx, qv = datagen.queries(w)
+    D, Q = oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+    I1 = oracle.Index(D, window=8192, alpha=1.0)
+    I7 = oracle.Index(D, window=8192, alpha=0.7)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=8192, alpha=1.0) as idx:
+        ids, sc = run_search(idx, qp, qx, qv, k=50, gamma=0, mode=mode)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=8192, alpha=0.7) as idx:
+        assert idx.info["postings"] == I7.postings
+        rids, rsc = run_search(idx, qp, qx, qv, k=50, gamma=500, mode=mode)
+    for r in range(Q.n):
+        oi, os_ = I1.search(Q, r, k=114, gamma=0)
+        check_ranked(ids[r], sc[r], oi, os_, 50, D.n, what=f"d {d} exact query {r}")
+        check_reranked(rids[r], rsc[r], D, Q, r, I7, 50, 500, what=f"d {d} alpha 0.7 query {r}")

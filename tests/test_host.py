@@ -166,7 +166,7 @@ def test_autotuner_choice_logic(monkeypatch, tmp_path):
         def __exit__(self, *exc):
             return False
 
-        def search(self, *q, k, gamma, mode="batched", block=0, out=None):
+        def search(self, *q, k, gamma, mode="batched", block=0, out=None, group=1):
             if self.alpha == 1.0 and gamma == 0:          # the exact reference
                 return _FakeTensor(truth.view(np.int32)), None
             ids = truth.copy()
@@ -176,8 +176,10 @@ def test_autotuner_choice_logic(monkeypatch, tmp_path):
 
     speed = {("plain", 0): 100.0, ("batched", 0): 150.0, ("batched", 512): 170.0, ("plain", 512): 90.0}
 
-    def fake_time(idx, q, k_, gamma, mode, block, repeats):
-        return speed[(mode, block)] * (2.0 if idx.window == 8192 else 1.0) / (gamma / 100.0), None
+    def fake_time(idx, q, k_, gamma, mode, block, repeats, group=1):
+        # query groups of 2 help the batched 512-thread scan by 10%
+        g = 1.1 if (mode, block, group) == ("batched", 512, 2) else (0.9 if group == 2 else 1.0)
+        return speed[(mode, block)] * g * (2.0 if idx.window == 8192 else 1.0) / (gamma / 100.0), None
 
     monkeypatch.setattr(autotune.sindi, "Index", FakeIndex)
     monkeypatch.setattr(autotune, "_time_search", fake_time)
@@ -187,16 +189,18 @@ def test_autotuner_choice_logic(monkeypatch, tmp_path):
     docs = (_FakeTensor(np.zeros(1001)), _FakeTensor(np.zeros(5)), _FakeTensor(np.zeros(5)))
     cache = str(tmp_path / "tune.json")
     res = autotune.autotune(*docs, 64, *q, k=k, alpha=0.5, windows=[4096, 8192], gammas=(100, 200, 300, 500),
-                            blocks=(0, 512), modes=("plain", "batched"), cache=cache)
+                            blocks=(0, 512), modes=("plain", "batched"), cache=cache, groups=(1, 2))
     ch = res["choice"]
-    # window 8192 reaches the target at gamma 200: 170 * 2 / 2 = 170 QPS beats window 4096 at gamma 300 (56.7)
-    assert (ch["window"], ch["gamma"], ch["mode"], ch["block"]) == (8192, 200, "batched", 512)
+    # window 8192 reaches the target at gamma 200: 170 * 1.1 * 2 / 2 = 187 QPS (batched, 512 threads, groups of
+    # 2) beats window 4096 at gamma 300 (62.3); the plain schedule is timed without groups
+    assert (ch["window"], ch["gamma"], ch["mode"], ch["block"], ch["group"]) == (8192, 200, "batched", 512, 2)
+    assert {r["group"] for r in res["table"] if r.get("mode") == "plain"} == {1}
     assert ch["recall"] == 1.0 and res["gpu"] == "fake GPU"
     tried = {(r["window"], r["gamma"]) for r in res["table"] if "qps" not in r}
     assert tried == {(4096, 100), (4096, 200), (4096, 300), (8192, 100), (8192, 200)}
     monkeypatch.setattr(autotune, "_time_search", lambda *a, **kw: (_ for _ in ()).throw(AssertionError("timed")))
     again = autotune.autotune(*docs, 64, *q, k=k, alpha=0.5, windows=[4096, 8192], gammas=(100, 200, 300, 500),
-                              blocks=(0, 512), modes=("plain", "batched"), cache=cache)
+                              blocks=(0, 512), modes=("plain", "batched"), cache=cache, groups=(1, 2))
     assert again["choice"] == ch                          # served from the cache, nothing timed
     none = autotune.autotune(*docs, 64, *q, k=k, alpha=0.5, windows=[4096], gammas=(100, 200), blocks=(0,),
                              modes=("plain",))
@@ -324,3 +328,58 @@ def test_serving_load_generator_is_open_loop():
     # bad arguments are refused before anything is submitted
     assert gen.sindi_load_open_loop(None, None, None, None, None, None, 0, 10, 1.0, 1.0, 1,
                                     ctypes.byref(res)) == -1
+
+
+def test_window_cost_model_fit():
+    """The autotuner's window prior (Sec. 3.4's double power law T = c_rand l^a + c_evict l^-b + c0): exact
+    data from known parameters gives back the closed-form optimum l* = (c_evict b / (c_rand a))^(1/(a+b)); noisy
+    data stays near it; a curve with no rising term has no optimum and keeps every candidate."""
+    from paper_2509_08395_gb300 import autotune as at
+
+    lam = np.array([2048, 4096, 8192, 16384, 32768], np.float64)
+    t = 3e-9 * lam ** 0.7 + 2e-3 * lam ** -0.9 + 1e-6
+    f = at.fit_window_model(lam, t)
+    want = (2e-3 * 0.9 / (3e-9 * 0.7)) ** (1 / 1.6)
+    assert abs(f["lambda_star"] / want - 1) < 1e-6, (f, want)
+    assert at.windows_near(f["lambda_star"], [2048, 4096, 8192, 16384, 32768]) == [2048, 4096, 8192]
+    rng = np.random.default_rng(3)
+    fn = at.fit_window_model(lam, t * (1 + 0.01 * rng.standard_normal(len(t))))
+    assert 0.5 < fn["lambda_star"] / want < 2.0, fn
+    falling = 2e-3 * lam ** -0.9 + 1e-6
+    fd = at.fit_window_model(lam, falling)
+    assert fd["lambda_star"] is None or fd["lambda_star"] > 1e6, fd
+    if fd["lambda_star"] is None:
+        assert at.windows_near(None, [4096, 2048]) == [2048, 4096]
+
+
+def test_checked_build_predicates(tmp_path):
+    """The bounds tests of the checked build (csrc/checks.cuh), compiled for the host: each accepts the last
+    valid offset or id and refuses the first invalid one."""
+    import subprocess
+
+    src = tmp_path / "checks_host.cpp"
+    src.write_text(r"""
+#include <cstdio>
+#include "checks.cuh"
+using namespace sindi;
+#define T(c) do { if (!(c)) { std::printf("failed: %s\n", #c); return 1; } } while (0)
+int main() {
+    static_assert(!kChecks, "host build: checks off unless asked for");
+    T(segment_in_bounds(0, 0, 0)); T(segment_in_bounds(5, 16, 16)); T(!segment_in_bounds(5, 17, 16));
+    T(!segment_in_bounds(9, 8, 16));
+    T(group_in_bounds(8, 16)); T(!group_in_bounds(16, 16)); T(!group_in_bounds(4, 16));
+    T(slot_in_bounds(4095, 4096)); T(!slot_in_bounds(4096, 4096));
+    T(list_in_bounds(0, 0, 1, 1)); T(list_in_bounds(29, 61, 30, 62)); T(!list_in_bounds(30, 0, 30, 62));
+    T(!list_in_bounds(-1, 0, 30, 62)); T(!list_in_bounds(0, 62, 30, 62));
+    T(doc_in_bounds(999, 1000)); T(!doc_in_bounds(1000, 1000)); T(!doc_in_bounds(0xFFFFFFFFu, 1000));
+    T(row_in_bounds(0, 0, 0)); T(row_in_bounds(3, 10, 10)); T(!row_in_bounds(3, 11, 10)); T(!row_in_bounds(5, 4, 10));
+    T(!row_in_bounds(-1, 4, 10));
+    std::printf("ok\n");
+    return 0;
+}
+""")
+    exe = tmp_path / "checks_host"
+    inc = os.path.join(ROOT, "paper_2509_08395_gb300", "csrc")
+    subprocess.run(["g++", "-std=c++17", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr

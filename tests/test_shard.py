@@ -36,6 +36,26 @@ def test_merge_topk_order_and_padding():
     assert mi.tolist() == [[5, 1, PAD_ID, PAD_ID]] and np.isneginf(ms[0, 2:]).all()
 
 
+def test_merge_topk_matches_a_per_row_sort():
+    """The vectorised host merge against a plain per-row sort by (score desc, id asc), with tied scores,
+    padding in every shard and rows with fewer than k entries."""
+    rng = np.random.default_rng(4)
+    S, nq, ks, k = 3, 50, 7, 10
+    ids = rng.permutation(10_000)[: S * nq * ks].reshape(S, nq, ks).astype(np.uint32)
+    sc = rng.integers(0, 5, (S, nq, ks)).astype(np.float32)   # many ties
+    pad = rng.random((S, nq, ks)) < 0.3
+    ids[pad] = PAD_ID
+    sc[pad] = -np.inf
+    mi, ms = merge_topk(ids, sc, k)
+    for q in range(nq):
+        items = [(-float(sc[s, q, j]), int(ids[s, q, j])) for s in range(S) for j in range(ks) if ids[s, q, j] != PAD_ID]
+        items.sort()
+        want_ids = [i for _, i in items[:k]] + [PAD_ID] * max(0, k - len(items))
+        assert mi[q].tolist() == want_ids
+        np.testing.assert_array_equal(ms[q][: len(items[:k])], [-x for x, _ in items[:k]])
+        assert np.isneginf(ms[q][len(items[:k]):]).all()
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
