@@ -240,6 +240,28 @@ def scatter_peak(window: int, block: int = 512):
     return rate.value if rc == 0 else None
 
 
+def scatter_forms(window: int, block: int = 512):
+    """adds/s of five forms of the shared-memory scatter (bench_native/scatter_peak.cu): the scan's FP32
+    atomicAdd at random slots and with the 32 lanes on 32 banks, a plain load-add-store by the warp that owns
+    the slots (random, and on 32 banks), and a uint32 atomicAdd. None if the probe is unavailable."""
+    path = bench_native_lib("libsindi_probe.so")
+    if path is None:
+        return None
+    lib = ctypes.CDLL(path)
+    f = lib.sindi_probe_scatter_mode
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]
+    w = 1 << (max(32 * (block // 32), int(window)) - 1).bit_length()   # a power of two the probe accepts
+    w = min(w, 32768)
+    out = {"window": w, "block": block, "unit": "adds/s"}
+    for mode, name in enumerate(("f32_atomic_random", "f32_atomic_banks", "owner_rmw_random", "owner_rmw_banks",
+                                 "u32_atomic_random")):
+        rate = ctypes.c_double(0.0)
+        out[name] = rate.value if f(mode, w, block, 256, ctypes.byref(rate)) == 0 and f(
+            mode, w, block, 256, ctypes.byref(rate)) == 0 else None
+    return out
+
+
 def _timed_qps(torch, fn, nq, reps, flush, stream):
     for _ in range(3):  # warm: a repeated plain call is recorded as a graph on its second run
         fn()
@@ -790,6 +812,7 @@ def main():
     adds_per_s = float(touched.sum()) * args.steps / (st2["scan_ms"] / 1000.0)
     adds_per_s_step = float(touched.sum()) * args.steps / (dev_ms_max / 1000.0)
     adds_peak = scatter_peak(int(info["window"]))
+    adds_forms = scatter_forms(int(info["window"])) if rank == 0 else None
     peak, peak_kind = measured_hbm_peak()
     sha = source_sha()
 
@@ -1034,7 +1057,8 @@ def main():
                                       "frac_one_chain": adds_per_s / adds_peak if adds_peak else None,
                                       "unit": "posting updates/s",
                                       "peak_from": "measured: FP32 shared-memory atomicAdd probe at random slots "
-                                                   "of a window-sized array, every SM full (libsindi_probe)"}},
+                                                   "of a window-sized array, every SM full (libsindi_probe)",
+                                      "forms": adds_forms}},
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
         "clocks": clocks,
