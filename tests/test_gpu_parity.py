@@ -390,6 +390,22 @@ def test_beta_query_pruning_parity(pruned_small, beta, mode):
     assert touched <= 2
 
 
+@pytest.mark.skipif(torch.cuda.device_count() < 2, reason="needs two GPUs in one process")
+def test_beta_query_pruning_on_two_devices_in_one_process(pruned_small):
+    """beta < 1 on a second GPU of the same process: the query-pruning kernel's shared-memory limit is set per
+    device with the other search kernels, so the second device's search runs and equals the first's."""
+    w, (ip, ix, v), (qp, qx, qv), D, Q = pruned_small
+    out = []
+    for d in (0, 1):
+        dv = torch.device("cuda", d)
+        to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dv)  # noqa: E731
+        with torch.cuda.device(dv), sindi.Index(to(ip), to(ix), to(v), w.dim, window=4096, alpha=0.5) as idx:
+            ids, sc = idx.search(to(qp), to(qx), to(qv), k=10, gamma=300, beta=0.5)
+            idx.check()
+            out.append(ids.cpu().numpy())
+    np.testing.assert_array_equal(out[0], out[1])
+
+
 @pytest.mark.parametrize("dtype", ["f16", "f8"])
 def test_reduced_precision_coarse_parity(pruned_small, dtype):
     """FP16 / E4M3 postings: GPU coarse scores vs the oracle on the same dequantised values."""
