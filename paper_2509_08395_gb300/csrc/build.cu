@@ -620,8 +620,34 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     P.free(sdim);
     P.free(sdoc);
     P.free(sval);
-    SINDI_CUDA(cudaStreamSynchronize(stream));
+    ix.nonneg = postings_nonnegative(ix, stream);  // synchronises the stream
     return SINDI_OK;
+}
+
+// Sets *flag when a stored posting value has its sign bit set (FP32, binary16
+// or E4M3 alike: the top bit of the stored word).
+__global__ void negative_values_kernel(const unsigned char* pval, int64_t P, int vbytes, uint32_t* flag) {
+    bool neg = false;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P && !neg;
+         p += (int64_t)gridDim.x * blockDim.x)
+        neg = (pval[p * vbytes + vbytes - 1] & 0x80u) != 0;  // little-endian: the sign is in the last byte
+    if (__syncthreads_or(neg) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+bool postings_nonnegative(const IndexImpl& ix, cudaStream_t stream) {
+    Pool P{ix.pool, stream};
+    uint32_t* flag = P.alloc<uint32_t>(1);
+    SINDI_CUDA(cudaMemsetAsync(flag, 0, 4, stream));
+    if (ix.postings > 0) {
+        negative_values_kernel<<<grid_for(ix.postings, 256), 256, 0, stream>>>(
+            static_cast<const unsigned char*>(ix.pval), ix.postings, (int)ix.value_bytes(), flag);
+        SINDI_CUDA(cudaGetLastError());
+    }
+    uint32_t h = 0;
+    SINDI_CUDA(cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, stream));
+    P.free(flag);
+    SINDI_CUDA(cudaStreamSynchronize(stream));
+    return h == 0;
 }
 
 }  // namespace sindi

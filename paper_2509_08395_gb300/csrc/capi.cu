@@ -770,6 +770,7 @@ sindi_status sindi_index_load(const char* path, void* stream, sindi_index** out)
             return SINDI_ERR_INVALID_DATA;
         }
         SINDI_CUDA(cudaStreamSynchronize(s));
+        ix.nonneg = postings_nonnegative(ix, s);
     } catch (const CudaError& e) {
         sindi_status st = from_cuda(e);
         free_index_memory(ix, s);

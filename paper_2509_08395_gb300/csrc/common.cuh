@@ -54,6 +54,7 @@ struct DevIndex {
     const float* scale;      // [dim]
     uint64_t pcap;           // entries of pid / pval (postings rounded up to 8)
     int64_t doc_nnz;         // entries of the unpruned documents
+    int32_t nonneg;          // 1: no stored posting value is negative
     const int64_t* indptr;   // unpruned documents (reordering)
     const int32_t* indices;
     const float* values;

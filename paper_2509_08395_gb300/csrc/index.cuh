@@ -26,6 +26,7 @@ struct IndexImpl {
     uint32_t prune_n = 0;
     int64_t doc_nnz = 0;
     int64_t postings = 0;
+    bool nonneg = false;         // every stored posting value >= 0 (set by the build and by a load)
     cudaMemPool_t pool = nullptr;
 
     // unpruned documents (Algorithm 3 keeps D for reordering)
@@ -83,6 +84,7 @@ struct IndexImpl {
         d.scale = scale;
         d.pcap = (uint64_t)((postings + 7) & ~(int64_t)7);
         d.doc_nnz = doc_nnz;
+        d.nonneg = nonneg ? 1 : 0;
         d.indptr = indptr;
         d.indices = indices;
         d.values = values;
@@ -94,6 +96,9 @@ struct IndexImpl {
 };
 
 sindi_status build_lists(IndexImpl& ix, cudaStream_t stream);
+
+// True when no stored posting value is negative (one pass over the values; synchronises `stream`).
+bool postings_nonnegative(const IndexImpl& ix, cudaStream_t stream);
 
 // Sets kErrDocIndptr in *err unless indptr[0] == 0 and indptr never decreases.
 void launch_validate_indptr(const int64_t* indptr, int64_t n, uint32_t* err, cudaStream_t stream);

@@ -425,7 +425,7 @@ __device__ __forceinline__ float key_floor_float(uint32_t k) {
 // Every thread of the group S (NW warps) calls it; the workspace must be free.
 template <typename S, int NW>
 __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uint32_t y, bool bounded, uint32_t pbin,
-                              const CutScratch& cs) {
+                              const CutScratch& cs, bool skip_zero = false) {
     constexpr int NT = S::kThreads;
     const DevIndex& ix = a.ix;
     const int tid = S::tid();
@@ -445,19 +445,24 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
     const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
     auto key_of = [&](int i) -> uint64_t { return result_key(A[i], (uint32_t)(gbase + i)); };
     uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
-    if (bounded) {
+    if (bounded || skip_zero) {
         // g candidates at or above bin pbin already exist, so only slots in
-        // bins >= pbin can be in the answer. When they fit the window's
-        // budget, emit all of them: no window histogram, no cut. One pass:
-        // every warp stages its slots in its own share of the staging area
-        // (in order, no atomics); then one reservation for the group.
+        // bins >= pbin can be in the answer. With skip_zero (every score of
+        // the query is >= 0 and the earlier windows hold at least g slots, all
+        // with scores >= 0 and lower ids), a slot whose score is exactly 0 can
+        // never be either: so only positive slots count. When the slots that
+        // can count fit the window's budget, emit all of them: no window
+        // histogram, no cut. One pass: every warp stages its slots in its own
+        // share of the staging area (in order, no atomics); then one
+        // reservation for the group.
         const unsigned lt = (1u << lane) - 1u;
         const uint32_t share = stage_cap / NW;
         uint64_t* mine_st = stage + (size_t)warp * share;
         // the window 4 slots per lane (one 16-byte load, one compare each against
-        // the least score in bin pbin); the per-slot work runs only for the rare
-        // 128-slot spans that hold a candidate
-        const float thr = key_floor_float(pbin << (32 - kHistBits));
+        // the least score that can count); the per-slot work runs only for the
+        // rare 128-slot spans that hold a candidate
+        float thr = bounded ? key_floor_float(pbin << (32 - kHistBits)) : -INFINITY;
+        if (skip_zero && thr <= 0.0f) thr = __int_as_float(1);  // the least positive float (NaN stays NaN)
         const int n4 = (n_eff + 3) >> 2;
         const float4* A4 = reinterpret_cast<const float4*>(A);
         auto scan_bounded = [&](auto&& emit) -> uint32_t {
@@ -803,7 +808,11 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
         __syncthreads();
     }
     const CutScratch cs{hist, hist2, region, (uint32_t)kRegionBytes, warp_off, red, st, &s_staged};
-    select_window<S, kScanWarps>(a, A, w, y, bounded, pbin, cs);
+    // zero-score slots cannot count once the earlier windows hold g slots, when no score can be negative
+    bool q_neg = false;
+    for (int t = threadIdx.x; t < nt; t += kScanThreads) q_neg |= a.q_values[qb + t] < 0.0f;
+    const bool skip_zero = __syncthreads_or(q_neg) == 0 && ix.nonneg && (uint64_t)w * lambda >= a.g;
+    select_window<S, kScanWarps>(a, A, w, y, bounded, pbin, cs, skip_zero);
 }
 
 // ---------------------------------------------------------------------------
@@ -1045,6 +1054,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) group_scan_kernel(GroupSc
     __shared__ uint32_t mrow[kMaxGroup];        // query row (within the launch) of each member
     __shared__ uint32_t mpre[kMaxGroup + 1];    // prefix of the members' term counts
     __shared__ int64_t mqb[kMaxGroup];          // first entry of each member's query row
+    __shared__ uint32_t s_negmask;              // bit i: member i has a negative query value
     const ScanArgs& sa = a.s;
     const DevIndex& ix = sa.ix;
     const uint32_t lambda = ix.lambda;
@@ -1084,6 +1094,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) group_scan_kernel(GroupSc
     if (tid == 0) {
         mpre[0] = 0;
         for (uint32_t i = 0; i < qn; i++) mpre[i + 1] += mpre[i];
+        s_negmask = 0;
     }
     __syncthreads();
     const uint32_t n_ent = mpre[qn];
@@ -1104,6 +1115,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) group_scan_kernel(GroupSc
             const int64_t at = mqb[i] + (e - mpre[i]);
             const int32_t j = sa.q_indices[at];
             const float qv = sa.q_values[at];
+            if (qv < 0.0f) atomicOr(&s_negmask, 1u << i);
             // entries the scan skips: dims out of range and non-finite values (the merge
             // reports them), zero weights (Definition 1: not entries)
             if (j >= 0 && j < ix.dim && isfinite(qv) && qv != 0.0f) {
@@ -1202,7 +1214,9 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) group_scan_kernel(GroupSc
         const bool bounded = st[3] >= sa.g;
         const uint32_t pbin = st[0];
         __syncthreads();
-        select_window<S, NW>(sa, A + (size_t)i * lam4, w, y, bounded, pbin, cs);
+        // zero-score slots cannot count once the earlier windows hold g slots, when no score can be negative
+        const bool skip_zero = !((s_negmask >> i) & 1u) && ix.nonneg && (uint64_t)w * lambda >= sa.g;
+        select_window<S, NW>(sa, A + (size_t)i * lam4, w, y, bounded, pbin, cs, skip_zero);
     }
 }
 

@@ -51,11 +51,18 @@ def find_bin(hist, g):
     raise AssertionError("unreachable")
 
 
-def window_emit(K, g_w, win_cap, bounded, pbin):
-    """The keys one window emits (its n_eff slots' keys K)."""
+ZERO_KEY_BITS = np.uint64(0x80000000)                 # order bits of +0.0
+
+
+def window_emit(K, g_w, win_cap, bounded, pbin, skip_zero=False):
+    """The keys one window emits (its n_eff slots' keys K). skip_zero: slots whose score is exactly 0 cannot
+    count (every score >= 0 and the earlier windows hold at least g slots)."""
     b = bins_of(K)
-    if bounded:
-        hi = K[b >= pbin]
+    if bounded or skip_zero:
+        ok = b >= pbin if bounded else np.ones(len(K), bool)
+        if skip_zero:
+            ok &= (K >> np.uint64(32)) > ZERO_KEY_BITS     # score > 0
+        hi = K[ok]
         if len(hi) <= win_cap:
             return hi
     bw, above_bw, _, _ = find_bin(np.bincount(b, minlength=1 << HIST_BITS), g_w)
@@ -71,9 +78,12 @@ def window_emit(K, g_w, win_cap, bounded, pbin):
     return K[K >= thr]
 
 
-def search_model(scores32, lam, g, schedule, rng):
-    """Candidates of every window under `schedule`, then the merge; returns the selected keys, best first."""
+def search_model(scores32, lam, g, schedule, rng, zero_rule="device"):
+    """Candidates of every window under `schedule`, then the merge; returns the selected keys, best first.
+    zero_rule: "device" skips zero-score slots of window w when no score is negative and w * lam >= g;
+    "off" never skips; "always" skips them whenever no score is negative (a planted mistake)."""
     n = len(scores32)
+    nonneg = bool(np.all(np.asarray(scores32) >= 0))
     sigma = -(-n // lam)
     keys = keys_of(scores32, np.arange(n))
     win_cap = 2 * min(g, lam)
@@ -88,7 +98,8 @@ def search_model(scores32, lam, g, schedule, rng):
         if snapshot is not None:
             pbin, _, _, total = find_bin(snapshot, g)
             bounded = total >= g
-        out = window_emit(K, g_w, win_cap, bounded, pbin)
+        skip = nonneg and ((zero_rule == "device" and w * lam >= g) or (zero_rule == "always" and w > 0))
+        out = window_emit(K, g_w, win_cap, bounded, pbin, skip)
         assert len(out) <= max(win_cap, g_w)
         emitted.append(out)
         np.add.at(H, bins_of(out), 1)
@@ -159,3 +170,19 @@ def test_model_keys_order_like_the_search():
     s = np.array([1.0, 2.0, 2.0, -1.0, 0.0, 0.0], np.float32)
     order = np.argsort(keys_of(s, np.arange(6)))[::-1]
     assert order.tolist() == [1, 2, 0, 4, 5, 3]
+
+
+def test_zero_skip_rule_needs_the_earlier_windows_to_hold_g_slots():
+    """The zero-score rule of the window cut: without its condition (the earlier windows hold at least g slots)
+    it drops zero-score documents that belong to the answer (fewer than g positive scores, windows smaller
+    than g); with it the selection stays exact (the parametrised test above runs the device rule)."""
+    rng = np.random.default_rng(5)
+    failed = False
+    for trial in range(40):
+        lam, g = 64, 300
+        n = 9 * lam + 1
+        s = score_pattern("sparse", n, rng)
+        want = truth(s, g)
+        assert np.array_equal(search_model(s, lam, g, "batched", rng, zero_rule="device"), want)
+        failed |= not np.array_equal(search_model(s, lam, g, "batched", rng, zero_rule="always"), want)
+    assert failed
