@@ -986,8 +986,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) scan_pipe_kernel(ScanArgs a) 
 //       build's bank-aware order is laid out for); the ids are decoded once
 //       and, for every holder, the 8 postings of a lane are added with FP32
 //       shared-memory atomics under one 8-bit lane mask.
-// Groups are consecutive query rows, or the rows of `perm` (queries sorted so
-// that a group shares its heaviest lists).
+// Groups are consecutive query rows of the launch.
 // ---------------------------------------------------------------------------
 constexpr int kMaxGroup = (int)kMaxQueryGroup;
 constexpr int kGroupEntries = 512;     // query entries hashed per pass (union terms per pass <= this)
@@ -1016,7 +1015,6 @@ struct GroupScanArgs {
     ScanArgs s;            // index, queries (rows q_first + y), g, win_cap, workspace, w0
     uint32_t Q;            // queries per group (1..kMaxGroup)
     uint32_t nq;           // query rows of the launch
-    const uint32_t* perm;  // [nq] row of the i-th query in group order, or null (consecutive rows)
 };
 
 // Adds a chunk of union term t into the window of every query of the group
@@ -1078,7 +1076,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) group_scan_kernel(GroupSc
     uint16_t* c_term = reinterpret_cast<uint16_t*>(t_w + kGroupEntries * kMaxGroup);
 
     if (tid < (int)qn) {
-        const uint32_t y = a.perm ? a.perm[first + tid] : first + (uint32_t)tid;
+        const uint32_t y = first + (uint32_t)tid;
         const int64_t r = sa.q_first + y;
         mrow[tid] = y;
         mqb[tid] = sa.q_indptr[r];
@@ -1927,7 +1925,7 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
         // query groups: one block per (group, window); groups vary fastest, so the
         // blocks of one window run together and its lists stay in L2
         const uint32_t bt = pl.block == 1024 ? 1024u : 512u;
-        const GroupScanArgs ga{sa, pl.group, nq, nullptr};
+        const GroupScanArgs ga{sa, pl.group, nq};
         launch_group_scan(ix.dtype, bt, ga, (nq + pl.group - 1) / pl.group, ix.sigma,
                           group_smem_bytes(ix.lambda, pl.group, (int)bt), stream, *chained && !ev0);
     } else if (pipe && batched) {
