@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--workload", default="pruned-1m")
     p.add_argument("--mode", choices=["plain", "batched"], default="plain")
     p.add_argument("--window", type=int, default=0, help="0 = the workload's window")
+    p.add_argument("--block", type=int, default=0, help="scan block shape (sindi_search_params.block_threads)")
+    p.add_argument("--group", type=int, default=0, help="batched schedule: queries per scan block")
     p.add_argument("--queries", type=int, default=0, help="0 = the workload's query count")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
     p.add_argument("--value-dtype", choices=["f32", "f16", "f8"], default=None,
@@ -742,7 +744,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step(mode):
-        idx.search(*q_dev, k=w.k, gamma=w.gamma, mode=mode, out=(out_ids, out_sc))
+        idx.search(*q_dev, k=w.k, gamma=w.gamma, mode=mode, out=(out_ids, out_sc), block=args.block,
+                   group=args.group if mode == "batched" else 0)
 
     for _ in range(args.warmup):
         step(args.mode)
@@ -823,12 +826,14 @@ def main():
     h_ids = torch.empty((nq, w.k), dtype=torch.int32).pin_memory()
     h_sc = torch.empty((nq, w.k), dtype=torch.float32).pin_memory()
     for _ in range(max(1, args.warmup)):
-        idx.search(h_ip, h_ix, h_v, k=w.k, gamma=w.gamma, mode=args.mode, out=(h_ids, h_sc), stream=stream.cuda_stream)
+        idx.search(h_ip, h_ix, h_v, k=w.k, gamma=w.gamma, mode=args.mode, out=(h_ids, h_sc), stream=stream.cuda_stream,
+                   block=args.block, group=args.group if args.mode == "batched" else 0)
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        idx.search(h_ip, h_ix, h_v, k=w.k, gamma=w.gamma, mode=args.mode, out=(h_ids, h_sc), stream=stream.cuda_stream)
+        idx.search(h_ip, h_ix, h_v, k=w.k, gamma=w.gamma, mode=args.mode, out=(h_ids, h_sc), stream=stream.cuda_stream,
+                   block=args.block, group=args.group if args.mode == "batched" else 0)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
     barrier(ws)
@@ -1030,6 +1035,7 @@ def main():
         "config": {"workload": w.name, "n_docs": w.docs.n_rows, "dim": w.dim, "queries_per_rank": nq,
                    "k": w.k, "gamma": w.gamma, "alpha": w.alpha, "window": info["window"],
                    "n_windows": sigma, "postings": info["postings"], "mode": args.mode,
+                   "block": args.block, "group": args.group if args.mode == "batched" else 0,
                    "batch": 1 if args.mode == "plain" else nq,
                    "l2": "flushed between steps (256 MiB write)"},
         "recall_at_k": recall,
