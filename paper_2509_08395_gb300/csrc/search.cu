@@ -354,13 +354,15 @@ struct CutScratch {
 // chunks. Every thread of the group S calls it.
 template <int DT, typename S>
 __device__ uint32_t build_term_table(const ScanArgs& a, uint32_t w, int64_t qb, int c0, int nc, uint32_t* t_start,
-                                     uint32_t* t_end, float* t_w, uint32_t* c_pre, uint16_t* c_term, uint32_t* red) {
+                                     uint32_t* t_end, float* t_w, uint32_t* c_pre, uint16_t* c_term, uint32_t* red,
+                                     uint32_t* negflag = nullptr) {
     const DevIndex& ix = a.ix;
     const int tid = S::tid();
     uint32_t nch = 0;
     if (tid < nc) {
         const int32_t j = a.q_indices[qb + c0 + tid];
         const float qv = a.q_values[qb + c0 + tid];
+        if (negflag && qv < 0.0f) *negflag = 1u;  // a negative query value (any thread may set it)
         uint32_t start = 0, len = 0;
         float wq = 0.0f;
         if (j >= 0 && j < ix.dim && isfinite(qv) && checked(list_in_bounds(j, w, ix.dim, ix.sigma), ix.err)) {
@@ -445,23 +447,23 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
     const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
     auto key_of = [&](int i) -> uint64_t { return result_key(A[i], (uint32_t)(gbase + i)); };
     uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
-    if (bounded || skip_zero) {
+    if (bounded) {
         // g candidates at or above bin pbin already exist, so only slots in
         // bins >= pbin can be in the answer. With skip_zero (every score of
         // the query is >= 0 and the earlier windows hold at least g slots, all
         // with scores >= 0 and lower ids), a slot whose score is exactly 0 can
-        // never be either: so only positive slots count. When the slots that
-        // can count fit the window's budget, emit all of them: no window
-        // histogram, no cut. One pass: every warp stages its slots in its own
-        // share of the staging area (in order, no atomics); then one
-        // reservation for the group.
+        // never be either: when the bound reaches down to 0, only positive
+        // slots count. When the slots that can count fit the window's budget,
+        // emit all of them: no window histogram, no cut. One pass: every warp
+        // stages its slots in its own share of the staging area (in order, no
+        // atomics); then one reservation for the group.
         const unsigned lt = (1u << lane) - 1u;
         const uint32_t share = stage_cap / NW;
         uint64_t* mine_st = stage + (size_t)warp * share;
         // the window 4 slots per lane (one 16-byte load, one compare each against
         // the least score that can count); the per-slot work runs only for the
         // rare 128-slot spans that hold a candidate
-        float thr = bounded ? key_floor_float(pbin << (32 - kHistBits)) : -INFINITY;
+        float thr = key_floor_float(pbin << (32 - kHistBits));
         if (skip_zero && thr <= 0.0f) thr = __int_as_float(1);  // the least positive float (NaN stays NaN)
         const int n4 = (n_eff + 3) >> 2;
         const float4* A4 = reinterpret_cast<const float4*>(A);
@@ -747,6 +749,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     __shared__ uint32_t red[kScanWarps + 1];
     __shared__ uint32_t st[4];
     __shared__ uint32_t s_staged;
+    __shared__ uint32_t s_qneg;  // the query has a negative value
     uint32_t* t_start = reinterpret_cast<uint32_t*>(region);
     uint32_t* t_end = t_start + kTermChunk;
     uint32_t* c_pre = t_end + kTermChunk;
@@ -771,6 +774,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     }
     const int64_t qb = a.q_indptr[r];
     const int nt = (int)(a.q_indptr[r + 1] - qb);
+    if (threadIdx.x == 0) s_qneg = 0;  // read after the term tables' barriers
 
     {
         float4* A4 = reinterpret_cast<float4*>(A);
@@ -781,7 +785,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     for (int c0 = 0; c0 < nt; c0 += kTermChunk) {
         const int nc = min(kTermChunk, nt - c0);
         __syncthreads();  // previous chunk fully consumed
-        const uint32_t total = build_term_table<DT, S>(a, w, qb, c0, nc, t_start, t_end, t_w, c_pre, c_term, red);
+        const uint32_t total =
+            build_term_table<DT, S>(a, w, qb, c0, nc, t_start, t_end, t_w, c_pre, c_term, red, &s_qneg);
         accumulate_table<DT, kScanWarps>(ix, t_start, t_end, t_w, c_pre, c_term, nc, total, warp, lane, A);
     }
     __syncthreads();
@@ -809,9 +814,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     }
     const CutScratch cs{hist, hist2, region, (uint32_t)kRegionBytes, warp_off, red, st, &s_staged};
     // zero-score slots cannot count once the earlier windows hold g slots, when no score can be negative
-    bool q_neg = false;
-    for (int t = threadIdx.x; t < nt; t += kScanThreads) q_neg |= a.q_values[qb + t] < 0.0f;
-    const bool skip_zero = __syncthreads_or(q_neg) == 0 && ix.nonneg && (uint64_t)w * lambda >= a.g;
+    const bool skip_zero = s_qneg == 0 && ix.nonneg && (uint64_t)w * lambda >= a.g;
     select_window<S, kScanWarps>(a, A, w, y, bounded, pbin, cs, skip_zero);
 }
 

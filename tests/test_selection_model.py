@@ -56,10 +56,11 @@ ZERO_KEY_BITS = np.uint64(0x80000000)                 # order bits of +0.0
 
 def window_emit(K, g_w, win_cap, bounded, pbin, skip_zero=False):
     """The keys one window emits (its n_eff slots' keys K). skip_zero: slots whose score is exactly 0 cannot
-    count (every score >= 0 and the earlier windows hold at least g slots)."""
+    count (every score >= 0 and the earlier windows hold at least g slots); a bounded window then emits only
+    positive slots at or above the bound."""
     b = bins_of(K)
-    if bounded or skip_zero:
-        ok = b >= pbin if bounded else np.ones(len(K), bool)
+    if bounded:
+        ok = b >= pbin
         if skip_zero:
             ok &= (K >> np.uint64(32)) > ZERO_KEY_BITS     # score > 0
         hi = K[ok]
