@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--window", type=int, default=0, help="0 = the workload's window")
     p.add_argument("--block", type=int, default=0, help="scan block shape (sindi_search_params.block_threads)")
     p.add_argument("--group", type=int, default=0, help="batched schedule: queries per scan block")
+    p.add_argument("--accum", choices=["auto", "f32", "fixed32"], default="auto",
+                   help="score window of the coarse scan (sindi_search_params.accumulator)")
     p.add_argument("--queries", type=int, default=0, help="0 = the workload's query count")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound of the oracle sample")
     p.add_argument("--value-dtype", choices=["f32", "f16", "f8"], default=None,
@@ -743,9 +745,9 @@ def main():
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(mode):
+    def step(mode, accum=None):
         idx.search(*q_dev, k=w.k, gamma=w.gamma, mode=mode, out=(out_ids, out_sc), block=args.block,
-                   group=args.group if mode == "batched" else 0)
+                   group=args.group if mode == "batched" else 0, accum=accum or args.accum)
 
     for _ in range(args.warmup):
         step(args.mode)
@@ -810,12 +812,21 @@ def main():
     # the same bytes for every scan of the timed region over the region's time (the plain schedule runs
     # many queries' scans at once; merge and rerank share the region, so this is a lower bound)
     achieved_step_gbs = alg_bytes_per_launch * scan_launches_per_step * args.steps / (dev_ms_max / 1000.0) / 1e9
-    # scatter-adds (one FP32 shared-memory atomicAdd per posting and query): the scan kernel's own rate
+    # scatter-adds (one shared-memory atomicAdd per posting and query): the scan kernel's own rate
     # (timed pass), the whole step's rate, and the probe's measured rate of that operation on this GPU
     adds_per_s = float(touched.sum()) * args.steps / (st2["scan_ms"] / 1000.0)
     adds_per_s_step = float(touched.sum()) * args.steps / (dev_ms_max / 1000.0)
-    adds_peak = scatter_peak(int(info["window"]))
     adds_forms = scatter_forms(int(info["window"])) if rank == 0 else None
+    fixed_sums = args.accum == "fixed32" or (args.accum == "auto" and w.gamma > 0)
+    if fixed_sums:
+        # the fixed-point window adds with a native integer atomic: its probe form is the op's peak
+        adds_peak = (adds_forms or {}).get("u32_atomic_random")
+        adds_peak_from = ("measured: uint32 shared-memory atomicAdd probe at random slots of a window-sized "
+                          "array, every SM full (libsindi_probe), the fixed-point window's add")
+    else:
+        adds_peak = scatter_peak(int(info["window"]))
+        adds_peak_from = ("measured: FP32 shared-memory atomicAdd probe at random slots of a window-sized array, "
+                          "every SM full (libsindi_probe)")
     peak, peak_kind = measured_hbm_peak()
     sha = source_sha()
 
@@ -827,13 +838,13 @@ def main():
     h_sc = torch.empty((nq, w.k), dtype=torch.float32).pin_memory()
     for _ in range(max(1, args.warmup)):
         idx.search(h_ip, h_ix, h_v, k=w.k, gamma=w.gamma, mode=args.mode, out=(h_ids, h_sc), stream=stream.cuda_stream,
-                   block=args.block, group=args.group if args.mode == "batched" else 0)
+                   block=args.block, group=args.group if args.mode == "batched" else 0, accum=args.accum)
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         idx.search(h_ip, h_ix, h_v, k=w.k, gamma=w.gamma, mode=args.mode, out=(h_ids, h_sc), stream=stream.cuda_stream,
-                   block=args.block, group=args.group if args.mode == "batched" else 0)
+                   block=args.block, group=args.group if args.mode == "batched" else 0, accum=args.accum)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
     barrier(ws)
@@ -873,9 +884,15 @@ def main():
             forms[other] = {"qps": timed(lambda: step(other), args.steps)}
             forms[other]["ids_equal_to_main"] = float(np.mean(out_ids.cpu().numpy().view(np.uint32)
                                                               == gpu_ids))
+            if args.accum != "f32":
+                # Alg. 2's FP32 score window in both schedules, for comparison with the fixed-point window
+                for m in (args.mode, other):
+                    forms["f32_window_" + m] = {"qps": timed(lambda: step(m, "f32"), args.steps)}
+                    forms["f32_window_" + m]["ids_equal_to_main"] = float(np.mean(
+                        out_ids.cpu().numpy().view(np.uint32) == gpu_ids))
             if nq <= 65535:
                 # the batched search captured once as a CUDA graph: one graph launch per step
-                with sindi.Plan(idx, *q_dev, k=w.k, gamma=w.gamma) as plan:
+                with sindi.Plan(idx, *q_dev, k=w.k, gamma=w.gamma, accum=args.accum) as plan:
                     forms["batched_graph"] = {"qps": timed(lambda: plan.launch(stream.cuda_stream), args.steps)}
                     gids = plan.out[0].cpu().numpy().view(np.uint32)
                     forms["batched_graph"]["ids_equal_to_main"] = float(np.mean(gids == gpu_ids))
@@ -1036,6 +1053,8 @@ def main():
                    "k": w.k, "gamma": w.gamma, "alpha": w.alpha, "window": info["window"],
                    "n_windows": sigma, "postings": info["postings"], "mode": args.mode,
                    "block": args.block, "group": args.group if args.mode == "batched" else 0,
+                   "accumulator": args.accum,
+                   "window_sums": "fixed32" if fixed_sums else "f32",
                    "batch": 1 if args.mode == "plain" else nq,
                    "l2": "flushed between steps (256 MiB write)"},
         "recall_at_k": recall,
@@ -1062,8 +1081,7 @@ def main():
                                       "frac": adds_per_s_step / adds_peak if adds_peak else None,
                                       "frac_one_chain": adds_per_s / adds_peak if adds_peak else None,
                                       "unit": "posting updates/s",
-                                      "peak_from": "measured: FP32 shared-memory atomicAdd probe at random slots "
-                                                   "of a window-sized array, every SM full (libsindi_probe)",
+                                      "peak_from": adds_peak_from,
                                       "forms": adds_forms}},
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,

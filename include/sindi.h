@@ -112,6 +112,38 @@ typedef struct {
 /* sindi_search_params.block_threads value of the pipelined window scan. */
 #define SINDI_SCAN_PIPELINED 1u
 
+/* The score window of the coarse scan (sindi_search_params.accumulator).
+
+   F32: Alg. 2 as written: every product q_j * x_ij (FP32) is added into the
+   window's FP32 score array (shared-memory FP32 atomicAdd).
+
+   FIXED32: the window holds 32-bit integers in units of 2^-e. Each product is
+   rounded to the nearest unit and added with an integer atomicAdd (native
+   in shared memory, where an FP32 atomicAdd is a compare-and-swap loop); the
+   sums are exact and do not depend on the order of the adds. The sums are
+   converted to FP32 (times 2^-e) before the window's top-gamma cut, so the
+   cut, merge and reorder are unchanged. Per (query, window):
+     B = sum of |q_j| * vmax_j over the query's terms whose list I_{j,w} is
+         not empty, vmax_j = the largest |stored value| of list I_j (all
+         windows, after pruning; for E4M3 lists q_j includes the list scale),
+     e = 30 - x, where 2^(x-1) <= B < 2^x (e = 0 when B = 0), clamped to
+         [-126, 126] and so that |q_j| * 2^e stays below 2^127,
+   so every window sum stays below 2^31 in magnitude. A coarse score of m
+   products, a = the sum of their magnitudes, is then within
+   2^-23 * a + m * 2^-(e+1) of the exact score (the FP32 rounding of each
+   product and of the final conversion, plus half a unit per product); with e
+   unclamped, m * 2^-(e+1) <= m * B * 2^-30.
+
+   AUTO (the default): FIXED32 when the search reorders (gamma > 0; the
+   window scores only choose the candidates that the exact FP32 reorder
+   scores), F32 when the window scores are the answer (gamma = 0). The
+   pipelined scan and the query-group scan always use F32. */
+typedef enum {
+    SINDI_ACCUM_AUTO = 0,
+    SINDI_ACCUM_F32 = 1,
+    SINDI_ACCUM_FIXED32 = 2
+} sindi_accumulator;
+
 /* Parameters of Algorithm 4. */
 typedef struct {
     uint32_t k;            /* results per query, 1..1024                            */
@@ -140,6 +172,7 @@ typedef struct {
                               windows and 36 KiB of tables within 207 KiB) is
                               reduced to what fits. Ignored by the plain schedule
                               and by SINDI_SCAN_PIPELINED                         */
+    uint32_t accumulator;  /* sindi_accumulator; 0 = AUTO                          */
 } sindi_search_params;
 
 typedef struct {

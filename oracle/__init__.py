@@ -77,6 +77,7 @@ def _load():
     L.orc_index_postings.argtypes = [vp]
     L.orc_index_postings.restype = i64
     L.orc_index_export.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.orc_list_vmax.argtypes = [vp, vp]
     L.orc_search.argtypes = [vp, vp, i64, dbl, i64, i64, vp, vp, vp, vp, vp]
     L.orc_search.restype = i64
     L.orc_f16_encode.argtypes = [ctypes.c_float]
@@ -213,6 +214,14 @@ class Index:
         _load().orc_index_export(self._h, seg.ctypes.data, pid.ctypes.data, pval.ctypes.data,
                                  scale.ctypes.data, kept.ctypes.data)
         return seg, pid[: self.postings], pval[: self.postings], scale, kept[: self.D.n]
+
+    def list_vmax(self) -> np.ndarray:
+        """The largest |stored value| of every list I_j over all its windows (FP64, [d]; cached)."""
+        if getattr(self, "_vmax", None) is None:
+            out = np.empty(max(self.D.dim, 1), np.float64)
+            _load().orc_list_vmax(self._h, out.ctypes.data)
+            self._vmax = out[: self.D.dim]
+        return self._vmax
 
     def search(self, Q: Dataset, r: int, k: int, gamma: int = 0, beta: float = 1.0, want_coarse: bool = False):
         """Algorithm 4 for query r: beta-mass query, Algorithm 2 for gamma candidates, exact reorder.

@@ -591,6 +591,18 @@ orc_index* orc_build(const orc_dataset* D, int64_t lambda, double alpha, int32_t
 int64_t orc_index_sigma(const orc_index* I) { return I->sigma; }
 int64_t orc_index_postings(const orc_index* I) { return I->seg[(int64_t)I->d * I->sigma]; }
 
+/* The largest |stored value| of every list I_j over all its windows (0 for
+   an empty list): out[j] = max |pval[p]|, p in seg[j*sigma] .. seg[(j+1)*sigma].
+   It bounds every product q^j * x^j_i that a window adds for term j. */
+void orc_list_vmax(const orc_index* I, double* out) {
+    for (int64_t j = 0; j < I->d; j++) {
+        double m = 0.0;
+        for (int64_t p = I->seg[j * I->sigma]; p < I->seg[(j + 1) * I->sigma]; p++)
+            if (fabs(I->pval[p]) > m) m = fabs(I->pval[p]);
+        out[j] = m;
+    }
+}
+
 /* Export the lists (for comparing a device-built index): seg[d*sigma + 1],
    pid[P], pval[P] (FP64), scale[d], kept_count[n]. */
 void orc_index_export(const orc_index* I, int64_t* seg, int64_t* pid, double* pval, float* scale, int64_t* kept) {

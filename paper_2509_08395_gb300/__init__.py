@@ -4,6 +4,7 @@ The computation lives in hand-written CUDA kernels behind the C ABI of
 ``include/sindi.h`` (``lib/libsindi.so``); ``sindi`` is its Python binding.
 """
 from .sindi import (  # noqa: F401
+    ACCUMS,
     DTYPES,
     MODES,
     PRUNES,

@@ -620,6 +620,7 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream) {
     P.free(sdim);
     P.free(sdoc);
     P.free(sval);
+    list_value_bounds(ix, stream);
     ix.nonneg = postings_nonnegative(ix, stream);  // synchronises the stream
     return SINDI_OK;
 }

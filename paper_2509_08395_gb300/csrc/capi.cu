@@ -85,7 +85,7 @@ struct DeviceGuard {
 };
 
 static void free_index_memory(IndexImpl& ix, cudaStream_t s) {
-    void* ptrs[] = {ix.indptr, ix.indices, ix.values, ix.seg, ix.pid, ix.pval, ix.scale, ix.kept, ix.err};
+    void* ptrs[] = {ix.indptr, ix.indices, ix.values, ix.seg, ix.pid, ix.pval, ix.scale, ix.vmax, ix.kept, ix.err};
     for (void* p : ptrs)
         if (p) (void)cudaFreeAsync(p, s);
     (void)cudaStreamSynchronize(s);
@@ -96,6 +96,7 @@ static void free_index_memory(IndexImpl& ix, cudaStream_t s) {
     ix.pid = nullptr;
     ix.pval = nullptr;
     ix.scale = nullptr;
+    ix.vmax = nullptr;
     ix.kept = nullptr;
     ix.err = nullptr;
     {
@@ -357,8 +358,9 @@ sindi_status sindi_search(const sindi_index* index, const int64_t* q_indptr, con
     const sindi_search_params prm = *params;
     if (prm.k < 1 || prm.k > kMaxK || (prm.gamma != 0 && (prm.gamma < prm.k || prm.gamma > kMaxGamma)) ||
         !(prm.beta > 0.0 && prm.beta <= 1.0) || prm.mode > SINDI_MODE_BATCHED ||
-        !valid_block_threads(prm.block_threads) || prm.group > kMaxQueryGroup) {
-        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; block_threads 0, 1 (pipelined), 256, 512 or 1024; group 0..8");
+        !valid_block_threads(prm.block_threads) || prm.group > kMaxQueryGroup ||
+        prm.accumulator > SINDI_ACCUM_FIXED32) {
+        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; block_threads 0, 1 (pipelined), 256, 512 or 1024; group 0..8; accumulator 0..2");
         return SINDI_ERR_INVALID_ARG;
     }
 
@@ -504,8 +506,9 @@ sindi_status sindi_search_noalloc(const sindi_index* index, const int64_t* q_ind
     const sindi_search_params prm = *params;
     if (prm.k < 1 || prm.k > kMaxK || (prm.gamma != 0 && (prm.gamma < prm.k || prm.gamma > kMaxGamma)) ||
         !(prm.beta > 0.0 && prm.beta <= 1.0) || prm.mode > SINDI_MODE_BATCHED ||
-        !valid_block_threads(prm.block_threads) || prm.group > kMaxQueryGroup) {
-        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; block_threads 0, 1 (pipelined), 256, 512 or 1024; group 0..8");
+        !valid_block_threads(prm.block_threads) || prm.group > kMaxQueryGroup ||
+        prm.accumulator > SINDI_ACCUM_FIXED32) {
+        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; mode 0/1; block_threads 0, 1 (pipelined), 256, 512 or 1024; group 0..8; accumulator 0..2");
         return SINDI_ERR_INVALID_ARG;
     }
     if (prm.beta < 1.0) {
@@ -770,6 +773,7 @@ sindi_status sindi_index_load(const char* path, void* stream, sindi_index** out)
             return SINDI_ERR_INVALID_DATA;
         }
         SINDI_CUDA(cudaStreamSynchronize(s));
+        list_value_bounds(ix, s);
         ix.nonneg = postings_nonnegative(ix, s);
     } catch (const CudaError& e) {
         sindi_status st = from_cuda(e);

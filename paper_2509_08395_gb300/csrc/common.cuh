@@ -52,6 +52,7 @@ struct DevIndex {
     const uint16_t* pid;     // [P] i mod lambda
     const void* pval;        // [P] float | __half | e4m3 code
     const float* scale;      // [dim]
+    const float* vmax;       // [dim] largest |stored value| of list I_j (all windows)
     uint64_t pcap;           // entries of pid / pval (postings rounded up to 8)
     int64_t doc_nnz;         // entries of the unpruned documents
     int32_t nonneg;          // 1: no stored posting value is negative

@@ -38,6 +38,7 @@ struct IndexImpl {
     uint16_t* pid = nullptr;     // [postings]
     void* pval = nullptr;        // [postings]
     float* scale = nullptr;      // [dim]
+    float* vmax = nullptr;       // [dim] largest |stored value| of each list (fixed-point scan)
     uint32_t* kept = nullptr;    // [n_docs]
     uint32_t* err = nullptr;     // device error word
 
@@ -51,11 +52,11 @@ struct IndexImpl {
     struct PlainCall {
         const void* buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
         int64_t n = -1;
-        uint32_t k = 0, gamma = 0, block = 0;
+        uint32_t k = 0, gamma = 0, block = 0, accum = 0;
         bool operator==(const PlainCall& o) const {
             for (int i = 0; i < 5; i++)
                 if (buf[i] != o.buf[i]) return false;
-            return n == o.n && k == o.k && gamma == o.gamma && block == o.block;
+            return n == o.n && k == o.k && gamma == o.gamma && block == o.block && accum == o.accum;
         }
     };
     mutable std::mutex graph_mu;
@@ -82,6 +83,7 @@ struct IndexImpl {
         d.pid = pid;
         d.pval = pval;
         d.scale = scale;
+        d.vmax = vmax;
         d.pcap = (uint64_t)((postings + 7) & ~(int64_t)7);
         d.doc_nnz = doc_nnz;
         d.nonneg = nonneg ? 1 : 0;
@@ -99,6 +101,10 @@ sindi_status build_lists(IndexImpl& ix, cudaStream_t stream);
 
 // True when no stored posting value is negative (one pass over the values; synchronises `stream`).
 bool postings_nonnegative(const IndexImpl& ix, cudaStream_t stream);
+
+// Allocates ix.vmax from the index's pool (once) and fills it: the largest
+// |stored value| of every list I_j over all its windows (search.cu).
+void list_value_bounds(IndexImpl& ix, cudaStream_t stream);
 
 // Sets kErrDocIndptr in *err unless indptr[0] == 0 and indptr never decreases.
 void launch_validate_indptr(const int64_t* indptr, int64_t n, uint32_t* err, cudaStream_t stream);

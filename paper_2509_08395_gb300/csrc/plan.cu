@@ -58,8 +58,9 @@ sindi_status sindi_plan_create(const sindi_index* index, const int64_t* q_indptr
     sindi_search_params prm = *params;
     if (prm.k < 1 || prm.k > kMaxK || (prm.gamma != 0 && (prm.gamma < prm.k || prm.gamma > kMaxGamma)) ||
         !(prm.beta > 0.0 && prm.beta <= 1.0) ||
-        !valid_block_threads(prm.block_threads) || prm.group > kMaxQueryGroup) {
-        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; block_threads 0, 1 (pipelined), 256, 512 or 1024; group 0..8");
+        !valid_block_threads(prm.block_threads) || prm.group > kMaxQueryGroup ||
+        prm.accumulator > SINDI_ACCUM_FIXED32) {
+        set_last_error("k in [1, 1024]; gamma 0 or in [k, 8192]; beta in (0, 1]; block_threads 0, 1 (pipelined), 256, 512 or 1024; group 0..8; accumulator 0..2");
         return SINDI_ERR_INVALID_ARG;
     }
     if (prm.beta < 1.0) {

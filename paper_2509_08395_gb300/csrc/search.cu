@@ -127,6 +127,41 @@ __device__ __forceinline__ float load_value(const void* pval, uint32_t p) {
     }
 }
 
+// vmax[j] = the largest |stored value| of list I_j over all its windows
+// (postings seg[j * sigma] .. seg[(j + 1) * sigma]), one warp per list. It
+// bounds every product of term j, which sets the unit of the fixed-point
+// window (window_scale_exp).
+template <int DT>
+__global__ void list_vmax_kernel(const uint32_t* seg, const void* pval, int32_t dim, uint32_t sigma, float* vmax) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < dim; j += warps) {
+        const uint32_t lo = seg[(uint64_t)j * sigma], hi = seg[(uint64_t)(j + 1) * sigma];
+        float m = 0.0f;
+        for (uint32_t p = lo + lane; p < hi; p += 32) m = fmaxf(m, fabsf(load_value<DT>(pval, p)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+        if (lane == 0) vmax[j] = m;
+    }
+}
+
+void list_value_bounds(IndexImpl& ix, cudaStream_t stream) {
+    if (!ix.vmax) {
+        Pool P{ix.pool, stream};
+        ix.vmax = P.alloc<float>(ix.dim > 0 ? ix.dim : 1);
+    }
+    if (ix.dim <= 0) return;
+    const int64_t blocks = std::min<int64_t>(((int64_t)ix.dim + 7) / 8, 152 * 32);
+    if (ix.dtype == SINDI_F32)
+        list_vmax_kernel<SINDI_F32><<<(unsigned)blocks, 256, 0, stream>>>(ix.seg, ix.pval, ix.dim, ix.sigma, ix.vmax);
+    else if (ix.dtype == SINDI_F16)
+        list_vmax_kernel<SINDI_F16><<<(unsigned)blocks, 256, 0, stream>>>(ix.seg, ix.pval, ix.dim, ix.sigma, ix.vmax);
+    else
+        list_vmax_kernel<SINDI_F8E4M3><<<(unsigned)blocks, 256, 0, stream>>>(ix.seg, ix.pval, ix.dim, ix.sigma,
+                                                                             ix.vmax);
+    SINDI_CUDA(cudaGetLastError());
+}
+
 // Programmatic dependent launch. Kernels after the first of a search call are
 // launched so that they may start while the previous kernel still runs; each
 // waits here before it touches memory the previous kernels write, and lets
@@ -258,6 +293,16 @@ __device__ __forceinline__ void add_chunk(float* A, uint32_t lambda, uint32_t* e
             atomicAdd(&A[chunk_slot(k, u)], k.wq * k.v[u]);
 }
 
+// The same into a fixed-point window: each product (its weight already
+// carries the window's 2^e) rounded to the nearest unit and added with a
+// native shared-memory integer atomic.
+__device__ __forceinline__ void add_chunk_fixed(int32_t* A, uint32_t lambda, uint32_t* err, const Chunk& k) {
+#pragma unroll
+    for (int u = 0; u < kChunkU; u++)
+        if ((k.lm & (1u << u)) && checked(slot_in_bounds(chunk_slot(k, u), lambda), err))
+            atomicAdd(&A[chunk_slot(k, u)], __float2int_rn(k.wq * k.v[u]));
+}
+
 // Chunks of a segment of at least kVecMin postings.
 __device__ __forceinline__ uint32_t long_segment_chunks(uint32_t ps, uint32_t pe) {
     return (((pe + 7u) & ~7u) - (ps & ~7u) + kChunkLen - 1) / kChunkLen;
@@ -334,6 +379,7 @@ struct ScanArgs {
     uint32_t nq;            // pipelined scan: query rows and windows of the launch's items
     uint32_t nwin;
     Workspace ws;
+    int fixed;              // 1: the window accumulates in 32-bit fixed point (sindi_accumulator FIXED32)
 };
 
 // Shared-memory scratch of one window cut, owned by the threads that select.
@@ -348,6 +394,63 @@ struct CutScratch {
     uint32_t* s_staged;     // [1]
 };
 
+// ---------------------------------------------------------------------------
+// The fixed-point window (sindi_accumulator FIXED32). For one (query, window):
+// B = the sum of |w_j| * vmax_j over the terms whose list I_{j,w} is not empty
+// (w_j = q_j, times the list scale for E4M3), e = 30 - x with 2^(x-1) <= B <
+// 2^x, clamped so that every |w_j| * 2^e < 2^127 and to [-126, 126]; 0 when B
+// = 0. The window holds integers in units of 2^-e, and every sum stays below
+// 2^31 (B * 2^e < 2^30, plus half a unit per product).
+// ---------------------------------------------------------------------------
+
+// x with 2^(x-1) <= f < 2^x for a finite f > 0 (from the exponent field; a
+// subnormal f gets x = -126, an upper bound); inf: the bound of a sum of at
+// most kMaxQueryTerms values below 2^128.
+__device__ __forceinline__ int exponent_bound(float f) {
+    const int E = (int)((__float_as_uint(f) >> 23) & 0xFFu);
+    return E == 0xFF ? 128 + 12 : (E == 0 ? -126 : E - 126);
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }  // |e| <= 126
+
+// A warp's share of B and of max |w_j| (b, m: this thread's terms) into
+// fred[warp] and fred[nw + warp]; every lane of the warp calls it.
+__device__ __forceinline__ void fx_warp_partials(float b, float m, float* fred, int warp, int nw) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        b += __shfl_xor_sync(kFull, b, o);
+        m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        fred[warp] = b;
+        fred[nw + warp] = m;
+    }
+}
+
+// e from the nw warps' partials (after a barrier). The warps are summed in a
+// fixed order, so every thread gets the same e.
+__device__ __forceinline__ int fx_exponent(const float* fred, int nw) {
+    float B = 0.0f, M = 0.0f;
+    for (int i = 0; i < nw; i++) {
+        B += fred[i];
+        M = fmaxf(M, fred[nw + i]);
+    }
+    if (!(B > 0.0f)) return 0;
+    int e = 30 - exponent_bound(B);
+    if (M > 0.0f) e = min(e, 127 - exponent_bound(M));
+    return max(-126, min(126, e));
+}
+
+// This thread's part of B for term j of weight qv over window w.
+template <int DT>
+__device__ __forceinline__ void fx_term_bound(const DevIndex& ix, int32_t j, float qv, uint32_t len, float& b,
+                                              float& m) {
+    if (len == 0) return;
+    const float wq = fabsf((DT == SINDI_F8E4M3) ? qv * ix.scale[j] : qv);
+    b += wq * ix.vmax[j];
+    m = fmaxf(m, wq);
+}
+
 // The term table of one query over one window, for terms c0 .. c0 + nc - 1
 // of the query (nc <= the group's thread count): every term's posting range
 // and weight, and the map from warp chunks to terms. Returns the number of
@@ -355,10 +458,11 @@ struct CutScratch {
 template <int DT, typename S>
 __device__ uint32_t build_term_table(const ScanArgs& a, uint32_t w, int64_t qb, int c0, int nc, uint32_t* t_start,
                                      uint32_t* t_end, float* t_w, uint32_t* c_pre, uint16_t* c_term, uint32_t* red,
-                                     uint32_t* negflag = nullptr) {
+                                     uint32_t* negflag = nullptr, float* fred = nullptr) {
     const DevIndex& ix = a.ix;
     const int tid = S::tid();
     uint32_t nch = 0;
+    float fb = 0.0f, fm = 0.0f;  // fixed-point window: this thread's part of B and of max |w_j|
     if (tid < nc) {
         const int32_t j = a.q_indices[qb + c0 + tid];
         const float qv = a.q_values[qb + c0 + tid];
@@ -376,10 +480,13 @@ __device__ uint32_t build_term_table(const ScanArgs& a, uint32_t w, int64_t qb, 
         t_start[tid] = start;
         t_end[tid] = start + len;
         t_w[tid] = wq;
+        if (fred) fx_term_bound<DT>(ix, j, qv, len, fb, fm);
         // chunks of a long list tile its 8-aligned groups of postings
         nch = len >= kVecMin ? (((start + len + 7u) & ~7u) - (start & ~7u) + kChunkLen - 1) / kChunkLen
                              : (len ? 1u : 0u);
     }
+    // (fred's partials are visible after the sum's barriers)
+    if (fred) fx_warp_partials(fb, fm, fred, tid >> 5, S::kThreads / 32);
     uint32_t total;
     const uint32_t excl = group_exclusive_sum<uint32_t, S>(nch, &total, red);
     if (tid < nc) {
@@ -393,21 +500,81 @@ __device__ uint32_t build_term_table(const ScanArgs& a, uint32_t w, int64_t qb, 
 // Scatter-add of one term table into the window A (Alg. 2's product and
 // accumulation loops): warp `warp` of NW takes chunks warp, warp + NW, ...;
 // the next chunk's loads are issued before this chunk's adds.
-template <int DT, int NW>
+template <int DT, int NW, bool FIXED = false>
 __device__ __forceinline__ void accumulate_table(const DevIndex& ix, const uint32_t* t_start, const uint32_t* t_end,
                                                  const float* t_w, const uint32_t* c_pre, const uint16_t* c_term,
-                                                 int nc, uint32_t total, int warp, int lane, float* A) {
+                                                 int nc, uint32_t total, int warp, int lane, float* A,
+                                                 float wscale = 1.0f) {
     uint32_t c = (uint32_t)warp;
     Chunk cur;
     if (c < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, c, lane, cur);
+    if (FIXED) cur.wq *= wscale;  // the fixed-point window's 2^e (exact)
     while (c < total) {
         const uint32_t cn = c + NW;
         Chunk nxt;
         if (cn < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, cn, lane, nxt);
-        add_chunk(A, ix.lambda, ix.err, cur);
+        if (FIXED) nxt.wq *= wscale;
+        if (FIXED) add_chunk_fixed(reinterpret_cast<int32_t*>(A), ix.lambda, ix.err, cur);
+        else add_chunk(A, ix.lambda, ix.err, cur);
         cur = nxt;
         c = cn;
     }
+}
+
+// The fixed-point window's e for a query of more terms than one term table
+// holds (its B must be known before the first table's adds): a pass over all
+// of them. Every thread of the block calls it; fred: [2 * BLOCK / 32] floats,
+// free on entry and on return.
+template <int DT, int BLOCK>
+__device__ int window_scale_exp(const ScanArgs& a, uint32_t w, int64_t qb, int nt, float* fred) {
+    const DevIndex& ix = a.ix;
+    float b = 0.0f, m = 0.0f;
+    for (int t = threadIdx.x; t < nt; t += BLOCK) {
+        const int32_t j = a.q_indices[qb + t];
+        const float qv = a.q_values[qb + t];
+        if (j >= 0 && j < ix.dim && isfinite(qv) && list_in_bounds(j, w, ix.dim, ix.sigma)) {
+            const uint64_t sg = (uint64_t)j * ix.sigma + w;
+            fx_term_bound<DT>(ix, j, qv, ix.seg[sg + 1] - ix.seg[sg], b, m);
+        }
+    }
+    fx_warp_partials(b, m, fred, threadIdx.x >> 5, BLOCK / 32);
+    __syncthreads();
+    const int e = fx_exponent(fred, BLOCK / 32);
+    __syncthreads();
+    return e;
+}
+
+constexpr int kNoFx = 1 << 30;  // select_window: the window holds FP32 scores
+
+// The fixed-point window's sums to FP32 scores in place: the rounded
+// conversion times 2^-e (exact scaling). Every thread of the group S calls it.
+template <typename S>
+__device__ __forceinline__ void fx_window_to_float(float* A, uint32_t lambda, int e) {
+    const float inv = pow2f(-e);
+    int4* I4 = reinterpret_cast<int4*>(A);
+    float4* F4 = reinterpret_cast<float4*>(A);
+    for (uint32_t m = (uint32_t)S::tid(); m < window_stride(lambda) / 4; m += S::kThreads) {
+        const int4 t = I4[m];
+        F4[m] = make_float4((float)t.x * inv, (float)t.y * inv, (float)t.z * inv, (float)t.w * inv);
+    }
+}
+
+// An integer t such that every sum n of a fixed-point window (unit 2^-e, |n| <
+// 2^31) whose FP32 score float(n) * 2^-e is >= thr has n >= t: the exact least
+// such n when |thr * 2^e| <= 2^24 (where the conversion is exact), else up to
+// 128 below it (the conversion's rounding at |n| < 2^31), so a few slots just
+// under the bound may also be emitted, which the merge drops. NaN: none; -inf:
+// all; thr > 0: at least 1 (a zero sum scores 0).
+__device__ __forceinline__ int32_t fx_threshold(float thr, int e) {
+    if (thr != thr) return INT32_MAX;
+    if (thr == -INFINITY) return INT32_MIN;
+    const float X = thr * pow2f(e);
+    int32_t t;
+    if (X >= 2147483648.0f) t = INT32_MAX;
+    else if (X < -2147483648.0f) t = INT32_MIN;
+    else if (fabsf(X) <= 16777216.0f) t = (int32_t)ceilf(X);
+    else t = (int32_t)floorf(X) - 128;
+    return thr > 0.0f ? max(t, 1) : t;
 }
 
 // The least float whose order key is at least k: a slot's key is >= k
@@ -425,9 +592,9 @@ __device__ __forceinline__ float key_floor_float(uint32_t k) {
 // it emitted to the query's histogram H (ids >= N are not candidates).
 // `bounded`: g candidates of the query already exist at or above bin pbin.
 // Every thread of the group S (NW warps) calls it; the workspace must be free.
-template <typename S, int NW>
-__device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uint32_t y, bool bounded, uint32_t pbin,
-                              const CutScratch& cs, bool skip_zero = false) {
+template <typename S, int NW, bool FX = false>
+__device__ void select_window(const ScanArgs& a, float* A, uint32_t w, uint32_t y, bool bounded, uint32_t pbin,
+                              const CutScratch& cs, bool skip_zero = false, int fx_e = kNoFx) {
     constexpr int NT = S::kThreads;
     const DevIndex& ix = a.ix;
     const int tid = S::tid();
@@ -445,7 +612,13 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
     const int64_t rest = ix.n_docs - gbase;
     const int n_eff = (int)(rest < (int64_t)lambda ? rest : (int64_t)lambda);
     const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
-    auto key_of = [&](int i) -> uint64_t { return result_key(A[i], (uint32_t)(gbase + i)); };
+    // fx_e != kNoFx (only with FX, only for a bounded window): A holds the fixed-point sums in units of 2^-fx_e
+    const bool fx = FX && fx_e != kNoFx;
+    const float fx_inv = fx ? pow2f(-fx_e) : 1.0f;
+    const int32_t* Ai = reinterpret_cast<const int32_t*>(A);
+    auto key_of = [&](int i) -> uint64_t {
+        return result_key(fx ? (float)Ai[i] * fx_inv : A[i], (uint32_t)(gbase + i));
+    };
     uint64_t* cand = a.ws.cand + (size_t)y * a.ws.cand_cap;
     if (bounded) {
         // g candidates at or above bin pbin already exist, so only slots in
@@ -467,15 +640,23 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
         if (skip_zero && thr <= 0.0f) thr = __int_as_float(1);  // the least positive float (NaN stays NaN)
         const int n4 = (n_eff + 3) >> 2;
         const float4* A4 = reinterpret_cast<const float4*>(A);
+        const int4* I4 = reinterpret_cast<const int4*>(A);
+        const int32_t ithr = fx ? fx_threshold(thr, fx_e) : 0;
         auto scan_bounded = [&](auto&& emit) -> uint32_t {
             uint32_t cnt = 0;
             for (int b4 = warp * 32; b4 < n4; b4 += NT) {
                 const int i4 = b4 + lane;
                 uint32_t m = 0;
                 if (i4 < n4) {
-                    const float4 x = A4[i4];
-                    m = (x.x >= thr ? 1u : 0u) | (x.y >= thr ? 2u : 0u) | (x.z >= thr ? 4u : 0u) |
-                        (x.w >= thr ? 8u : 0u);
+                    if (fx) {
+                        const int4 x = I4[i4];
+                        m = (x.x >= ithr ? 1u : 0u) | (x.y >= ithr ? 2u : 0u) | (x.z >= ithr ? 4u : 0u) |
+                            (x.w >= ithr ? 8u : 0u);
+                    } else {
+                        const float4 x = A4[i4];
+                        m = (x.x >= thr ? 1u : 0u) | (x.y >= thr ? 2u : 0u) | (x.z >= thr ? 4u : 0u) |
+                            (x.w >= thr ? 8u : 0u);
+                    }
                     const int rem = n_eff - 4 * i4;
                     if (rem < 4) m &= (1u << rem) - 1u;
                 }
@@ -531,7 +712,11 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
             S::sync();  // warp_off, st and the staging area are reused by the caller's next cut
             return;
         }
-        // too many: the cut below decides (group-uniform)
+        // too many: the cut below decides (group-uniform), on FP32 scores
+        if (fx) {
+            fx_window_to_float<S>(A, lambda, fx_e);
+            S::sync();
+        }
     }
     // level 1: 12-bit bins of the score key. Each warp counts its slots in a
     // private histogram of the 256 bins below the window's top bin (no
@@ -729,7 +914,7 @@ __device__ void select_window(const ScanArgs& a, const float* A, uint32_t w, uin
 // One block per (window, query): the term tables are staged in shared memory,
 // the block's warps scatter-add every term's postings of the window into A,
 // then the block cuts the window.
-template <int DT, bool QUERY_MAJOR, int BLOCK>
+template <int DT, bool QUERY_MAJOR, int BLOCK, bool FX>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanArgs a) {
     constexpr int kScanThreads = BLOCK;
     constexpr int kScanWarps = BLOCK / 32;
@@ -750,6 +935,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     __shared__ uint32_t st[4];
     __shared__ uint32_t s_staged;
     __shared__ uint32_t s_qneg;  // the query has a negative value
+    __shared__ float fred[2 * kScanWarps];  // fixed-point window: the warps' parts of B and of max |w_j|
     uint32_t* t_start = reinterpret_cast<uint32_t*>(region);
     uint32_t* t_end = t_start + kTermChunk;
     uint32_t* c_pre = t_end + kTermChunk;
@@ -782,12 +968,23 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
             A4[m] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
+    // fixed-point window: the unit 2^-e of this (query, window). B comes with the
+    // term table when one table holds the query's terms, else from a pass of its own.
+    int fx_e = 0;
+    const bool fx_pre = FX && nt > kTermChunk;
+    if (fx_pre) fx_e = window_scale_exp<DT, BLOCK>(a, w, qb, nt, fred);
     for (int c0 = 0; c0 < nt; c0 += kTermChunk) {
         const int nc = min(kTermChunk, nt - c0);
         __syncthreads();  // previous chunk fully consumed
-        const uint32_t total =
-            build_term_table<DT, S>(a, w, qb, c0, nc, t_start, t_end, t_w, c_pre, c_term, red, &s_qneg);
-        accumulate_table<DT, kScanWarps>(ix, t_start, t_end, t_w, c_pre, c_term, nc, total, warp, lane, A);
+        const uint32_t total = build_term_table<DT, S>(a, w, qb, c0, nc, t_start, t_end, t_w, c_pre, c_term, red,
+                                                       &s_qneg, FX && !fx_pre ? fred : nullptr);
+        if (FX) {
+            if (!fx_pre) fx_e = fx_exponent(fred, kScanWarps);
+            accumulate_table<DT, kScanWarps, true>(ix, t_start, t_end, t_w, c_pre, c_term, nc, total, warp, lane, A,
+                                                   pow2f(fx_e));
+        } else {
+            accumulate_table<DT, kScanWarps>(ix, t_start, t_end, t_w, c_pre, c_term, nc, total, warp, lane, A);
+        }
     }
     __syncthreads();
 
@@ -815,7 +1012,12 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     const CutScratch cs{hist, hist2, region, (uint32_t)kRegionBytes, warp_off, red, st, &s_staged};
     // zero-score slots cannot count once the earlier windows hold g slots, when no score can be negative
     const bool skip_zero = s_qneg == 0 && ix.nonneg && (uint64_t)w * lambda >= a.g;
-    select_window<S, kScanWarps>(a, A, w, y, bounded, pbin, cs, skip_zero);
+    // a fixed-point window without a bound goes to FP32 for the full cut; a bounded one is read as integers
+    if (FX && !bounded) {
+        fx_window_to_float<S>(A, lambda, fx_e);
+        S::sync();
+    }
+    select_window<S, kScanWarps, FX>(a, A, w, y, bounded, pbin, cs, skip_zero, FX && bounded ? fx_e : kNoFx);
 }
 
 // ---------------------------------------------------------------------------
@@ -1728,6 +1930,7 @@ struct Plan {
     bool final_stage;
     uint32_t g, win_cap, cand_cap, fcap, top_cap, merge_blocks, block;
     uint32_t group;  // batched scan: queries per block (1 = one block per (query, window))
+    bool fixed;      // the one-block-per-window scan accumulates in fixed point
 };
 
 // Queries per block of the batched scan: as asked (0: one, the fastest shape
@@ -1755,6 +1958,7 @@ static Plan make_plan(const IndexImpl& ix, const sindi_search_params& prm) {
     p.merge_blocks = std::max<uint32_t>(1, std::min<uint32_t>(16, p.cand_cap / 8192));
     p.block = prm.block_threads;
     p.group = group_size(ix, prm.group, prm.block_threads);
+    p.fixed = prm.accumulator == SINDI_ACCUM_FIXED32 || (prm.accumulator == SINDI_ACCUM_AUTO && !p.final_stage);
     return p;
 }
 
@@ -1779,8 +1983,10 @@ static void launch_kernel(void (*kern)(Params...), dim3 grid, dim3 block, size_t
 
 template <int DT, bool QM, int BLOCK>
 static void allow_window_smem() {
-    SINDI_CUDA(cudaFuncSetAttribute(scan_window_kernel<DT, QM, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(kMaxWindow * sizeof(float))));
+    SINDI_CUDA(cudaFuncSetAttribute(scan_window_kernel<DT, QM, BLOCK, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxWindow * sizeof(float))));
+    SINDI_CUDA(cudaFuncSetAttribute(scan_window_kernel<DT, QM, BLOCK, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxWindow * sizeof(float))));
 }
 
 template <int DT>
@@ -1869,7 +2075,8 @@ void configure_search_kernels(int device) {
 template <int DT, bool QM, int BLOCK>
 static void launch_scan_t(const ScanArgs& a, uint32_t sigma, uint32_t nq, size_t smem, cudaStream_t s, bool pdl) {
     dim3 grid = QM ? dim3(nq, sigma) : dim3(sigma, nq);
-    launch_kernel(scan_window_kernel<DT, QM, BLOCK>, grid, dim3(BLOCK), smem, s, pdl, a);
+    if (a.fixed) launch_kernel(scan_window_kernel<DT, QM, BLOCK, true>, grid, dim3(BLOCK), smem, s, pdl, a);
+    else launch_kernel(scan_window_kernel<DT, QM, BLOCK, false>, grid, dim3(BLOCK), smem, s, pdl, a);
 }
 
 // Plain schedules (one query) take window-major grids; batched schedules take
@@ -1917,7 +2124,8 @@ static void launch_group(const IndexImpl& ix, const Plan& pl, const Workspace& w
     // the coarse scan reads the beta-pruned queries when there are any (Alg. 4, the query-pruning step);
     // merge and rerank check and reorder with the full queries
     ScanArgs sa{dix, scan_q ? scan_q->indptr : q_indptr, scan_q ? scan_q->indices : q_indices,
-                scan_q ? scan_q->values : q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, 0u, nq, ix.sigma, ws};
+                scan_q ? scan_q->values : q_values, q0, pl.g, pl.win_cap, batched ? 1 : 0, 0u, nq, ix.sigma, ws,
+                pl.fixed ? 1 : 0};
     if (ev0) SINDI_CUDA(cudaEventRecord(ev0, stream));
     // the pipelined scan when asked for and its two window arrays fit; any
     // other shape is one block per window (block 0 or 1: the default size)
@@ -2123,6 +2331,7 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
         call.k = k;
         call.gamma = prm.gamma;
         call.block = prm.block_threads;
+        call.accum = prm.accumulator;
         std::lock_guard<std::mutex> lk(ix.graph_mu);
         bool failed = false;
         if (!(ix.graph_exec && ix.graph_call == call) && ix.graph_seen == call) {

@@ -246,9 +246,10 @@ sindi_status sindi_server_create(const sindi_index* index, const sindi_server_pa
     const sindi_search_params& sp = p.search;
     if (p.max_batch > 4096 || p.max_slots > 64 || p.max_query_nnz > 2048 || sp.k < 1 || sp.k > kMaxK ||
         (sp.gamma != 0 && (sp.gamma < sp.k || sp.gamma > kMaxGamma)) || !(sp.beta > 0.0 && sp.beta <= 1.0) ||
-        !valid_block_threads(sp.block_threads) || sp.group > kMaxQueryGroup) {
+        !valid_block_threads(sp.block_threads) || sp.group > kMaxQueryGroup ||
+        sp.accumulator > SINDI_ACCUM_FIXED32) {
         set_last_error("max_batch <= 4096, max_slots <= 64, max_query_nnz <= 2048; k in [1, 1024]; gamma 0 or in "
-                       "[k, 8192]; beta in (0, 1]; block_threads 0, 1, 256, 512 or 1024; group 0..8");
+                       "[k, 8192]; beta in (0, 1]; block_threads 0, 1, 256, 512 or 1024; group 0..8; accumulator 0..2");
         return SINDI_ERR_INVALID_ARG;
     }
     if (sp.beta < 1.0) {

@@ -26,6 +26,8 @@ DTYPES = {"f32": SINDI_F32, "f16": SINDI_F16, "f8": SINDI_F8E4M3, "e4m3": SINDI_
 MODES = {"plain": SINDI_MODE_PLAIN, "batched": SINDI_MODE_BATCHED}
 SINDI_PRUNE_MASS, SINDI_PRUNE_VECTOR_NUMBER, SINDI_PRUNE_LIST, SINDI_PRUNE_MASS_LIST = 0, 1, 2, 3
 SINDI_SCAN_PIPELINED = 1  # block_threads value of the pipelined window scan
+SINDI_ACCUM_AUTO, SINDI_ACCUM_F32, SINDI_ACCUM_FIXED32 = 0, 1, 2
+ACCUMS = {"auto": SINDI_ACCUM_AUTO, "f32": SINDI_ACCUM_F32, "fixed32": SINDI_ACCUM_FIXED32}
 PRUNES = {"mass": SINDI_PRUNE_MASS, "vector_number": SINDI_PRUNE_VECTOR_NUMBER, "list": SINDI_PRUNE_LIST,
           "mass_list": SINDI_PRUNE_MASS_LIST}
 STATUS_NAMES = {0: "SINDI_OK", 1: "SINDI_ERR_INVALID_ARG", 2: "SINDI_ERR_INVALID_DATA", 3: "SINDI_ERR_OOM",
@@ -45,7 +47,8 @@ class sindi_build_params(ctypes.Structure):
 
 class sindi_search_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_uint32), ("gamma", ctypes.c_uint32), ("beta", ctypes.c_double),
-                ("mode", ctypes.c_uint32), ("block_threads", ctypes.c_uint32), ("group", ctypes.c_uint32)]
+                ("mode", ctypes.c_uint32), ("block_threads", ctypes.c_uint32), ("group", ctypes.c_uint32),
+                ("accumulator", ctypes.c_uint32)]
 
 
 class sindi_index_info_t(ctypes.Structure):
@@ -203,11 +206,12 @@ def sindi_build(indptr, indices, values, n_docs: int, dim: int, window: int = 0,
 
 def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
                  gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None, block: int = 0,
-                 group: int = 0) -> None:
-    """Algorithm 4 for every query row; writes out_ids (uint32/int32) and out_scores (float32), [n_queries, k]."""
+                 group: int = 0, accum: str = "auto") -> None:
+    """Algorithm 4 for every query row; writes out_ids (uint32/int32) and out_scores (float32), [n_queries, k].
+    accum: the coarse scan's score window, "auto", "f32" or "fixed32" (sindi_accumulator)."""
     lib = load()
     prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block),
-                              group=int(group))
+                              group=int(group), accumulator=ACCUMS[accum])
     _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     st = lib.sindi_search(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                           _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm), _ptr(out_ids, np.uint32),
@@ -217,12 +221,12 @@ def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_
 
 def sindi_search_noalloc(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
                          gamma: int = 0, beta: float = 1.0, mode: str = "plain", stream=None,
-                         block: int = 0, group: int = 0) -> None:
+                         block: int = 0, group: int = 0, accum: str = "auto") -> None:
     """sindi_search for callers that cannot allocate device memory: all working memory comes from the library's
     static 8 MiB device array. Device tensors only; calls that overlap on the GPU race on that array."""
     lib = load()
     prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block),
-                              group=int(group))
+                              group=int(group), accumulator=ACCUMS[accum])
     _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     st = lib.sindi_search_noalloc(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                                   _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm),
@@ -334,7 +338,7 @@ class Index:
         self.info = sindi_index_info(self.handle)
 
     def search(self, q_indptr, q_indices, q_values, k: int, gamma: int = 0, beta: float = 1.0,
-               mode: str = "plain", out=None, stream=None, block: int = 0, group: int = 0):
+               mode: str = "plain", out=None, stream=None, block: int = 0, group: int = 0, accum: str = "auto"):
         """Returns (ids, scores) of shape [n_queries, k]; device tensors for device queries."""
         n_q = (q_indptr.shape[0] if hasattr(q_indptr, "shape") else len(q_indptr)) - 1
         if out is None:
@@ -346,7 +350,7 @@ class Index:
                 out = (torch.empty((n_q, k), dtype=torch.int32, device=dev),
                        torch.empty((n_q, k), dtype=torch.float32, device=dev))
         sindi_search(self.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma, beta, mode, stream,
-                     block, group)
+                     block, group, accum)
         return out
 
     def save(self, path: str) -> None:
@@ -391,9 +395,9 @@ class Index:
 
 # ---- graph-captured batched search -------------------------------------------------
 def sindi_plan_create(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
-                      gamma: int = 0, beta: float = 1.0, block: int = 0, group: int = 0) -> int:
+                      gamma: int = 0, beta: float = 1.0, block: int = 0, group: int = 0, accum: str = "auto") -> int:
     prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=SINDI_MODE_BATCHED, block_threads=int(block),
-                              group=int(group))
+                              group=int(group), accumulator=ACCUMS[accum])
     _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     out = ctypes.c_void_p()
     _check(load().sindi_plan_create(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
@@ -420,7 +424,7 @@ class Plan:
     """A batched search of fixed device buffers, captured once as a CUDA graph."""
 
     def __init__(self, index: "Index", q_indptr, q_indices, q_values, k: int, gamma: int = 0, out=None,
-                 block: int = 0, group: int = 0):
+                 block: int = 0, group: int = 0, accum: str = "auto"):
         import torch
         self.index = index
         n_q = q_indptr.shape[0] - 1
@@ -430,7 +434,7 @@ class Plan:
                    torch.empty((n_q, k), dtype=torch.float32, device=q_indptr.device))
         self.out = out
         self.handle = sindi_plan_create(index.handle, q_indptr, q_indices, q_values, n_q, out[0], out[1], k, gamma,
-                                        block=block, group=group)
+                                        block=block, group=group, accum=accum)
         index._dependents.add(self)
 
     def launch(self, stream=None):
@@ -458,11 +462,11 @@ class Plan:
 # ---- serving (continuous batching) -----------------------------------------------
 def sindi_server_create(index: int, k: int, gamma: int = 0, beta: float = 1.0, max_batch: int = 0,
                         max_slots: int = 0, max_query_nnz: int = 0, max_wait_us: int = 0,
-                        memory_budget: int = 0) -> int:
+                        memory_budget: int = 0, accum: str = "auto") -> int:
     prm = sindi_server_params(max_batch=max_batch, max_slots=max_slots, max_query_nnz=max_query_nnz,
                               max_wait_us=max_wait_us, memory_budget=memory_budget,
                               search=sindi_search_params(k=k, gamma=gamma, beta=beta, mode=SINDI_MODE_BATCHED,
-                                                         block_threads=0))
+                                                         block_threads=0, accumulator=ACCUMS[accum]))
     out = ctypes.c_void_p()
     _check(load().sindi_server_create(ctypes.c_void_p(index), ctypes.byref(prm), ctypes.byref(out)),
            "sindi_server_create")

@@ -55,27 +55,58 @@ def check_ranked(gids, gsc, oids, osc, k, n_docs, tol=REL_TOL, what=""):
             assert got <= want, f"{what}: boundary ranks [{a},{n}) gpu {sorted(got)} not in oracle group"
 
 
-def check_reranked(gids, gsc, D, Q, r, I, k, gamma, tol=REL_TOL, what="", beta=1.0):
+FIXED_UNIT = 2.0 ** -30
+
+
+def _rows(Q):
+    if getattr(Q, "_rows", None) is None:
+        Q._rows = Q.export()
+    return Q._rows
+
+
+def fixed_extra(I, Q, r):
+    """What a fixed-point window score (sindi_accumulator FIXED32) may add to the FP32 dot-product bound of
+    its products: half a unit 2^-e per product, with 2^-(e+1) <= B * 2^-30 for B = the sum over the window's
+    terms of |q_j| * vmax_j (vmax_j = the largest |stored value| of list I_j). Taken over all the query's
+    terms (a B at least the window's) and m = the query's term count (at least the products of any
+    document); a small allowance covers the FP32 evaluation of B on the device. The FP32 part, 2^-23 * a for
+    a = the sum of |products|, is within fp32_sum_bound(a, m) for m >= 1."""
+    ptr, dims, vals = _rows(Q)
+    a, b = int(ptr[r]), int(ptr[r + 1])
+    B = float(np.sum(np.abs(vals[a:b]) * I.list_vmax()[dims[a:b]]))
+    return (b - a) * B * FIXED_UNIT * (1 + 1e-3)
+
+
+def check_reranked(gids, gsc, D, Q, r, I, k, gamma, tol=REL_TOL, what="", beta=1.0, fixed=True):
     """GPU results of Algorithm 4 (pruned coarse stage + exact reorder of gamma candidates).
 
-    The GPU's coarse scores are FP32, so its candidate set may differ from the
-    oracle's only by documents whose coarse score is within tol of the
-    oracle's gamma-th coarse score ("ambiguous"). The GPU answer must be the
-    exact top-k of some candidate set C with robust <= C <= robust + ambiguous.
-    Returns the number of ambiguous documents that touched the answer."""
+    The GPU's coarse scores are rounded (FP32 sums, or with `fixed` the fixed-point window that a search
+    with gamma > 0 uses by default), so its candidate set may differ from the oracle's only by documents
+    whose coarse score is within tol, or within twice the fixed-point allowance (fixed_extra), of the
+    oracle's gamma-th coarse score ("ambiguous"). The GPU answer must be the exact top-k of some candidate
+    set C with robust <= C <= robust + ambiguous. Returns the number of ambiguous documents that touched
+    the answer."""
     n = min(k, D.n)
     g = min(gamma, D.n)
     cids, csc = I.search(Q, r, k=min(g + 256, D.n), gamma=0, beta=beta)
     s_g = csc[g - 1]
+    atol = 2.0 * fixed_extra(I, Q, r) if fixed else 0.0
+
+    def near(s):
+        return _close(s, s_g, tol) or abs(s - s_g) <= atol
+
     if s_g == 0.0:
-        # fewer than gamma documents score above zero: zero scores are exact on both sides (no rounding)
-        # and both fill the pool with the lowest ids, so the candidate set is the oracle's
-        amb = set()
-        robust = set(int(c) for c in cids[:g])
-    else:
-        amb = set(int(c) for c, s in zip(cids, csc) if _close(s, s_g, tol))
+        # fewer than gamma documents score above zero: zero scores are exact on both sides (no product) and
+        # both fill the pool with the lowest ids. A positive score within the fixed-point allowance may
+        # round to zero, and lower-id zeros past the oracle's pool then take its place.
+        amb = set(int(c) for c, s in zip(cids, csc) if 0.0 < s <= atol)
+        if amb:
+            amb |= set(int(c) for c, s in zip(cids[g:], csc[g:]) if s == 0.0)
         robust = set(int(c) for c in cids[:g]) - amb
-        if len(cids) > g and _close(csc[-1], s_g, tol) and len(cids) < D.n:
+    else:
+        amb = set(int(c) for c, s in zip(cids, csc) if near(s))
+        robust = set(int(c) for c in cids[:g]) - amb
+        if len(cids) > g and near(csc[-1]) and len(cids) < D.n:
             raise AssertionError(f"{what}: coarse tie group at rank gamma longer than the probe")
     gids = np.asarray(gids).astype(np.int64) & 0xFFFFFFFF
     gsc = np.asarray(gsc, np.float64)
@@ -121,16 +152,16 @@ def fp32_sum_bound(a, m):
     return g * np.asarray(a, np.float64) * (1 + 1e-9) + 1e-300
 
 
-def check_ranked_conditioned(gids, gsc, s, a, m, k, what=""):
+def check_ranked_conditioned(gids, gsc, s, a, m, k, what="", extra=0.0):
     """GPU top-k over signed data against the exact FP64 scores s[i] of every document i.
 
     With signed values a score can cancel to near zero, so no relative tolerance holds. Each document gets
     its own bound b[i] = fp32_sum_bound(a[i], m), a[i] = sum of |q_j x_j| over its products. The GPU's
     scores must be within b of the exact ones and non-increasing, its ids distinct, and no document it
     left out may certainly beat one it returned: max over the rest of (s - b) <= min over the answer of
-    (s + b)."""
+    (s + b). `extra` widens every bound (a fixed-point window: fixed_extra)."""
     s = np.asarray(s, np.float64)
-    b = fp32_sum_bound(a, m)
+    b = fp32_sum_bound(a, m) + extra
     n = min(k, len(s))
     gids = np.asarray(gids).astype(np.int64)[:n] & 0xFFFFFFFF
     gsc = np.asarray(gsc, np.float64)[:n]
@@ -173,7 +204,7 @@ def _beat_counts(s, b, exact0):
     return certain, might
 
 
-def check_reranked_conditioned(gids, gsc, sc, ac, mc, sf, af, mf, k, gamma, what=""):
+def check_reranked_conditioned(gids, gsc, sc, ac, mc, sf, af, mf, k, gamma, what="", coarse_extra=0.0):
     """GPU results of Algorithm 4 over signed data, for one query.
 
     sc, ac: the exact coarse score of every document (pruned document, pruned query) and its sum of
@@ -182,11 +213,12 @@ def check_reranked_conditioned(gids, gsc, sc, ac, mc, sf, af, mf, k, gamma, what
     best k of their FP32 reorder scores. So: every returned id must be a possible candidate (fewer than
     gamma documents certainly beat it on the coarse score); its score must lie within the FP32 bound of
     sf; the scores must descend; and no certain candidate (fewer than gamma documents might beat it) that
-    was left out may certainly beat a returned one on sf."""
+    was left out may certainly beat a returned one on sf. `coarse_extra` widens the coarse bounds (a
+    fixed-point window: fixed_extra)."""
     sc, sf = np.asarray(sc, np.float64), np.asarray(sf, np.float64)
     n_docs = len(sc)
     g, n = min(gamma, n_docs), min(k, n_docs)
-    bc, bf = fp32_sum_bound(ac, mc), fp32_sum_bound(af, mf)
+    bc, bf = fp32_sum_bound(ac, mc) + coarse_extra, fp32_sum_bound(af, mf)
     certain_c, might_c = _beat_counts(sc, bc, np.asarray(ac) == 0)
     possible, certain = certain_c < g, might_c < g
     gids = np.asarray(gids).astype(np.int64)[:n] & 0xFFFFFFFF

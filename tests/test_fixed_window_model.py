@@ -1,0 +1,111 @@
+"""A host model of the fixed-point score window (sindi_accumulator FIXED32), checked against exact sums.
+
+The device's rule for one (query, window): B = the FP32 sum of |w_j| * vmax_j over the window's terms (w_j the
+term weight, vmax_j the largest |stored value| of list j), e = 30 - x with 2^(x-1) <= B < 2^x, clamped so that
+every |w_j| * 2^e < 2^127 and to [-126, 126] (0 when B = 0). Each product is the FP32 product of the weight
+times 2^e (exact) and the stored value, rounded to the nearest integer (ties to even); the integer sums are
+exact; the score is the FP32 conversion of the sum times 2^-e.
+
+The model follows that rule in numpy and checks what the design depends on: no window sum reaches 2^31 even
+when every product of a document sits at its bound with one sign and B is summed in any order, and a score of
+m products is within 2^-23 * a + m * 2^-(e+1) <= 2^-23 * a + m * B * 2^-30 of the exact score. A mistake
+planted in the model's B (one term's bound instead of the sum) must overflow on the adversarial case."""
+import numpy as np
+import pytest
+
+F32 = np.float32
+
+
+def exponent_bound(f):
+    """x with 2^(x-1) <= f < 2^x for finite f > 0 (from the exponent field); subnormal: -126; inf: 140."""
+    E = int((np.array(f, F32).view(np.uint32) >> 23) & 0xFF)
+    return 140 if E == 0xFF else (-126 if E == 0 else E - 126)
+
+
+def pow2f(e):
+    return np.array((e + 127) << 23, np.uint32).view(F32)[()]
+
+
+def window_exponent(wq, vmax, order=None):
+    """The device's e for term weights wq and list bounds vmax (FP32), B summed in `order`."""
+    idx = np.arange(len(wq)) if order is None else order
+    B, M = F32(0), F32(0)
+    for t in idx:
+        B = F32(B + F32(abs(wq[t])) * F32(vmax[t]))
+        M = max(M, F32(abs(wq[t])))
+    if not B > 0:
+        return 0
+    e = 30 - exponent_bound(B)
+    if M > 0:
+        e = min(e, 127 - exponent_bound(M))
+    return max(-126, min(126, e))
+
+
+def fixed_score(wq, vals, e):
+    """(integer sum, FP32 score) of the products wq[t] * vals[t] in the fixed-point window with unit 2^-e."""
+    s = pow2f(e)
+    units = [np.rint(F32(F32(w) * s) * F32(x)) for w, x in zip(wq, vals)]
+    total = int(sum(int(u) for u in units))
+    return total, F32(F32(total) * pow2f(-e))
+
+
+def _terms(rng, n, lo, hi):
+    wq = (10.0 ** rng.uniform(lo, hi, n)).astype(F32)
+    vmax = (10.0 ** rng.uniform(lo, hi, n)).astype(F32)
+    return wq, vmax
+
+
+@pytest.mark.parametrize("n,lo,hi", [(1, 0, 0), (47, -1, 1), (400, -3, 3), (4096, -2, 2), (60, -30, -20),
+                                     (60, 15, 18), (200, -8, 8)])
+def test_no_window_sum_reaches_2_31(n, lo, hi):
+    """Every product at its bound, all of one sign, B summed in three orders: |sum| < 2^31."""
+    rng = np.random.default_rng(n * 7 + lo)
+    wq, vmax = _terms(rng, n, lo, hi)
+    for order in (None, np.argsort(wq * vmax), np.argsort(-(wq * vmax))):
+        e = window_exponent(wq, vmax, order)
+        for sign in (1, -1):
+            total, _ = fixed_score(wq * F32(sign), vmax, e)
+            assert abs(total) < 2 ** 31
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_score_error_within_the_bound(seed):
+    """Random documents over random terms (signed, some cancelling): |score - exact| <= 2^-23 a + m 2^-(e+1)
+    and m 2^-(e+1) <= m B 2^-30, with the exact sum taken in FP64 from the FP32 inputs."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 300))
+    wq, vmax = _terms(rng, n, -2, 2)
+    wq = wq * np.where(rng.random(n) < 0.3, F32(-1), F32(1)).astype(F32)
+    e = window_exponent(wq, vmax)
+    B = float(np.sum(np.abs(wq.astype(np.float64)) * vmax))
+    for _ in range(50):
+        m = int(rng.integers(1, n + 1))
+        terms = rng.choice(n, m, replace=False)
+        vals = (vmax[terms] * rng.uniform(0, 1, m)).astype(F32)
+        exact = float(np.sum(wq[terms].astype(np.float64) * vals.astype(np.float64)))
+        a = float(np.sum(np.abs(wq[terms].astype(np.float64) * vals.astype(np.float64))))
+        _, score = fixed_score(wq[terms], vals, e)
+        half_units = m * 2.0 ** (-(e + 1))
+        assert half_units <= m * B * 2.0 ** -30 * (1 + 1e-6)
+        assert abs(float(score) - exact) <= 2.0 ** -23 * a * (1 + 1e-6) + half_units * (1 + 1e-6)
+
+
+def test_unit_clamps():
+    """A weight so large that |w| * 2^e would pass 2^127 lowers e; tiny data stops at e = 126."""
+    wq, vmax = np.array([F32(1e30)], F32), np.array([F32(1e-35)], F32)
+    e = window_exponent(wq, vmax)
+    assert abs(float(wq[0]) * 2.0 ** e) < 2.0 ** 127 and np.isfinite(F32(wq[0] * pow2f(e)))
+    assert window_exponent(np.array([F32(1e-20)], F32), np.array([F32(1e-20)], F32)) == 126
+    assert window_exponent(np.zeros(3, F32), np.ones(3, F32)) == 0
+
+
+def test_a_planted_max_for_sum_overflows():
+    """The rule with B taken as the largest |w_j| * vmax_j instead of their sum (a plausible slip: one term's
+    bound for the window's) lets the adversarial sum of a 47-term query reach 2^31; the overflow test above
+    would catch it."""
+    rng = np.random.default_rng(5)
+    wq, vmax = _terms(rng, 47, -1, 1)
+    i = int(np.argmax(wq.astype(np.float64) * vmax))
+    e = window_exponent(wq[i:i + 1], vmax[i:i + 1])
+    total, _ = fixed_score(wq, vmax, e)
+    assert abs(total) >= 2 ** 31

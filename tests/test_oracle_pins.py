@@ -262,6 +262,21 @@ def test_unpruned_lists_are_the_transpose():
         assert kept.tolist() == np.diff(ip).tolist()
 
 
+def test_list_vmax_is_the_column_maximum():
+    """orc_list_vmax over an unpruned index (signed values) is max |column j| of D, and over a List-Pruning
+    index (which keeps each list's largest |x|) the same maximum: scipy's column maxima, a library routine."""
+    ip, ix, v = datagen.random_csr(300, 40, 7.0, seed=23)
+    v = np.where(np.arange(len(v)) % 3 == 1, -v, v).astype(np.float32)
+    D = oracle.Dataset(ip, ix, v, 40)
+    C = abs(_scipy(ip, ix, v, 40)).tocsc()
+    col_max = np.asarray(C.max(axis=0).todense()).ravel()
+    for I in (oracle.Index(D, window=64, alpha=1.0), oracle.Index(D, window=7, alpha=1.0, prune="list", prune_n=3)):
+        np.testing.assert_array_equal(I.list_vmax(), col_max)
+    empty = oracle.Index(oracle.Dataset(np.zeros(4, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32), 5),
+                         window=2)
+    np.testing.assert_array_equal(empty.list_vmax(), np.zeros(5))
+
+
 def test_pruned_lists_hold_exactly_the_alpha_mass_entries():
     ip, ix, v = datagen.random_csr(200, 50, 12.0, seed=31)
     D = oracle.Dataset(ip, ix, v, 50)
