@@ -228,6 +228,7 @@ struct Chunk {
     float v[kChunkU];
     uint32_t lm;
     float wq;
+    uint32_t vec;               // a long segment's chunk: every lane's 8 ids were loaded
 };
 
 // Loads the chunk at offset `off` (a multiple of kChunkLen) of the segment
@@ -244,8 +245,10 @@ __device__ __forceinline__ void load_segment_chunk(const DevIndex& ix, uint32_t 
 #pragma unroll
     for (int u = 0; u < kChunkU / 2; u++) k.id2[u] = 0;
     k.lm = 0;
+    k.vec = 0;
     if (!checked(segment_in_bounds(ps, pe, ix.pcap), ix.err)) return;
     if (pe - ps >= kVecMin) {
+        k.vec = 1;
         const uint32_t q0 = (ps & ~7u) + off + (uint32_t)lane * kChunkU;
         const uint32_t lo = ps > q0 ? ps - q0 : 0u;  // < 8: only the segment's first group
         const uint32_t hi = pe > q0 ? min(pe - q0, (uint32_t)kChunkU) : 0u;
@@ -280,6 +283,17 @@ __device__ __forceinline__ void load_chunk(const DevIndex& ix, const uint32_t* t
     load_segment_chunk<DT>(ix, t_start[t], t_end[t], (c - c_pre[t]) * (uint32_t)kChunkLen, lane, k);
 }
 
+// The same from the term table's packed records: {start, end, first chunk,
+// weight bits} per term, one 16-byte shared load.
+template <int DT>
+__device__ __forceinline__ void load_chunk_rec(const DevIndex& ix, const uint4* rec, const uint32_t* c_pre,
+                                               const uint16_t* c_term, int nc, uint32_t c, int lane, Chunk& k) {
+    const int t = c < (uint32_t)kChunkTable ? (int)c_term[c] : term_of(c_pre, nc, c);
+    const uint4 r = rec[t];
+    k.wq = __uint_as_float(r.w);
+    load_segment_chunk<DT>(ix, r.x, r.y, (c - r.z) * (uint32_t)kChunkLen, lane, k);
+}
+
 __device__ __forceinline__ uint32_t chunk_slot(const Chunk& k, int u) {
     return (k.id2[u >> 1] >> (16 * (u & 1))) & 0xFFFFu;
 }
@@ -295,8 +309,20 @@ __device__ __forceinline__ void add_chunk(float* A, uint32_t lambda, uint32_t* e
 
 // The same into a fixed-point window: each product (its weight already
 // carries the window's 2^e) rounded to the nearest unit and added with a
-// native shared-memory integer atomic.
+// native shared-memory integer atomic. In a long segment's chunk every lane
+// that loaded its group adds all 8 postings, the ones outside the segment
+// as 0 at the slot its load returned (an id of a neighbouring segment, or the
+// zero padding: a valid slot, and an integer + 0 changes nothing), so the
+// adds need no branch.
 __device__ __forceinline__ void add_chunk_fixed(int32_t* A, uint32_t lambda, uint32_t* err, const Chunk& k) {
+    if (k.vec && !kChecks) {
+        if (k.lm) {
+#pragma unroll
+            for (int u = 0; u < kChunkU; u++)
+                atomicAdd(&A[chunk_slot(k, u)], ((k.lm >> u) & 1u) ? __float2int_rn(k.wq * k.v[u]) : 0);
+        }
+        return;
+    }
 #pragma unroll
     for (int u = 0; u < kChunkU; u++)
         if ((k.lm & (1u << u)) && checked(slot_in_bounds(chunk_slot(k, u), lambda), err))
@@ -458,11 +484,13 @@ __device__ __forceinline__ void fx_term_bound(const DevIndex& ix, int32_t j, flo
 template <int DT, typename S>
 __device__ uint32_t build_term_table(const ScanArgs& a, uint32_t w, int64_t qb, int c0, int nc, uint32_t* t_start,
                                      uint32_t* t_end, float* t_w, uint32_t* c_pre, uint16_t* c_term, uint32_t* red,
-                                     uint32_t* negflag = nullptr, float* fred = nullptr) {
+                                     uint32_t* negflag = nullptr, float* fred = nullptr, uint4* rec = nullptr) {
     const DevIndex& ix = a.ix;
     const int tid = S::tid();
     uint32_t nch = 0;
     float fb = 0.0f, fm = 0.0f;  // fixed-point window: this thread's part of B and of max |w_j|
+    uint32_t r_start = 0, r_end = 0;  // the term's packed record (rec), once its first chunk is known
+    float r_w = 0.0f;
     if (tid < nc) {
         const int32_t j = a.q_indices[qb + c0 + tid];
         const float qv = a.q_values[qb + c0 + tid];
@@ -480,6 +508,9 @@ __device__ uint32_t build_term_table(const ScanArgs& a, uint32_t w, int64_t qb, 
         t_start[tid] = start;
         t_end[tid] = start + len;
         t_w[tid] = wq;
+        r_start = start;
+        r_end = start + len;
+        r_w = wq;
         if (fred) fx_term_bound<DT>(ix, j, qv, len, fb, fm);
         // chunks of a long list tile its 8-aligned groups of postings
         nch = len >= kVecMin ? (((start + len + 7u) & ~7u) - (start & ~7u) + kChunkLen - 1) / kChunkLen
@@ -491,6 +522,7 @@ __device__ uint32_t build_term_table(const ScanArgs& a, uint32_t w, int64_t qb, 
     const uint32_t excl = group_exclusive_sum<uint32_t, S>(nch, &total, red);
     if (tid < nc) {
         c_pre[tid] = excl;
+        if (rec) rec[tid] = make_uint4(r_start, r_end, excl, __float_as_uint(r_w));
         for (uint32_t c = excl; c < excl + nch && c < (uint32_t)kChunkTable; c++) c_term[c] = (uint16_t)tid;
     }
     S::sync();
@@ -504,20 +536,28 @@ template <int DT, int NW, bool FIXED = false>
 __device__ __forceinline__ void accumulate_table(const DevIndex& ix, const uint32_t* t_start, const uint32_t* t_end,
                                                  const float* t_w, const uint32_t* c_pre, const uint16_t* c_term,
                                                  int nc, uint32_t total, int warp, int lane, float* A,
-                                                 float wscale = 1.0f) {
+                                                 float wscale = 1.0f, const uint4* rec = nullptr) {
+    // two chunks in registers, taking turns (no copy between them)
     uint32_t c = (uint32_t)warp;
-    Chunk cur;
-    if (c < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, c, lane, cur);
-    if (FIXED) cur.wq *= wscale;  // the fixed-point window's 2^e (exact)
+    Chunk ka, kb;
+    auto load = [&](uint32_t cc, Chunk& k) {
+        if (rec) load_chunk_rec<DT>(ix, rec, c_pre, c_term, nc, cc, lane, k);
+        else load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, cc, lane, k);
+        if (FIXED) k.wq *= wscale;  // the fixed-point window's 2^e (exact)
+    };
+    auto add = [&](const Chunk& k) {
+        if (FIXED) add_chunk_fixed(reinterpret_cast<int32_t*>(A), ix.lambda, ix.err, k);
+        else add_chunk(A, ix.lambda, ix.err, k);
+    };
+    if (c < total) load(c, ka);
     while (c < total) {
-        const uint32_t cn = c + NW;
-        Chunk nxt;
-        if (cn < total) load_chunk<DT>(ix, t_start, t_end, t_w, c_pre, c_term, nc, cn, lane, nxt);
-        if (FIXED) nxt.wq *= wscale;
-        if (FIXED) add_chunk_fixed(reinterpret_cast<int32_t*>(A), ix.lambda, ix.err, cur);
-        else add_chunk(A, ix.lambda, ix.err, cur);
-        cur = nxt;
-        c = cn;
+        c += NW;
+        if (c < total) load(c, kb);
+        add(ka);
+        if (c >= total) break;
+        c += NW;
+        if (c < total) load(c, ka);
+        add(kb);
     }
 }
 
@@ -923,7 +963,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     // Shared memory: the window's scores, two histograms, and one region that
     // holds the term tables while postings are added and the staged
     // candidates of the window afterwards.
-    constexpr int kTableBytes = ((4 * kTermChunk + 1) * 4 + kChunkTable * 2 + 15) & ~15;
+    constexpr int kTableBytes = 16 * kTermChunk + (((4 * kTermChunk + 1) * 4 + kChunkTable * 2 + 15) & ~15);
     constexpr int kPrivBytes = kScanWarps * kRelBins * 4;
     constexpr int kRegionBytes = kTableBytes > kPrivBytes ? kTableBytes : kPrivBytes;
     extern __shared__ float A[];                    // [lambda]
@@ -936,7 +976,8 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
     __shared__ uint32_t s_staged;
     __shared__ uint32_t s_qneg;  // the query has a negative value
     __shared__ float fred[2 * kScanWarps];  // fixed-point window: the warps' parts of B and of max |w_j|
-    uint32_t* t_start = reinterpret_cast<uint32_t*>(region);
+    uint4* t_rec = reinterpret_cast<uint4*>(region);  // the terms' packed records, read once per chunk
+    uint32_t* t_start = reinterpret_cast<uint32_t*>(region + 16 * kTermChunk);
     uint32_t* t_end = t_start + kTermChunk;
     uint32_t* c_pre = t_end + kTermChunk;
     float* t_w = reinterpret_cast<float*>(c_pre + kTermChunk + 1);
@@ -977,13 +1018,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) scan_window_kernel(ScanAr
         const int nc = min(kTermChunk, nt - c0);
         __syncthreads();  // previous chunk fully consumed
         const uint32_t total = build_term_table<DT, S>(a, w, qb, c0, nc, t_start, t_end, t_w, c_pre, c_term, red,
-                                                       &s_qneg, FX && !fx_pre ? fred : nullptr);
+                                                       &s_qneg, FX && !fx_pre ? fred : nullptr, t_rec);
         if (FX) {
             if (!fx_pre) fx_e = fx_exponent(fred, kScanWarps);
             accumulate_table<DT, kScanWarps, true>(ix, t_start, t_end, t_w, c_pre, c_term, nc, total, warp, lane, A,
-                                                   pow2f(fx_e));
+                                                   pow2f(fx_e), t_rec);
         } else {
-            accumulate_table<DT, kScanWarps>(ix, t_start, t_end, t_w, c_pre, c_term, nc, total, warp, lane, A);
+            accumulate_table<DT, kScanWarps>(ix, t_start, t_end, t_w, c_pre, c_term, nc, total, warp, lane, A,
+                                             1.0f, t_rec);
         }
     }
     __syncthreads();
