@@ -467,29 +467,35 @@ def _recall_vs_fp64(ids, truth, D, Q):
 
 def _score_errors(idx, torch, dev, w, ip, ix, v, qp, qx, qv, D, Q, rows, final_ids, final_sc):
     """Max relative score error against FP64 on sampled rows: coarse (the GPU's gamma = 0 scores, quantised
-    postings, against the FP64 dot product of the same document's alpha-mass subvector with the query) and
-    final (the reordered FP32 scores against exact delta)."""
+    postings, against the FP64 dot product of the same document's alpha-mass subvector with the query), in
+    the FP32 window (the default at gamma = 0) and in the fixed-point window (the default when the search
+    reorders), and final (the reordered FP32 scores against exact delta)."""
     import oracle
 
     sub = [torch.from_numpy(a).to(dev) for a in (np.concatenate([[0], np.cumsum([qp[r + 1] - qp[r] for r in rows])]),
                                                   np.concatenate([qx[qp[r]:qp[r + 1]] for r in rows]),
                                                   np.concatenate([qv[qp[r]:qp[r + 1]] for r in rows]))]
-    cids, csc = idx.search(*sub, k=w.k, gamma=0, mode="batched")
-    cids, csc = cids.cpu().numpy().view(np.uint32), csc.cpu().numpy()
-    ce = fe = 0.0
+    coarse = {}
+    for accum in ("f32", "fixed32"):
+        cids, csc = idx.search(*sub, k=w.k, gamma=0, mode="batched", accum=accum)
+        coarse[accum] = (cids.cpu().numpy().view(np.uint32), csc.cpu().numpy())
+    ce = {"f32": 0.0, "fixed32": 0.0}
+    fe = 0.0
     for n, r in enumerate(rows):
         qd = dict(zip(qx[qp[r]:qp[r + 1]].tolist(), qv[qp[r]:qp[r + 1]].astype(np.float64).tolist()))
-        for i, sc in zip(cids[n], csc[n]):
-            a, b = ip[i], ip[i + 1]
-            pos = oracle.alpha_mass(ix[a:b], v[a:b], w.alpha)
-            ref = sum(qd.get(int(j), 0.0) * float(x) for j, x in zip(ix[a:b][pos], v[a:b][pos]))
-            if ref != 0.0:
-                ce = max(ce, abs(float(sc) - ref) / abs(ref))
+        for accum, (cids, csc) in coarse.items():
+            for i, sc in zip(cids[n], csc[n]):
+                a, b = ip[i], ip[i + 1]
+                pos = oracle.alpha_mass(ix[a:b], v[a:b], w.alpha)
+                ref = sum(qd.get(int(j), 0.0) * float(x) for j, x in zip(ix[a:b][pos], v[a:b][pos]))
+                if ref != 0.0:
+                    ce[accum] = max(ce[accum], abs(float(sc) - ref) / abs(ref))
         for i, sc in zip(final_ids[r], final_sc[r]):
             ex = oracle.inner_product(D, int(i), Q, r)
             if ex != 0.0:
                 fe = max(fe, abs(float(sc) - ex) / abs(ex))
-    return {"coarse_max_rel_err_vs_fp64": ce, "final_max_rel_err_vs_fp64": fe, "score_error_queries": len(rows)}
+    return {"coarse_max_rel_err_vs_fp64": ce["f32"], "coarse_fixed_window_max_rel_err_vs_fp64": ce["fixed32"],
+            "final_max_rel_err_vs_fp64": fe, "score_error_queries": len(rows)}
 
 
 def plan_leg(sindi, torch, dev, w, dd, qp, qx, qv, dtype, steps, warmup, flush, stream, D, Q, truth, host_docs):

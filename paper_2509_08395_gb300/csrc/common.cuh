@@ -145,7 +145,7 @@ inline uint32_t ceil_div_u32(uint64_t a, uint64_t b) { return (uint32_t)((a + b 
 // segment is one chunk whose lane l owns postings s + l + 32u.
 constexpr int kChunkU = 8;                 // postings per lane in one warp chunk
 constexpr int kChunkLen = 32 * kChunkU;    // postings of one warp chunk (one list only)
-constexpr uint32_t kVecMin = 128;          // segments this long are read with vector loads
+constexpr uint32_t kVecMin = 32;           // segments this long are read with vector loads
 
 // sindi_search_params.block_threads: 0 (default), SINDI_SCAN_PIPELINED, 256, 512 or 1024.
 inline bool valid_block_threads(uint32_t b) {
