@@ -257,6 +257,12 @@ __device__ __forceinline__ void load_segment_chunk(const DevIndex& ix, uint32_t 
         if (k.lm) {
             load_ids8(ix.pid, q0, k.id2);
             load_values8<DT>(ix.pval, q0, k.v);
+            if (k.lm != 0xFFu) {
+                // a group at the segment's start or end: the postings outside it weigh 0
+#pragma unroll
+                for (int u = 0; u < kChunkU; u++)
+                    if (!((k.lm >> u) & 1u)) k.v[u] = 0.0f;
+            }
         }
     } else {
         const uint32_t q0 = ps + (uint32_t)lane;
@@ -310,16 +316,17 @@ __device__ __forceinline__ void add_chunk(float* A, uint32_t lambda, uint32_t* e
 // The same into a fixed-point window: each product (its weight already
 // carries the window's 2^e) rounded to the nearest unit and added with a
 // native shared-memory integer atomic. In a long segment's chunk every lane
-// that loaded its group adds all 8 postings, the ones outside the segment
-// as 0 at the slot its load returned (an id of a neighbouring segment, or the
-// zero padding: a valid slot, and an integer + 0 changes nothing), so the
-// adds need no branch.
+// that loaded its group adds all 8 postings: the ones outside the segment
+// have value 0 (load_segment_chunk) and add 0 at the slot their load
+// returned (an id of a neighbouring segment, or the zero padding: a valid
+// slot, and an integer + 0 changes nothing), so the adds need no branch and
+// no select.
 __device__ __forceinline__ void add_chunk_fixed(int32_t* A, uint32_t lambda, uint32_t* err, const Chunk& k) {
     if (k.vec && !kChecks) {
         if (k.lm) {
 #pragma unroll
             for (int u = 0; u < kChunkU; u++)
-                atomicAdd(&A[chunk_slot(k, u)], ((k.lm >> u) & 1u) ? __float2int_rn(k.wq * k.v[u]) : 0);
+                atomicAdd(&A[chunk_slot(k, u)], __float2int_rn(k.wq * k.v[u]));
         }
         return;
     }
