@@ -1610,9 +1610,31 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
     }
     wait_previous_kernels();
     const uint32_t C = min(ws.cand_count[y], ws.cand_cap);
+    uint32_t* H = ws.hist + (size_t)y * kHistBins;
+    // Every block takes one ticket on the query's way out, whatever path it takes; the last one leaves
+    // the query's counters and H at zero for the next launch that uses this workspace. (A block must not
+    // reset them while another block of the grid may still read H.)
+    auto finish = [&]() {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = (atomicAdd(ws.mticket + y, 1u) == gridDim.x - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        for (int b = threadIdx.x; b < kHistBins; b += kMergeThreads) H[b] = 0;
+        if (threadIdx.x == 0) {
+            ws.cand_count[y] = 0;
+            ws.fcount[y] = 0;
+            ws.mticket[y] = 0;
+        }
+    };
+    // S <= C: with C within both limits block 0 merges the query alone (below), the others have no work
+    if (blockIdx.x != 0 && C <= kMergeOneBlock && C <= ws.fcap) {
+        finish();
+        return;
+    }
     const uint32_t g = a.g < C ? a.g : C;
     const uint64_t* cand = ws.cand + (size_t)y * ws.cand_cap;
-    uint32_t* H = ws.hist + (size_t)y * kHistBins;
 
     // bin of the g-th best candidate; every candidate below it is out
     block_find_bin<kHistBins, kMergeThreads>([&](int b) { return __ldcg(H + b); }, g, red, st);
@@ -1624,8 +1646,11 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
     const uint32_t dcap = a.final_stage ? (uint32_t)kMaxK : ws.top_cap;
     if (C <= kMergeOneBlock && S <= ws.fcap) {
         // few candidates: block 0 alone gathers the survivors into shared
-        // memory and selects; no filter buffer, fence or ticket
-        if (blockIdx.x != 0) return;
+        // memory and selects; no filter buffer
+        if (blockIdx.x != 0) {
+            finish();
+            return;
+        }
         for (uint32_t base = 0; base < C; base += kMergeThreads * 4) {
             uint64_t kk[4];
 #pragma unroll
@@ -1648,7 +1673,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
         __syncthreads();
         if (threadIdx.x == 0) s_n = 0;
         __syncthreads();
-        allow_next_kernel();  // the other blocks have exited: the rerank may start
+        allow_next_kernel();  // the rerank may launch once the other block has taken its ticket and exited
         auto key_of = [&](int i) -> uint64_t { return sbuf[i]; };
         const uint64_t T = nf > g ? block_select_threshold<kMergeThreads>(key_of, (int)nf, (int)g, hist256, st) : 0ull;
         gather_at_least<kMergeThreads>(key_of, nf, T, dst, dcap, &s_n);
@@ -1658,13 +1683,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(MergeArgs a) {
         } else if (threadIdx.x == 0) {
             ws.top_count[y] = min(s_n, ws.top_cap);
         }
-        __syncthreads();
-        for (int b = threadIdx.x; b < kHistBins; b += kMergeThreads) H[b] = 0;
-        if (threadIdx.x == 0) {
-            ws.cand_count[y] = 0;
-            ws.fcount[y] = 0;
-            ws.mticket[y] = 0;
-        }
+        finish();
         return;
     }
     {
@@ -2004,7 +2023,9 @@ static Plan make_plan(const IndexImpl& ix, const sindi_search_params& prm) {
     while (f < 2 * p.g && f < 16384) f <<= 1;
     p.fcap = f;
     p.top_cap = p.final_stage ? 1 : p.g;
-    p.merge_blocks = std::max<uint32_t>(1, std::min<uint32_t>(16, p.cand_cap / 8192));
+    // two blocks: a query's merge is one block unless its candidates crowd the cut, and every block of
+    // the grid is resident (holding its shared memory) while the scan finishes
+    p.merge_blocks = std::max<uint32_t>(1, std::min<uint32_t>(2, p.cand_cap / 8192));
     p.block = prm.block_threads;
     p.group = group_size(ix, prm.group, prm.block_threads);
     p.fixed = prm.accumulator == SINDI_ACCUM_FIXED32 || (prm.accumulator == SINDI_ACCUM_AUTO && !p.final_stage);
