@@ -2264,7 +2264,7 @@ static void enqueue_plain_lanes(const IndexImpl& ix, const Plan& pl, const std::
                                 const int64_t* q_indptr, const int32_t* q_indices, const float* q_values,
                                 int64_t n_queries, uint32_t k, uint32_t* out_ids, float* out_scores,
                                 cudaStream_t stream, const std::vector<cudaStream_t>& ls, const QueryCsr* pruned,
-                                std::vector<cudaEvent_t>& evs) {
+                                std::vector<cudaEvent_t>& evs, bool chain_queries) {
     const int lanes = (int)ls.size();
     cudaEvent_t fork = nullptr;
     SINDI_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
@@ -2274,7 +2274,9 @@ static void enqueue_plain_lanes(const IndexImpl& ix, const Plan& pl, const std::
     std::vector<char> lane_chained(lanes, 0);
     for (int64_t q = 0; q < n_queries; q++) {
         const int l = (int)(q % lanes);
-        bool c = lane_chained[l] != 0;
+        // chain_queries: a lane's next query may start (programmatic dependent launch) while the previous
+        // one's last kernel runs; otherwise it follows that kernel's completion in stream order
+        bool c = chain_queries && lane_chained[l] != 0;
         launch_group(ix, pl, wss[l], q_indptr, q_indices, q_values, q, 1, false, k, out_ids, out_scores, ls[l], &c,
                      nullptr, nullptr, pruned);
         lane_chained[l] = c ? 1 : 0;
@@ -2326,7 +2328,7 @@ static void capture_plain_graph(const IndexImpl& ix, const Plan& pl, const Index
         for (int l = 0; l < lanes; l++)
             SINDI_CUDA(cudaMemsetAsync(mem + ws_stride * l, 0, workspace_counter_bytes(1), cap));
         enqueue_plain_lanes(ix, pl, wss, q_indptr, q_indices, q_values, n_queries, k, out_ids, out_scores, cap, ls,
-                            nullptr, evs);
+                            nullptr, evs, true);
         capturing = false;
         SINDI_CUDA(cudaStreamEndCapture(cap, &graph));
         SINDI_CUDA(cudaGraphInstantiate(&ix.graph_exec, graph, 0));
@@ -2481,7 +2483,7 @@ sindi_status search_impl(const IndexImpl& ix, const int64_t* q_indptr, const int
         }
         std::vector<cudaEvent_t> evs_lane;
         enqueue_plain_lanes(ix, pl, wss, q_indptr, q_indices, q_values, n_queries, k, out_ids, out_scores, stream, ls,
-                            pruned.indptr ? &pruned : nullptr, evs_lane);
+                            pruned.indptr ? &pruned : nullptr, evs_lane, false);
         for (cudaEvent_t e : evs_lane) SINDI_CUDA(cudaEventDestroy(e));
     }
     for (int64_t q0 = 0; lanes == 1 && q0 < n_queries; q0 += chunk) {

@@ -106,6 +106,25 @@ def test_fixed_window_sums_do_not_depend_on_the_order_of_the_adds():
                 np.testing.assert_array_equal(a[1].view(np.uint32), x[1].view(np.uint32))
 
 
+def test_plain_lanes_reuse_workspaces_across_queries():
+    """The plain schedule runs a lane's queries one after another on one workspace, which each query's merge
+    leaves at zero for the next. With gamma 2,000 most queries' candidates exceed one merge block's filter
+    buffer, so both merge blocks read the query's histogram before the workspace is reset. 200 queries (about
+    8 per lane): three plain calls and the batched schedule give bit-identical answers, and sampled rows
+    reorder to the oracle's answer."""
+    w, (ip, ix, v), (qp, qx, qv) = _workload(40_000, 200, False)
+    D, Q = oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+    I = oracle.Index(D, window=4096, alpha=0.5)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=4096, alpha=0.5) as idx:
+        runs = [search(idx, (qp, qx, qv), k=20, gamma=2000, mode="plain", accum="auto") for _ in range(3)]
+        runs.append(search(idx, (qp, qx, qv), k=20, gamma=2000, mode="batched", accum="auto"))
+    for x in runs[1:]:
+        np.testing.assert_array_equal(runs[0][0], x[0])
+        np.testing.assert_array_equal(runs[0][1].view(np.uint32), x[1].view(np.uint32))
+    for r in range(0, Q.n, 13):
+        check_reranked(runs[0][0][r], runs[0][1][r], D, Q, r, I, 20, 2000, what=f"query {r}")
+
+
 @pytest.mark.parametrize("mode", ["plain", "batched"])
 def test_both_windows_reorder_to_the_oracle_answer(mode):
     """gamma > 0 with either window (FP32 atomics, or the default fixed point): each answer is the oracle's
