@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fixed_point.cuh"
 #include "index.cuh"
 #include "mass.cuh"
 #include "primitives.cuh"
@@ -428,23 +429,11 @@ struct CutScratch {
 };
 
 // ---------------------------------------------------------------------------
-// The fixed-point window (sindi_accumulator FIXED32). For one (query, window):
-// B = the sum of |w_j| * vmax_j over the terms whose list I_{j,w} is not empty
-// (w_j = q_j, times the list scale for E4M3), e = 30 - x with 2^(x-1) <= B <
-// 2^x, clamped so that every |w_j| * 2^e < 2^127 and to [-126, 126]; 0 when B
-// = 0. The window holds integers in units of 2^-e, and every sum stays below
-// 2^31 (B * 2^e < 2^30, plus half a unit per product).
+// The fixed-point window (sindi_accumulator FIXED32): the block-wide sums of
+// B and of max |w_j| for one (query, window); fixed_point.cuh holds the rule
+// that turns them into the unit 2^-e, and the integer bound of a bounded
+// window.
 // ---------------------------------------------------------------------------
-
-// x with 2^(x-1) <= f < 2^x for a finite f > 0 (from the exponent field; a
-// subnormal f gets x = -126, an upper bound); inf: the bound of a sum of at
-// most kMaxQueryTerms values below 2^128.
-__device__ __forceinline__ int exponent_bound(float f) {
-    const int E = (int)((__float_as_uint(f) >> 23) & 0xFFu);
-    return E == 0xFF ? 128 + 12 : (E == 0 ? -126 : E - 126);
-}
-
-__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }  // |e| <= 126
 
 // A warp's share of B and of max |w_j| (b, m: this thread's terms) into
 // fred[warp] and fred[nw + warp]; every lane of the warp calls it.
@@ -468,10 +457,7 @@ __device__ __forceinline__ int fx_exponent(const float* fred, int nw) {
         B += fred[i];
         M = fmaxf(M, fred[nw + i]);
     }
-    if (!(B > 0.0f)) return 0;
-    int e = 30 - exponent_bound(B);
-    if (M > 0.0f) e = min(e, 127 - exponent_bound(M));
-    return max(-126, min(126, e));
+    return fx_exponent_from(B, M);
 }
 
 // This thread's part of B for term j of weight qv over window w.
@@ -604,24 +590,6 @@ __device__ __forceinline__ void fx_window_to_float(float* A, uint32_t lambda, in
         const int4 t = I4[m];
         F4[m] = make_float4((float)t.x * inv, (float)t.y * inv, (float)t.z * inv, (float)t.w * inv);
     }
-}
-
-// An integer t such that every sum n of a fixed-point window (unit 2^-e, |n| <
-// 2^31) whose FP32 score float(n) * 2^-e is >= thr has n >= t: the exact least
-// such n when |thr * 2^e| <= 2^24 (where the conversion is exact), else up to
-// 128 below it (the conversion's rounding at |n| < 2^31), so a few slots just
-// under the bound may also be emitted, which the merge drops. NaN: none; -inf:
-// all; thr > 0: at least 1 (a zero sum scores 0).
-__device__ __forceinline__ int32_t fx_threshold(float thr, int e) {
-    if (thr != thr) return INT32_MAX;
-    if (thr == -INFINITY) return INT32_MIN;
-    const float X = thr * pow2f(e);
-    int32_t t;
-    if (X >= 2147483648.0f) t = INT32_MAX;
-    else if (X < -2147483648.0f) t = INT32_MIN;
-    else if (fabsf(X) <= 16777216.0f) t = (int32_t)ceilf(X);
-    else t = (int32_t)floorf(X) - 128;
-    return thr > 0.0f ? max(t, 1) : t;
 }
 
 // The least float whose order key is at least k: a slot's key is >= k

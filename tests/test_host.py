@@ -383,3 +383,94 @@ int main() {
     subprocess.run(["g++", "-std=c++17", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe)], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_fixed_point_rule_compiled_for_the_host(tmp_path):
+    """The fixed-point window's arithmetic (csrc/fixed_point.cuh), compiled for the host:
+    - exponent_bound brackets every positive float (2^(x-1) <= f < 2^x; subnormal, inf);
+    - pow2f is 2^e;
+    - fx_exponent_from keeps B * 2^e below 2^30 and every |w| * 2^e below 2^127, within [-126, 126];
+    - fx_threshold, brute-forced around every threshold it returns: no sum whose FP32 score reaches the
+      bound is below it, it is exact while the bound is within 2^24 units, and at most 129 units low above
+      that (also next to -2^31, where a 32-bit margin would wrap)."""
+    import subprocess
+
+    src = tmp_path / "fixed_host.cpp"
+    src.write_text(r"""
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <random>
+#include "fixed_point.cuh"
+using namespace sindi;
+#define T(c) do { if (!(c)) { std::printf("failed line %d: %s\n", __LINE__, #c); return 1; } } while (0)
+static bool qualifies(int64_t n, float thr, int e) { return (float)n * pow2f(-e) >= thr; }
+int main() {
+    std::mt19937 rng(7);
+    // exponent_bound and pow2f
+    for (int e = -126; e <= 126; e++) T(pow2f(e) == std::ldexp(1.0f, e));
+    std::uniform_real_distribution<double> ex(-125.0, 127.0), fr(1.0, 2.0);
+    for (int i = 0; i < 20000; i++) {
+        const float f = (float)std::ldexp(fr(rng), (int)std::floor(ex(rng)));
+        if (!(f > 0.0f) || std::isinf(f)) continue;
+        const int x = exponent_bound(f);
+        T(std::ldexp(1.0, x - 1) <= (double)f && (double)f < std::ldexp(1.0, x));
+    }
+    T(exponent_bound(1.0f) == 1 && exponent_bound(0.75f) == 0 && exponent_bound(2.0f) == 2);
+    T(exponent_bound(1e-40f) == -126 && exponent_bound(INFINITY) == 140);
+    // fx_exponent_from
+    T(fx_exponent_from(0.0f, 1.0f) == 0 && fx_exponent_from(-1.0f, 1.0f) == 0);
+    T(fx_exponent_from(1e-38f, 1e-38f) == 126 && fx_exponent_from(1e38f, 1.0f) == -97);  // 1e38 < 2^127
+    T(fx_exponent_from(1.0f, 1e30f) == 127 - exponent_bound(1e30f));
+    for (int i = 0; i < 20000; i++) {
+        const float B = (float)std::ldexp(fr(rng), (int)std::floor(ex(rng)) - 1);
+        const float M = (float)std::ldexp(fr(rng), (int)std::floor(ex(rng)) - 1);
+        if (!(B > 0.0f) || std::isinf(B) || !(M > 0.0f) || std::isinf(M)) continue;
+        const int e = fx_exponent_from(B, M);
+        T(e >= -126 && e <= 126);
+        if (e > -126) T((double)B * std::ldexp(1.0, e) < std::ldexp(1.0, 30));
+        T((double)M * std::ldexp(1.0, e) < std::ldexp(1.0, 127));
+    }
+    // fx_threshold: specials
+    T(fx_threshold(NAN, 0) == INT32_MAX && fx_threshold(-INFINITY, 5) == INT32_MIN);
+    T(fx_threshold(INFINITY, 0) == INT32_MAX);
+    T(fx_threshold(1.0e-45f, -126) == 1);  // the least positive float: only positive sums
+    T(fx_threshold(0.0f, 7) == 0 && fx_threshold(-0.0f, 7) == 0);
+    // fx_threshold: brute force around the threshold
+    const int es[] = {-126, -60, -3, 0, 5, 30, 90, 126};
+    std::uniform_real_distribution<double> lg(-31.5, 31.5), sg(0.0, 1.0);
+    int checked = 0;
+    for (int e : es) {
+        for (int i = 0; i < 400; i++) {
+            // bounds at every scale of units, both signs, and at the 2^24 and 2^31 edges
+            double units = std::pow(2.0, lg(rng));
+            if (i % 10 == 0) units = 16777216.0 + (double)(i % 7) - 3.0;
+            if (i % 10 == 1) units = 2147483648.0 - (double)(i % 200);
+            const double sign = sg(rng) < 0.5 ? -1.0 : 1.0;
+            const float thr = (float)(sign * units * std::ldexp(1.0, -e));
+            if (thr == 0.0f || std::isinf(thr)) continue;
+            const int32_t t = fx_threshold(thr, e);
+            const double X = (double)thr * std::ldexp(1.0, e);
+            int64_t lo = (int64_t)t - 400, hi = (int64_t)t + 400;
+            if (lo < INT32_MIN) lo = INT32_MIN;
+            if (hi > INT32_MAX) hi = INT32_MAX;
+            for (int64_t n = lo; n <= hi; n++) {
+                if (qualifies(n, thr, e)) T(n >= t);                            // never above the least qualifying sum
+                if (std::fabs(X) < 16777216.0 && n >= t) T(qualifies(n, thr, e));   // exact below 2^24 units
+                checked++;
+            }
+            if (X > 16777216.0 && X < 2147483648.0) T((double)t >= std::floor(X) - 129.0);
+            if (X < -16777216.0 && X >= -2147483648.0) T((double)t >= std::floor(X) - 129.0 || t == INT32_MIN);
+        }
+    }
+    T(fx_threshold(-2147483648.0f, 0) == INT32_MIN);                  // -2^31 units: no 32-bit wrap
+    T(fx_threshold(-2147483520.0f, 0) == INT32_MIN);                  // within 128 of -2^31
+    std::printf("ok %d\n", checked);
+    return 0;
+}
+""")
+    exe = tmp_path / "fixed_host"
+    inc = os.path.join(ROOT, "paper_2509_08395_gb300", "csrc")
+    subprocess.run(["g++", "-std=c++17", "-O2", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
