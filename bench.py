@@ -66,7 +66,7 @@ def parse():
     p.add_argument("--scale-steps", type=int, default=3, help="timed graph launches per full-size leg")
     p.add_argument("--scale-queries", type=int, default=0, help="0 = every query of configs 3-5 (10,000)")
     p.add_argument("--scale-serve-sweep", default="0.25,0.5,0.75,0.9,1.1",
-                   help="offered loads of config 5's serving leg (fractions of its batched capacity)")
+                   help="offered loads of the serve-25m serving leg (fractions of its batched capacity)")
     p.add_argument("--serve-sweep", default=None,
                    help="comma-separated offered loads (fractions of batched QPS) for the serving leg "
                         "(default 0.25,0.5,0.75,0.9,1.1)")
@@ -567,7 +567,7 @@ def scale_legs(sindi, torch, dev, args, flush, stream, base_qps_fn=None):
     gen_s = time.perf_counter() - t0
     dd = [torch.from_numpy(a).to(dev) for a in (ip, ix, v)]
     D = oracle.Dataset(ip, ix, v, w3.dim)
-    # config 4's queries also on FP32 postings: the reduced-precision legs' baseline in the same schedule
+    # the lowprec-8.8m queries also on FP32 postings: the reduced-precision legs' baseline in the same schedule
     for w, dtypes in ((w3, ("f32",)), (w4, ("f32", "f16", "f8"))):
         qp, qx, qv = datagen.queries(w)
         if args.scale_queries:
@@ -584,7 +584,7 @@ def scale_legs(sindi, torch, dev, args, flush, stream, base_qps_fn=None):
             out[f"{w.name}/{dt}"] = leg
     del dd, D
     torch.cuda.empty_cache()
-    # config 5: 25M documents, FP16 postings; batched capacity, then open-loop serving up to saturation
+    # serve-25m: 25M documents, FP16 postings; batched capacity, then open-loop serving up to saturation
     w5 = datagen.WORKLOADS["serve-25m"]
     t0 = time.perf_counter()
     ip, ix, v = datagen.docs(w5)
