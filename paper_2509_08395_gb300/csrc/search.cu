@@ -627,8 +627,10 @@ __device__ void select_window(const ScanArgs& a, float* A, uint32_t w, uint32_t 
     const int64_t rest = ix.n_docs - gbase;
     const int n_eff = (int)(rest < (int64_t)lambda ? rest : (int64_t)lambda);
     const uint32_t g_w = a.g < (uint32_t)n_eff ? a.g : (uint32_t)n_eff;
-    // fx_e != kNoFx (only with FX, only for a bounded window): A holds the fixed-point sums in units of 2^-fx_e
-    const bool fx = FX && fx_e != kNoFx;
+    // fx_e != kNoFx (only with FX, only for a bounded window): A holds the fixed-point sums in units of 2^-fx_e,
+    // until a bounded window with too many slots at the bound converts them to FP32 for the full cut (fx
+    // then turns false, and key_of reads the FP32 scores)
+    bool fx = FX && fx_e != kNoFx;
     const float fx_inv = fx ? pow2f(-fx_e) : 1.0f;
     const int32_t* Ai = reinterpret_cast<const int32_t*>(A);
     auto key_of = [&](int i) -> uint64_t {
@@ -731,6 +733,7 @@ __device__ void select_window(const ScanArgs& a, float* A, uint32_t w, uint32_t 
         if (fx) {
             fx_window_to_float<S>(A, lambda, fx_e);
             S::sync();
+            fx = false;
         }
     }
     // level 1: 12-bit bins of the score key. Each warp counts its slots in a

@@ -159,3 +159,37 @@ def test_emulated_window_on_oracle_lists_is_within_the_test_allowance():
         assert np.all(np.abs(score.astype(np.float64) - s) <= fp32_sum_bound(a, m) + extra), f"query {r}"
         order = sorted(range(D.n), key=lambda i: (-float(score[i]), i))[:50]
         check_ranked_conditioned(np.array(order), score[order], s, a, m, 50, what=f"query {r}", extra=extra)
+
+
+def _fp32_bits_read_as_sums(keys, e=18):
+    """A fault the scan once had: after a bounded fixed-point window converted its sums to FP32 for the full cut,
+    the cut kept reading slots as integer sums, so each emitted score became (FP32 bits as an integer) * 2^-e."""
+    from test_selection_model import keys_of
+    ob = (keys >> np.uint64(32)).astype(np.uint64)
+    u = np.where(ob & np.uint64(0x80000000), ob & np.uint64(0x7FFFFFFF), (~ob) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    as_sum = u.view(np.float32).view(np.int32).astype(np.float32)
+    ids = np.uint64(0xFFFFFFFF) - (keys & np.uint64(0xFFFFFFFF))
+    return keys_of((as_sum * F32(2.0 ** -e)).astype(F32), ids)
+
+
+@pytest.mark.parametrize("schedule", ["plain_split", "batched"])
+def test_a_bounded_window_that_falls_back_keeps_fp32_keys(schedule):
+    """Windows whose slots at the bound outnumber what one window may emit (here: many equal scores) fall back
+    on the full cut after converting their sums to FP32. The model of the device returns exactly the best g.
+    With the fault planted (the cut still reading slots as fixed-point sums) the answer is taken over by a
+    window that fell back, the symptom the GPU determinism test once showed: every returned id from one
+    window."""
+    from test_selection_model import search_model, truth
+    lam, g = 512, 50
+    rng = np.random.default_rng(3)
+    scores = np.ones(8 * lam, F32)                      # massive ties: every slot of every window at the bound
+    scores[rng.choice(2 * lam, 20, replace=False)] = F32(1.5)
+    want = truth(scores, g)
+    for seed in range(6):
+        got = search_model(scores, lam, g, schedule, np.random.default_rng(seed))
+        assert np.array_equal(got, want), seed
+    planted = search_model(scores, lam, g, schedule, np.random.default_rng(0),
+                           fallthrough_keys=_fp32_bits_read_as_sums)
+    assert not np.array_equal(planted, want)
+    ids = (np.uint64(0xFFFFFFFF) - (planted & np.uint64(0xFFFFFFFF))).astype(np.int64)
+    assert len(set((ids // lam).tolist())) == 1         # one window's slots fill the answer

@@ -106,6 +106,34 @@ def test_fixed_window_sums_do_not_depend_on_the_order_of_the_adds():
                 np.testing.assert_array_equal(a[1].view(np.uint32), x[1].view(np.uint32))
 
 
+@pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_fixed_window_falls_back_to_the_full_cut_on_crowded_bounds(mode):
+    """40,000 documents of one score (exact ties) but 20 higher ones: every bounded fixed-point window holds far
+    more slots at the bound than it may emit, so it converts its sums to FP32 and falls back on the full cut.
+    The answer's scores must be the exact ones (a cut that kept reading FP32 bits as fixed-point sums would
+    return scores thousands of times too large), descending, and no document left out may certainly beat a
+    returned one."""
+    n, dim = 40_000, 16
+    rows = [[(1, 1.0), (2, 0.5), (3, 0.25)] for _ in range(n)]
+    rng = np.random.default_rng(11)
+    for i in rng.choice(n, 20, replace=False):
+        rows[i] = [(1, 1.5), (2, 0.5), (3, 0.25)]
+    ip = np.array([0] + [3 * (i + 1) for i in range(n)], np.int64)
+    ix = np.array([j for r in rows for j, _ in r], np.int32)
+    v = np.array([x for r in rows for _, x in r], np.float32)
+    qp = np.array([0, 3, 5], np.int64)
+    qx = np.array([1, 2, 3, 1, 3], np.int32)
+    qv = np.array([1.0, 1.0, 1.0, 2.0, 0.5], np.float32)
+    D, Q = oracle.Dataset(ip, ix, v, dim), oracle.Dataset(qp, qx, qv, dim)
+    I = oracle.Index(D, window=4096, alpha=1.0)
+    with sindi.Index(dev(ip), dev(ix), dev(v), dim, window=4096, alpha=1.0) as idx:
+        ids, sc = search(idx, (qp, qx, qv), k=50, mode=mode)
+    for r in range(Q.n):
+        s, a = exact_scores(I, I, Q, Q, D.n, r)
+        check_ranked_conditioned(ids[r], sc[r], s, a, int(qp[r + 1] - qp[r]), 50, what=f"query {r}",
+                                 extra=fixed_extra(I, Q, r))
+
+
 def test_plain_lanes_reuse_workspaces_across_queries():
     """The plain schedule runs a lane's queries one after another on one workspace, which each query's merge
     leaves at zero for the next. With gamma 2,000 most queries' candidates exceed one merge block's filter

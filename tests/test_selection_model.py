@@ -54,10 +54,11 @@ def find_bin(hist, g):
 ZERO_KEY_BITS = np.uint64(0x80000000)                 # order bits of +0.0
 
 
-def window_emit(K, g_w, win_cap, bounded, pbin, skip_zero=False):
+def window_emit(K, g_w, win_cap, bounded, pbin, skip_zero=False, fallthrough_keys=None):
     """The keys one window emits (its n_eff slots' keys K). skip_zero: slots whose score is exactly 0 cannot
     count (every score >= 0 and the earlier windows hold at least g slots); a bounded window then emits only
-    positive slots at or above the bound."""
+    positive slots at or above the bound. fallthrough_keys: what a bounded window with more slots at the bound
+    than it may emit does to the keys of the full cut it falls back on (None: nothing, as the device does)."""
     b = bins_of(K)
     if bounded:
         ok = b >= pbin
@@ -66,6 +67,9 @@ def window_emit(K, g_w, win_cap, bounded, pbin, skip_zero=False):
         hi = K[ok]
         if len(hi) <= win_cap:
             return hi
+        if fallthrough_keys is not None:
+            out = window_emit(K, g_w, win_cap, False, 0)
+            return fallthrough_keys(out)
     bw, above_bw, _, _ = find_bin(np.bincount(b, minlength=1 << HIST_BITS), g_w)
     lo = max(bw, pbin) if bounded else bw
     thr = np.uint64(lo) << np.uint64(KEY_BIN_SHIFT)
@@ -79,7 +83,7 @@ def window_emit(K, g_w, win_cap, bounded, pbin, skip_zero=False):
     return K[K >= thr]
 
 
-def search_model(scores32, lam, g, schedule, rng, zero_rule="device"):
+def search_model(scores32, lam, g, schedule, rng, zero_rule="device", fallthrough_keys=None):
     """Candidates of every window under `schedule`, then the merge; returns the selected keys, best first.
     zero_rule: "device" skips zero-score slots of window w when no score is negative and w * lam >= g;
     "off" never skips; "always" skips them whenever no score is negative (a planted mistake)."""
@@ -100,7 +104,7 @@ def search_model(scores32, lam, g, schedule, rng, zero_rule="device"):
             pbin, _, _, total = find_bin(snapshot, g)
             bounded = total >= g
         skip = nonneg and ((zero_rule == "device" and w * lam >= g) or (zero_rule == "always" and w > 0))
-        out = window_emit(K, g_w, win_cap, bounded, pbin, skip)
+        out = window_emit(K, g_w, win_cap, bounded, pbin, skip, fallthrough_keys)
         assert len(out) <= max(win_cap, g_w)
         emitted.append(out)
         np.add.at(H, bins_of(out), 1)
