@@ -107,6 +107,26 @@ def test_fixed_window_sums_do_not_depend_on_the_order_of_the_adds():
 
 
 @pytest.mark.parametrize("mode", ["plain", "batched"])
+def test_fixed_window_queries_longer_than_one_term_table(mode):
+    """Queries of 700 distinct terms, more than one 512-term table holds: the window's unit comes from a pass
+    of its own over all the query's terms before the first table's adds. Coarse scores within the bound of
+    the exact FP64 scores, descending, and no left-out document certainly beats a returned one."""
+    w, (ip, ix, v), _ = _workload(40_000, 2, False)
+    rng = np.random.default_rng(21)
+    nq, nt = 6, 700
+    qx = np.concatenate([np.sort(rng.choice(w.dim, nt, replace=False)) for _ in range(nq)]).astype(np.int32)
+    qv = rng.lognormal(0.0, 0.8, nq * nt).astype(np.float32)
+    qp = np.arange(0, nq * nt + 1, nt, dtype=np.int64)
+    D, Q = oracle.Dataset(ip, ix, v, w.dim), oracle.Dataset(qp, qx, qv, w.dim)
+    I = oracle.Index(D, window=4096, alpha=0.5)
+    with sindi.Index(dev(ip), dev(ix), dev(v), w.dim, window=4096, alpha=0.5) as idx:
+        ids, sc = search(idx, (qp, qx, qv), k=50, mode=mode)
+    for r in range(Q.n):
+        s, a = exact_scores(I, I, Q, Q, D.n, r)
+        check_ranked_conditioned(ids[r], sc[r], s, a, nt, 50, what=f"query {r}", extra=fixed_extra(I, Q, r))
+
+
+@pytest.mark.parametrize("mode", ["plain", "batched"])
 def test_fixed_window_falls_back_to_the_full_cut_on_crowded_bounds(mode):
     """40,000 documents of one score (exact ties) but 20 higher ones: every bounded fixed-point window holds far
     more slots at the bound than it may emit, so it converts its sums to FP32 and falls back on the full cut.
