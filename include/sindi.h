@@ -98,8 +98,8 @@ typedef enum {
    unpruned index. */
 typedef struct {
     uint32_t window;       /* lambda, documents per window (Sec. 3.3.1); 1..32768.
-                              0 picks a default. A window's FP32 score array lives
-                              in one thread block's shared memory.                */
+                              0 picks a default. A window's score array (4 bytes a
+                              slot) lives in one thread block's shared memory.    */
     int32_t value_dtype;   /* sindi_dtype                                          */
     double alpha;          /* document pruning ratio in (0, 1]; 1 = no pruning.
                               Used by MASS and MASS_LIST, ignored otherwise      */

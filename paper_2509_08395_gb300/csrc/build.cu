@@ -304,7 +304,7 @@ __global__ void lp_compact_kernel(const uint32_t* keep, const uint32_t* off, int
 // Posting order inside every list segment I_{j,w}, for the window scan's
 // shared-memory scatter-add: the 32 postings one add instruction of a warp
 // takes should sit in 32 different shared-memory banks (window slot mod 32),
-// which makes the FP32 atomicAdd conflict-free. One warp per segment:
+// which makes the shared-memory atomicAdd conflict-free. One warp per segment:
 //   1. every posting gets its bank b and a rank r among the segment's
 //      postings of bank b; ordering the postings by (r, b) visits the banks
 //      round robin, so any 32 consecutive ones hold 32 banks while every bank

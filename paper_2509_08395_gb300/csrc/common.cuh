@@ -16,7 +16,7 @@ namespace sindi {
 // ---------------------------------------------------------------------------
 // Limits of this build.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kMaxWindow = 32768;       // lambda: FP32 window must fit one block's smem
+constexpr uint32_t kMaxWindow = 32768;       // lambda: the window's 4-byte slots must fit one block's smem
 constexpr uint32_t kDefaultWindow = 8192;
 constexpr int64_t kMaxRowNnz = 16384;        // longest document row the build sorts on chip
 constexpr uint32_t kMaxK = 1024;

@@ -2,9 +2,11 @@
 // stage.
 //
 //   scan_window  (one block per (query, window)): the query's postings in the
-//       window, I_{j,w} for every term j, are scatter-added into an FP32 score
-//       array A[lambda] in shared memory (Alg. 2, the product + accumulation
-//       loops). The block then histograms the window's scores on the top 12
+//       window, I_{j,w} for every term j, are scatter-added into a score array
+//       A[lambda] in shared memory (Alg. 2, the product + accumulation loops):
+//       FP32 sums, or 32-bit fixed-point sums of the FP32 products (the default
+//       when the search reorders; fixed_point.cuh), read as FP32 scores by the
+//       cut. The block then histograms the window's scores on the top 12
 //       bits of their order key and emits every slot in the bins at or above
 //       the bin that holds its g-th best slot (the window's share of the heap
 //       update of Alg. 2). When ties crowd that bin, an exact radix select
