@@ -28,6 +28,13 @@ SINDI_PRUNE_MASS, SINDI_PRUNE_VECTOR_NUMBER, SINDI_PRUNE_LIST, SINDI_PRUNE_MASS_
 SINDI_SCAN_PIPELINED = 1  # block_threads value of the pipelined window scan
 SINDI_ACCUM_AUTO, SINDI_ACCUM_F32, SINDI_ACCUM_FIXED32 = 0, 1, 2
 ACCUMS = {"auto": SINDI_ACCUM_AUTO, "f32": SINDI_ACCUM_F32, "fixed32": SINDI_ACCUM_FIXED32}
+
+
+def _accum(accum: str) -> int:
+    """sindi_accumulator value of `accum` ("auto", "f32" or "fixed32")."""
+    if accum not in ACCUMS:
+        raise ValueError(f"accum must be one of {sorted(ACCUMS)}, not {accum!r}")
+    return ACCUMS[accum]
 PRUNES = {"mass": SINDI_PRUNE_MASS, "vector_number": SINDI_PRUNE_VECTOR_NUMBER, "list": SINDI_PRUNE_LIST,
           "mass_list": SINDI_PRUNE_MASS_LIST}
 STATUS_NAMES = {0: "SINDI_OK", 1: "SINDI_ERR_INVALID_ARG", 2: "SINDI_ERR_INVALID_DATA", 3: "SINDI_ERR_OOM",
@@ -211,7 +218,7 @@ def sindi_search(index: int, q_indptr, q_indices, q_values, n_queries: int, out_
     accum: the coarse scan's score window, "auto", "f32" or "fixed32" (sindi_accumulator)."""
     lib = load()
     prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block),
-                              group=int(group), accumulator=ACCUMS[accum])
+                              group=int(group), accumulator=_accum(accum))
     _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     st = lib.sindi_search(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                           _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm), _ptr(out_ids, np.uint32),
@@ -226,7 +233,7 @@ def sindi_search_noalloc(index: int, q_indptr, q_indices, q_values, n_queries: i
     static 8 MiB device array. Device tensors only; calls that overlap on the GPU race on that array."""
     lib = load()
     prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=MODES[mode], block_threads=int(block),
-                              group=int(group), accumulator=ACCUMS[accum])
+                              group=int(group), accumulator=_accum(accum))
     _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     st = lib.sindi_search_noalloc(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
                                   _ptr(q_values, np.float32), int(n_queries), ctypes.byref(prm),
@@ -397,7 +404,7 @@ class Index:
 def sindi_plan_create(index: int, q_indptr, q_indices, q_values, n_queries: int, out_ids, out_scores, k: int,
                       gamma: int = 0, beta: float = 1.0, block: int = 0, group: int = 0, accum: str = "auto") -> int:
     prm = sindi_search_params(k=int(k), gamma=int(gamma), beta=float(beta), mode=SINDI_MODE_BATCHED, block_threads=int(block),
-                              group=int(group), accumulator=ACCUMS[accum])
+                              group=int(group), accumulator=_accum(accum))
     _require_search(q_indptr, out_ids, out_scores, n_queries, k)
     out = ctypes.c_void_p()
     _check(load().sindi_plan_create(ctypes.c_void_p(index), _ptr(q_indptr, np.int64), _ptr(q_indices, np.int32),
@@ -466,7 +473,7 @@ def sindi_server_create(index: int, k: int, gamma: int = 0, beta: float = 1.0, m
     prm = sindi_server_params(max_batch=max_batch, max_slots=max_slots, max_query_nnz=max_query_nnz,
                               max_wait_us=max_wait_us, memory_budget=memory_budget,
                               search=sindi_search_params(k=k, gamma=gamma, beta=beta, mode=SINDI_MODE_BATCHED,
-                                                         block_threads=0, accumulator=ACCUMS[accum]))
+                                                         block_threads=0, accumulator=_accum(accum)))
     out = ctypes.c_void_p()
     _check(load().sindi_server_create(ctypes.c_void_p(index), ctypes.byref(prm), ctypes.byref(out)),
            "sindi_server_create")

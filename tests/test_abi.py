@@ -110,6 +110,9 @@ def test_binding_checks_buffer_sizes_before_the_call(lib):
         sindi.sindi_search(1, qp, qx, qv, 3, np.empty((3, 10), np.uint32), np.empty((3, 10), np.float32), k=10)
     with pytest.raises(ValueError, match="indptr"):
         sindi.sindi_build(np.zeros(3, np.int64), qx, qv, 5, 4)
+    with pytest.raises(ValueError, match="accum"):
+        sindi.sindi_search(1, qp, qx, qv, 2, ids, sc, k=10, accum="fp16")
+    assert sindi._accum("auto") == 0 and sindi._accum("f32") == 1 and sindi._accum("fixed32") == 2
 
     class FakeStream:
         cuda_stream = 1234
