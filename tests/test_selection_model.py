@@ -54,14 +54,16 @@ def find_bin(hist, g):
 ZERO_KEY_BITS = np.uint64(0x80000000)                 # order bits of +0.0
 
 
-def window_emit(K, g_w, win_cap, bounded, pbin, skip_zero=False, fallthrough_keys=None):
+def window_emit(K, g_w, win_cap, bounded, pbin, skip_zero=False, fallthrough_keys=None, slack=0):
     """The keys one window emits (its n_eff slots' keys K). skip_zero: slots whose score is exactly 0 cannot
     count (every score >= 0 and the earlier windows hold at least g slots); a bounded window then emits only
     positive slots at or above the bound. fallthrough_keys: what a bounded window with more slots at the bound
-    than it may emit does to the keys of the full cut it falls back on (None: nothing, as the device does)."""
+    than it may emit does to the keys of the full cut it falls back on (None: nothing, as the device does).
+    slack: a bounded window also emits the slots of this many bins below the bound (the fixed-point window's
+    integer bound may emit a few slots just under it)."""
     b = bins_of(K)
     if bounded:
-        ok = b >= pbin
+        ok = b >= pbin - slack
         if skip_zero:
             ok &= (K >> np.uint64(32)) > ZERO_KEY_BITS     # score > 0
         hi = K[ok]
@@ -83,7 +85,7 @@ def window_emit(K, g_w, win_cap, bounded, pbin, skip_zero=False, fallthrough_key
     return K[K >= thr]
 
 
-def search_model(scores32, lam, g, schedule, rng, zero_rule="device", fallthrough_keys=None):
+def search_model(scores32, lam, g, schedule, rng, zero_rule="device", fallthrough_keys=None, slack=0):
     """Candidates of every window under `schedule`, then the merge; returns the selected keys, best first.
     zero_rule: "device" skips zero-score slots of window w when no score is negative and w * lam >= g;
     "off" never skips; "always" skips them whenever no score is negative (a planted mistake)."""
@@ -104,7 +106,7 @@ def search_model(scores32, lam, g, schedule, rng, zero_rule="device", fallthroug
             pbin, _, _, total = find_bin(snapshot, g)
             bounded = total >= g
         skip = nonneg and ((zero_rule == "device" and w * lam >= g) or (zero_rule == "always" and w > 0))
-        out = window_emit(K, g_w, win_cap, bounded, pbin, skip, fallthrough_keys)
+        out = window_emit(K, g_w, win_cap, bounded, pbin, skip, fallthrough_keys, slack)
         assert len(out) <= max(win_cap, g_w)
         emitted.append(out)
         np.add.at(H, bins_of(out), 1)
@@ -168,6 +170,22 @@ def test_selection_returns_exactly_the_best_g(kind, schedule):
         got = search_model(s, lam, g, schedule, rng)
         want = truth(s, g)
         assert np.array_equal(got, want), (kind, schedule, lam, n, g)
+
+
+@pytest.mark.parametrize("schedule", ["batched", "plain_split"])
+@pytest.mark.parametrize("kind", ["sparse", "ties", "one_bin", "signed"])
+def test_bounded_windows_may_emit_slots_under_the_bound(kind, schedule):
+    """The fixed-point window compares a bounded window's sums with an integer bound that may sit a little
+    under the FP32 bound, so a few slots below it are emitted too. Emitting the whole bin below the bound (a
+    wider superset) still gives exactly the best g: the merge drops the extra slots."""
+    rng = np.random.default_rng(zlib.crc32(f"slack/{kind}/{schedule}".encode()))
+    for trial in range(10):
+        lam = int(rng.choice([64, 256, 1000]))
+        n = int(rng.choice([lam - 1, 3 * lam + 5, 9 * lam + 1, 17 * lam]))
+        g = int(rng.choice([1, 10, 50, 300]))
+        s = score_pattern(kind, n, rng)
+        got = search_model(s, lam, g, schedule, rng, slack=1)
+        assert np.array_equal(got, truth(s, g)), (kind, schedule, lam, n, g)
 
 
 def test_model_keys_order_like_the_search():
